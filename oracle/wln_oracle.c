@@ -216,7 +216,13 @@ void wln_oracle_loop_phase_spin(const double* y, int32_t N, const oracle_profile
     double B = x0 * dx + y0 * dy;
     double C = dx * dx + dy * dy;
     double X = x0 * y1 - y0 * x1;
-    if (C == 0.0) continue;            /* a zero-length segment contributes nothing */
+    if (C == 0.0) {
+      /* A stationary step adds no phase, but the particle still spends proper
+       * time T/N at that point, so the spin integral gains e B(rho^2) T/N. */
+      double Q0s = l2 + A;
+      sp += (T / (double)N) * 2.0 * calF * l2 / (Q0s * Q0s);
+      continue;
+    }
     /* Q(t) = C t^2 + 2 B t + (lambda^2 + A); its discriminant
      * C (lambda^2 + A) - B^2 equals lambda^2 C + X^2 (Lagrange identity
      * A C - B^2 = X^2), which is > 0 for lambda > 0. */

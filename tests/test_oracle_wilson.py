@@ -187,3 +187,19 @@ def test_symmetries():
         ph_q, sp_q = oracle.loop_phase_spin(shifted, prof, 0.0, Tq)
         assert ph_q == pytest.approx(ph, rel=1e-11, abs=1e-13)
         assert sp_q == pytest.approx(spn, rel=1e-11)
+
+
+def test_repeated_point_still_accumulates_spin():
+    # A loop that rests at one point for one step: the phase is unchanged,
+    # the spin integral gains eB(rho^2) T/N for that step (Eq. Wfermfpl).
+    F, lam, T = 6.0, 0.8, 1.3
+    calF = F / (2 * math.pi)
+    base = oracle.gen_loops(707, 1, 8)[0]
+    rep = np.concatenate([base[:, :3], base[:, 2:3], base[:, 3:]], axis=1)   # point 2 twice, N = 9
+    prof = Profile(PROFILE_FLUX_TUBE, F=F, lam=lam)
+    ph9, sp9 = oracle.loop_phase_spin(rep, prof, 0.4, T)
+    ph8, sp8 = oracle.loop_phase_spin(base, prof, 0.4, T)
+    assert ph9 == pytest.approx(ph8, rel=1e-13)
+    r2 = (0.4 + math.sqrt(T) * base[0, 2]) ** 2 + (math.sqrt(T) * base[1, 2]) ** 2
+    eB = 2 * calF * lam**2 / (lam**2 + r2) ** 2
+    assert sp9 == pytest.approx(sp8 * 8 / 9 + eB * T / 9, rel=1e-12)
