@@ -1,0 +1,407 @@
+"""Benchmark of the worldline Wilson-loop path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload paper|small] [--prec fp32|fp64]
+
+One step is one pass of the whole path over the paper-scale workload
+(10240 unit loops of 2048 points, flux tubes F = 1, 10, 50 with lambda = 1,
+64 log-spaced T in [1e-3, 20] x 128 radii in [0, 8], 32 groups):
+  loop generation (Philox -> Box-Muller -> closed, centred loops),
+  Wilson group sums (FP32 compensated unless --prec fp64),
+  group statistics with the full covariance of the spinor loop per profile,
+  and the per-group effective action with its group error.
+The metric is loop-point evaluations per second (loops x points / step time).
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1407_7486_gb300 import inputs as I  # noqa: E402
+
+METRIC = "loop-point evals/s (Wilson loops, FP32-compensated, |d<W>| <= 1e-6)"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 operations per (segment, point) of the compensated walk,
+# counted from the formula in csrc/wln_wilson.cu (FMA = 1 operation): 22
+# for the geometry, closed-form integrals and products, 8 for the two
+# compensated (Kahan) additions, about 12 for the arctangent's reduction and
+# polynomial, and 11 per segment shared by the P = 4 radii of a lane (11/4).
+N_ALG_FP32 = 22 + 8 + 12 + 11 / 4
+N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
+
+
+def _workload(name: str) -> I.Workload:
+    return {"paper": I.paper, "small": I.small}[name]()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1407_7486_gb300", "csrc", "wln_wilson.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _ncu_traffic(workload: str):
+    """DRAM bytes per Wilson launch from the committed ncu summary, or None when
+    the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"wilson_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = k = None
+    for line in text.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            h = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            k = float(line.split(":", 1)[1].strip())
+    return k if (h == _kernel_source_hash() and k) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", cov: bool = True):
+    """One pass of the path; returns (outputs, h2d_bytes, d2h_bytes)."""
+    ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
+    S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec, where=where)
+    lpg = wl.n_loops // wl.n_groups
+    outs = {"S": S}
+    off = 0
+    d2h = S.nbytes if where == "host" else 0
+    h2d = sum(r.nbytes + t.nbytes for r, t in zip(wl.rho, wl.T))
+    for q, (r, t) in enumerate(zip(wl.rho, wl.T)):
+        n = len(r) * len(t)
+        Sq = S[off:off + n]
+        jf = ctx.jackknife(Sq, wl.n_groups, lpg, 1, jk_var=True, cov=cov, where=where)
+        js = ctx.jackknife(Sq, wl.n_groups, lpg, 0, jk_var=False, cov=False, where=where)
+        outs[f"ferm{q}"] = jf
+        outs[f"scal{q}"] = js
+        if where == "host":
+            d2h += sum(v.nbytes for v in jf.values() if v is not None)
+            d2h += sum(v.nbytes for v in js.values() if v is not None)
+            h2d += Sq.nbytes * 2
+        off += n
+    gg, ms = ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True,
+                                  where=where)
+    outs["gamma"] = (gg, ms)
+    if where == "host":
+        d2h += gg.nbytes + ms.nbytes
+        h2d += S.nbytes
+    ens.free()
+    return outs, h2d, d2h
+
+
+def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0):
+    """Time the FP64 oracle on the host cores on a bounded sample of the workload
+    (one flux tube, a sparse subset of points, loops of the first groups), and
+    compare the GPU's group sums on that sample with it."""
+    import oracle
+    threads = oracle.max_threads()
+    q = 1 if len(wl.profiles) > 1 else 0
+    prof = wl.profiles[q]
+    rho = wl.rho[q][::8]
+    T = wl.T[q][::8]
+    lpg = wl.n_loops // wl.n_groups
+    # calibrate on one group
+    y = oracle.gen_loops(wl.seed, lpg, wl.ppl).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.group_sums(y, prof, rho[:1], T[:1], 1, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    per_lp = dt / lpg
+    n_groups = int(max(1, min(wl.n_groups, budget_s / (per_lp * lpg * len(rho) * len(T)))))
+    y = oracle.gen_loops(wl.seed, n_groups * lpg, wl.ppl).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    ref = oracle.group_sums(y, prof, rho, T, n_groups, threads=threads)
+    dt = time.perf_counter() - t0
+    lp = n_groups * lpg * len(rho) * len(T)
+    # GPU result on the same sample (same loops: the first n_groups groups of the ensemble)
+    err = {}
+    ens = gpu_ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+    for prec in ("fp32", "fp64"):
+        S = gpu_ctx.wilson_avg(ens, [prof], [rho], [T], wl.n_groups, prec=prec, where="host")
+        S = S[:, :n_groups]
+        d = np.abs(S - ref) / lpg
+        err[prec] = {"scal_max_abs": float(d[:, :, 0].max()), "ferm_max_abs": float(d[:, :, 1].max())}
+    ens.free()
+    return {"value": lp / dt, "unit": "loop-point evals/s", "cores": threads, "kind": "oracle",
+            "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every 8th), "
+                      f"{n_groups * lpg} loops ({n_groups} groups) x {wl.ppl} ppl; {dt:.1f} s",
+            "gpu_error_vs_oracle_on_sample": err}
+
+
+def reference_arm(args, wl: I.Workload):
+    """The oracle as it stands on the host cores, each step a bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    threads = oracle.max_threads()
+    q = 1 if len(wl.profiles) > 1 else 0
+    prof, rho, T = wl.profiles[q], wl.rho[q][::16], wl.T[q][::16]
+    lpg = wl.n_loops // wl.n_groups
+    y = oracle.gen_loops(wl.seed, lpg, wl.ppl)
+
+    def step():
+        oracle.group_sums(y, prof, rho, T, 1, threads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    lp = lpg * len(rho) * len(T)
+    v = lp / dt
+    sample = (f"per step: F={prof.F}, {len(rho)} rho x {len(T)} T (every 16th), {lpg} loops "
+              f"(one group) x {wl.ppl} ppl")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "loop-point evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name},
+        "cpu_baseline": {"value": v, "unit": "loop-point evals/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "loop-point evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wln", choices=["wln", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = _workload(args.workload)
+
+    if args.impl == "reference":
+        return reference_arm(args, wl)
+
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    build.build()
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    ctx = wln.Context(dev, stream)
+    seed = wl.seed + rank       # weak scaling: every rank its own ensemble
+
+    # warm-up (compiles nothing; fills caches, grows scratch)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run_step(ctx, wl, seed, args.prec)
+    stream.synchronize()
+
+    # device-resident timed region
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = ctx.launch_count
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk, torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(args.steps):
+            ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
+            wk[i][0].record(stream)
+            S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+            wk[i][1].record(stream)
+            lpg = wl.n_loops // wl.n_groups
+            off = 0
+            for q, (r, t) in enumerate(zip(wl.rho, wl.T)):
+                n = len(r) * len(t)
+                ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 1, jk_var=True, cov=True)
+                ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 0, jk_var=False, cov=False)
+                off += n
+            ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True)
+            ens.free()
+        e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    launches = ctx.launch_count - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = _max_over_ranks(ms, ws)
+    wilson_ms = statistics.mean(a.elapsed_time(b) for a, b in wk)
+    loop_points = wl.loop_points
+    value = loop_points * ws / (ms / 1e3)
+
+    # end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 2))
+    h2d = d2h = 0
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            _, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True)
+    stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = _max_over_ranks(e2e_s, ws)
+
+    if rank != 0:
+        ctx.close()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
+    seg = wl.segment_evals
+    achieved = N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12
+    traffic = _ncu_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "loop-point evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_loops": wl.n_loops, "ppl": wl.ppl,
+                   "n_points": wl.n_points, "n_groups": wl.n_groups,
+                   "precision": "fp32 compensated" if args.prec == "fp32" else "fp64",
+                   "covariance": "full, spinor, per profile",
+                   "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                     "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "wilson_kernel<F32Comp,4,8>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
+                     "kernel_ms": wilson_ms,
+                     "segment_evals_per_s": seg / (wilson_ms / 1e3),
+                     "n_alg_fp32_per_segment": N_ALG_FP32, "n_alg_mufu_per_segment": N_ALG_MUFU,
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"},
+        "e2e": {"value": loop_points * ws / e2e_s, "unit": "loop-point evals/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    # FP64 GPU path on one profile and a sparse subset of points (it is ~10^2 slower)
+    if args.prec == "fp32":
+        sub_rho = [wl.rho[1][::8]]
+        sub_T = [wl.T[1][::4]]
+        ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
+        ctx.wilson_avg(ens, [wl.profiles[1]], sub_rho, sub_T, wl.n_groups, prec="fp64")
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.wilson_avg(ens, [wl.profiles[1]], sub_rho, sub_T, wl.n_groups, prec="fp64")
+        b.record(stream)
+        stream.synchronize()
+        n_lp = wl.n_loops * len(sub_rho[0]) * len(sub_T[0])
+        line["fp64_gpu"] = {"value": n_lp / (a.elapsed_time(b) / 1e3), "unit": "loop-point evals/s",
+                            "sample": f"F={wl.profiles[1].F}, {len(sub_rho[0])} rho x "
+                                      f"{len(sub_T[0])} T, all loops, Wilson kernel only"}
+        ens.free()
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(wl, ctx)
+    ctx.close()
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

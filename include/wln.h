@@ -1,0 +1,240 @@
+/*
+ * wln.h — C ABI of the GB300 worldline Wilson-loop library (libwln.so).
+ *
+ * The library computes ensemble averages of Wilson loops in cylindrically
+ * symmetric magnetic fields by worldline numerics, following D. Mazur and
+ * J. S. Heyl, "Parallel Worldline Numerics: Implementation and Error
+ * Analysis" (arXiv:1407.7486):
+ *   - unit loops of N points drawn on the device (Sec. "Loop Generation");
+ *   - per loop and per point (rho_cm, T): the loop scaled by sqrt(T), shifted
+ *     to x_cm = (rho_cm, 0), the phase e * closed line integral of A along
+ *     straight segments (Sec. "Wilson Loop", Eqs. rhoi-Ci) and the spin factor
+ *     cosh(e int B dtau) (Sec. "Fermion Part", Eq. Wfermfpl);
+ *   - sums of W over contiguous groups of loops, and the group statistics
+ *     (Sec. "Grouping Worldlines");
+ *   - the effective-action density by quadrature over rho_cm and T, done for
+ *     every group separately (Eq. cylEA; Sec. "Computing an Effective Action").
+ *
+ * Units: e = m = 1.  A flux-tube profile has raw flux F and radius lambda:
+ *   A_phi(rho) = F rho / (2 pi (lambda^2 + rho^2)),
+ *   e B(rho)   = (F / (pi lambda^2)) (1 + rho^2/lambda^2)^-2,
+ * i.e. f(rho^2) = rho^2/(lambda^2 + rho^2) and calF = F / (2 pi).
+ *
+ * Conventions for every call:
+ *   - Every call returns a wln_status.  On failure the context keeps a
+ *     message (wln_last_error).  The library never aborts the process.
+ *   - Device work is ordered on the context's stream.  Unless stated
+ *     otherwise, output arrays may be host or device memory; the library
+ *     inspects each pointer.  A call with any host output synchronises the
+ *     stream before it returns.  A call whose outputs are all device
+ *     pointers returns as soon as the work is queued.
+ *   - Arrays described as "host" must be host memory.  The caller owns
+ *     every array it passes.  The library owns contexts and ensembles.
+ *   - Errors detected on the device (a bounded wait that ran out) are
+ *     reported as WLN_ETIMEOUT by the next call that synchronises, or by
+ *     wln_synchronize.
+ */
+#ifndef WLN_H_
+#define WLN_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wln_ctx wln_ctx;            /* opaque; one device, one stream */
+typedef struct wln_ensemble wln_ensemble;  /* opaque; device-resident loops */
+
+typedef enum {
+  WLN_OK = 0,
+  WLN_EINVAL = 1,    /* an argument breaks a documented rule */
+  WLN_ENOMEM = 2,    /* device or pinned host allocation failed */
+  WLN_ECUDA = 3,     /* a CUDA runtime call failed (message holds its text) */
+  WLN_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+  WLN_EBUSY = 5      /* resource in use (server full, request pending) */
+} wln_status;
+
+typedef enum {
+  WLN_PREC_FP64 = 0,        /* segment sums and transcendentals in double */
+  WLN_PREC_FP32_COMP = 1,   /* FP32 segments, compensated (Kahan) sums, phase
+                               range-reduced in turns, W and its sums in FP64 */
+  WLN_PREC_FP32_NAIVE = 2   /* FP32 segments and plain FP32 sums */
+} wln_prec;
+
+enum {
+  WLN_PROFILE_FLUX_TUBE = 0,  /* uses F and lambda (lambda > 0) */
+  WLN_PROFILE_CONST_B = 1     /* uses B: phase = B * area, spin = B T */
+};
+
+typedef struct {
+  int32_t kind;       /* WLN_PROFILE_* */
+  int32_t reserved;   /* set to 0 */
+  double F;           /* flux-tube raw flux */
+  double lambda;      /* flux-tube radius */
+  double B;           /* constant field strength */
+} wln_profile;
+
+/* Components of a group sum, in this order (WLN_K per point and group). */
+#define WLN_K 5
+enum {
+  WLN_C_SCAL = 0,     /* sum over the group of (W_scal - 1), W_scal = cos(phase) */
+  WLN_C_FERM = 1,     /* sum of (W_ferm - 1), W_ferm = cos(phase) cosh(spin) */
+  WLN_C_SIN = 2,      /* sum of sin(phase) (imaginary part, zero on average) */
+  WLN_C_SCAL_SQ = 3,  /* sum of (W_scal - 1)^2 */
+  WLN_C_FERM_SQ = 4   /* sum of (W_ferm - 1)^2 */
+};
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t (NULL: the legacy default stream).  The caller keeps
+ * ownership of the stream. */
+wln_status wln_create(wln_ctx** out, int device, void* cuda_stream);
+wln_status wln_destroy(wln_ctx* ctx);
+/* Replace the stream used by later calls. */
+wln_status wln_set_stream(wln_ctx* ctx, void* cuda_stream);
+/* Wait for all queued work; report device-side errors. */
+wln_status wln_synchronize(wln_ctx* ctx);
+/* Message of the last failure on this context ("" if none).  The string is
+ * owned by the context and valid until its next call. */
+const char* wln_last_error(const wln_ctx* ctx);
+/* Number of kernel launches this context has issued since creation. */
+int64_t wln_launch_count(const wln_ctx* ctx);
+
+/* --------------------------------------------------------------- ensembles */
+
+/*
+ * Draw n_loops closed unit loops of ppl points (Sec. "Loop Generation").
+ * Loop l uses Philox-4x32-10 (Salmon et al., SC'11) with counter (j, l, 0, 0),
+ * j = 0 .. ppl/2 - 1, and key (seed & 0xffffffff, seed >> 32).  The four
+ * words u0..u3 of call j map to u = (k + 1/2) 2^-32, and Box-Muller gives
+ *   (u0, u1) -> (xi_x[2j], xi_y[2j]),  (u2, u3) -> (xi_x[2j+1], xi_y[2j+1]),
+ *   z = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b),  xi = z sqrt(2/ppl),
+ * the discretised free action's increment law (variance 2/ppl per component).
+ * Then, in double precision: xi <- xi - mean(xi) (closure), y_k = sum_{j<k}
+ * xi_j, y <- y - mean(y) (common centre of mass, d-loop step 5).  The points
+ * are stored as float on the device.  keep_fp64 != 0 also keeps a double copy.
+ * Rules: ppl a power of two, 4 <= ppl <= 16384; 1 <= n_loops <= 2^24.
+ * The call synchronises.  It returns WLN_EINVAL if two consecutive stored
+ * points coincide (a zero-length segment), which has negligible probability.
+ */
+wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int32_t n_loops, int32_t ppl,
+                         int32_t keep_fp64, wln_ensemble** out);
+
+/*
+ * Make an ensemble from given loops, e.g. a saved one.  xy is
+ * float[n_loops][2][ppl] (x block, then y block of each loop).  It may be host
+ * or device memory.  Same rules as wln_gen_loops, and no two consecutive points
+ * of a loop (cyclically) may coincide.  The library copies the data.  The call
+ * synchronises.
+ */
+wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops,
+                                  int32_t ppl, wln_ensemble** out);
+wln_status wln_free_ensemble(wln_ctx* ctx, wln_ensemble* ens);
+/* Sizes of an ensemble; any output may be NULL. */
+wln_status wln_ensemble_info(const wln_ensemble* ens, int32_t* n_loops, int32_t* ppl,
+                             int32_t* has_fp64);
+/*
+ * Copy the loops out as float[n_loops][2][ppl] and/or double[n_loops][2][ppl]
+ * (host or device).  Either pointer may be NULL.  The double copy needs
+ * keep_fp64.
+ */
+wln_status wln_loops_copy(wln_ctx* ctx, const wln_ensemble* ens, float* xy_f32,
+                          double* xy_f64);
+/*
+ * The raw Philox words used for loops loop0 .. loop0 + n_loops - 1 (the
+ * first step of wln_gen_loops).  out is uint32[n_loops][n_calls][4], host or
+ * device.
+ */
+wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                             int32_t n_calls, uint32_t* out);
+
+/* ------------------------------------------------------------ Wilson loops */
+
+/*
+ * Group sums of Wilson loops for a batch of profiles, each with its own grid.
+ *
+ * Points: profile q has radii rho_cm[rho_off[q] .. rho_off[q+1]) and proper
+ * times T[T_off[q] .. T_off[q+1]).  Its points are all (rho, T) pairs.
+ * Point index: p = base_q + iT * n_rho_q + i_rho, where base_q counts the
+ * points of profiles 0..q-1.  For each point and each loop the loop is
+ * r_k = (rho_cm, 0) + sqrt(T) y_k, k = 0..N-1, closed by straight segments
+ * r_k -> r_{k+1 mod N}:
+ *   phase = e * closed int A.dr along the segments, exactly (Eqs. rhoi-Ci);
+ *   spin  = e int_0^T B dtau, each segment taking proper time T/N, exactly.
+ * W_scal = cos(phase), W_ferm = cos(phase) cosh(spin) (Eq. wilsonloop, its
+ * real part).
+ * Group g holds loops g n/G .. (g+1) n/G - 1 (Sec. "Grouping Worldlines").
+ *
+ * group_sums: double[n_points][n_groups][WLN_K], host or device (see
+ * WLN_C_*).  Every point's sums are accumulated in one fixed order, whatever
+ * else is in the batch, so a point's result does not depend on the batch.
+ * profiles, rho_cm, rho_off, T, T_off: host arrays.
+ * Rules: n_groups >= 2 divides n_loops; T > 0; rho_cm >= 0; lambda > 0 for
+ * flux tubes; every profile has at least one rho and one T.
+ */
+wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
+                          const wln_profile* profiles, int32_t n_profiles,
+                          const double* rho_cm, const int32_t* rho_off,
+                          const double* T, const int32_t* T_off,
+                          int32_t n_groups, wln_prec prec, double* group_sums);
+
+/* -------------------------------------------------------------- statistics */
+
+/*
+ * Group statistics of component `comp` of group sums (layout as
+ * wln_wilson_avg), Sec. "Grouping Worldlines":
+ *   m_g(p) = S_g(p) / loops_per_group       (the group means)
+ *   mean(p) = (1/G) sum_g m_g(p)             (= the mean over all loops)
+ *   sem(p) = sqrt(sum_g (m_g - mean)^2 / (G (G - 1)))
+ *   jk_var(p) = (G-1)/G sum_g (m_(-g) - mean)^2, m_(-g) = (G mean - m_g)/(G-1)
+ *   cov(p, q) = sum_g (m_g(p) - mean(p)) (m_g(q) - mean(q)) / (G (G - 1))
+ * For comp = WLN_C_SCAL or WLN_C_FERM the mean is <W> - 1.
+ * Arrays: group_sums double[n_points][n_groups][WLN_K]; mean, sem, jk_var
+ * double[n_points]; cov double[n_points][n_points].  jk_var and cov may be
+ * NULL.  All arrays are host or device.
+ */
+wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                         int32_t n_groups, int32_t loops_per_group, int32_t comp,
+                         double* mean, double* sem, double* jk_var, double* cov);
+
+/*
+ * Standard error in the mean over individual loops (Sec. "The Worldline
+ * Ensemble Distribution is not Normal"), from the sums of W - 1 (comp_sum) and
+ * (W - 1)^2 (comp_sq):
+ *   sqrt((sum w^2 - (sum w)^2 / n_loops) / (n_loops (n_loops - 1))).
+ * out: double[n_points], host or device.
+ */
+wln_status wln_loop_sem(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                        int32_t n_groups, int32_t n_loops, int32_t comp_sum,
+                        int32_t comp_sq, double* out);
+
+/*
+ * Effective-action density per group and its group mean and standard error
+ * (Eq. cylEA; Sec. "Grouping Worldlines": integrate each group separately):
+ *   Gamma_g = (1/4 pi) int rho drho int dT e^{-T}/T^3 {<W>_g - 1 - c (eB T)^2}
+ * with c = 1/3 for the spinor loop (spinor != 0, component WLN_C_FERM) and
+ * c = -1/6 for the scalar loop (component WLN_C_SCAL, counterterm of Eq.
+ * scalI).  eB is the profile's field at rho_cm.  Quadrature: Simpson in rho
+ * on evenly spaced radii, and Simpson in u = ln T on geometrically spaced
+ * proper times (dT = T du).  An even point count ends with a 3/8 panel; two
+ * points use the trapezoid; one point gives zero.
+ * Profiles and grids as in wln_wilson_avg (host arrays); each profile's rho
+ * must be evenly spaced and its T geometric (relative tolerance 1e-9), else
+ * WLN_EINVAL.  group_sums as written by wln_wilson_avg for the same batch.
+ * gamma_groups: double[n_profiles][n_groups] or NULL; gamma_mean_sem:
+ * double[n_profiles][2] (mean, standard error).  Host or device.
+ */
+wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles,
+                                int32_t n_profiles, const double* rho_cm,
+                                const int32_t* rho_off, const double* T,
+                                const int32_t* T_off, const double* group_sums,
+                                int32_t n_groups, int32_t loops_per_group, int32_t spinor,
+                                double* gamma_groups, double* gamma_mean_sem);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WLN_H_ */

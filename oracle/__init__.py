@@ -65,6 +65,9 @@ def _load():
     lib.wln_oracle_phase_spin_many.argtypes = [f64p, ctypes.c_int64, ctypes.c_int32,
                                                ctypes.POINTER(_Profile), ctypes.c_double,
                                                ctypes.c_double, f64p, f64p, ctypes.c_int32]
+    lib.wln_oracle_phase_abs_many.argtypes = [f64p, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.POINTER(_Profile), ctypes.c_double,
+                                              ctypes.c_double, f64p, ctypes.c_int32]
     lib.wln_oracle_wilson_terms.argtypes = [ctypes.c_double, ctypes.c_double, f64p]
     lib.wln_oracle_group_sums.argtypes = [f64p, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(_Profile), f64p, ctypes.c_int32,
@@ -145,6 +148,16 @@ def phase_spin(y: np.ndarray, profile, rho_cm: float, T: float, threads: int = 0
     _load().wln_oracle_phase_spin_many(y, n, y.shape[-1], ctypes.byref(_prof(profile)),
                                        float(rho_cm), float(T), ph, sp, threads or max_threads())
     return ph, sp
+
+
+def phase_abs(y: np.ndarray, profile, rho_cm: float, T: float, threads: int = 0) -> np.ndarray:
+    """Per loop, the sum over segments of |segment phase| (condition number of
+    the phase sum, used to size rounding-error bars)."""
+    y = np.ascontiguousarray(y, np.float64)
+    out = np.zeros(y.shape[0], np.float64)
+    _load().wln_oracle_phase_abs_many(y, y.shape[0], y.shape[-1], ctypes.byref(_prof(profile)),
+                                      float(rho_cm), float(T), out, threads or max_threads())
+    return out
 
 
 def wilson_terms(phase: float, spin: float) -> np.ndarray:

@@ -243,6 +243,44 @@ void wln_oracle_loop_phase_spin(const double* y, int32_t N, const oracle_profile
   *spin = sp;
 }
 
+/* Sum over segments of |phase of the segment|: the condition number of the
+ * phase sum (how much rounding in the terms can move the total).  Same
+ * closed forms as wln_oracle_loop_phase_spin; flux tube only (the constant
+ * field returns |B| times the sum of |shoelace terms| / 2). */
+double wln_oracle_loop_phase_abs(const double* y, int32_t N, const oracle_profile* prof,
+                                 double rho_cm, double T) {
+  const double* yx = y;
+  const double* yy = y + N;
+  const double sqT = sqrt(T);
+  const double calF = prof->F / (2.0 * M_PI);
+  const double l2 = prof->lambda * prof->lambda;
+  double acc = 0.0;
+  for (int32_t k = 0; k < N; ++k) {
+    int32_t k1 = (k + 1) % N;
+    double x0 = rho_cm + sqT * yx[k], y0 = sqT * yy[k];
+    double x1 = rho_cm + sqT * yx[k1], y1 = sqT * yy[k1];
+    double X = x0 * y1 - y0 * x1;
+    if (prof->kind == 1) {
+      acc += fabs(prof->B * 0.5 * X);
+      continue;
+    }
+    double dx = x1 - x0, dy = y1 - y0;
+    double B = x0 * dx + y0 * dy, C = dx * dx + dy * dy;
+    if (C == 0.0) continue;
+    double D = l2 * C + X * X, sD = sqrt(D);
+    acc += fabs(calF * X * atan2(C * sD, D + B * (B + C)) / sD);
+  }
+  return acc;
+}
+
+void wln_oracle_phase_abs_many(const double* y, int64_t n_loops, int32_t N,
+                               const oracle_profile* prof, double rho_cm, double T,
+                               double* out, int32_t threads) {
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+  for (int64_t l = 0; l < n_loops; ++l)
+    out[l] = wln_oracle_loop_phase_abs(y + (size_t)l * 2 * N, N, prof, rho_cm, T);
+}
+
 /* Per-loop phase and spin for loops y[l][2][N] at one point. */
 void wln_oracle_phase_spin_many(const double* y, int64_t n_loops, int32_t N,
                                 const oracle_profile* prof, double rho_cm, double T,

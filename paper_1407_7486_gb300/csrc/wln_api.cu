@@ -1,0 +1,648 @@
+// C ABI of libwln: argument checks, device buffers and launch sequencing.
+// The arithmetic lives in wln_gen.cu, wln_wilson.cu and wln_stats.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wln_internal.cuh"
+
+namespace wln {
+
+wln_status fail(wln_ctx* ctx, wln_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+wln_status cuda_fail(wln_ctx* ctx, cudaError_t err, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(err);
+  (void)cudaGetLastError();
+  return fail(ctx, err == cudaErrorMemoryAllocation ? WLN_ENOMEM : WLN_ECUDA, m);
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+wln_status ensure_scratch(wln_ctx* ctx, size_t bytes) {
+  if (ctx->scratch.bytes >= bytes) return WLN_OK;
+  cudaError_t err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "synchronize before growing scratch");
+  if (ctx->scratch.ptr) cudaFree(ctx->scratch.ptr);
+  ctx->scratch.ptr = nullptr;
+  ctx->scratch.bytes = 0;
+  const size_t want = bytes + bytes / 4;
+  err = cudaMalloc(&ctx->scratch.ptr, want);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMalloc scratch");
+  ctx->scratch.bytes = want;
+  return WLN_OK;
+}
+
+wln_status ensure_pinned(wln_ctx* ctx, size_t bytes) {
+  // The previous upload from the staging buffer must have finished.
+  cudaError_t err = cudaEventSynchronize(ctx->staging_done);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "wait for staging buffer");
+  if (ctx->pinned_bytes >= bytes) return WLN_OK;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  const size_t want = bytes + bytes / 4 + 4096;
+  err = cudaMallocHost(&ctx->pinned, want);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaMallocHost staging");
+  ctx->pinned_bytes = want;
+  return WLN_OK;
+}
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the context's scratch buffer for one call.
+struct Carve {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t n) {
+    const size_t at = align_up(off);
+    off = at + n * sizeof(T);
+    return at;
+  }
+};
+
+template <class T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+wln_status check_flag(wln_ctx* ctx) {
+  int h = 0;
+  cudaError_t err = cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "synchronize");
+  if (h != 0) {
+    cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, WLN_ETIMEOUT,
+                h == kErrTimeoutFull ? "a staged-copy wait ran out (device)"
+                                     : "a buffer-release wait ran out (device)");
+  }
+  return WLN_OK;
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+wln_status check_loops(wln_ctx* ctx, int32_t n_loops, int32_t ppl) {
+  if (!is_pow2(ppl) || ppl < 4 || ppl > 16384)
+    return fail(ctx, WLN_EINVAL, "ppl must be a power of two in [4, 16384]");
+  if (n_loops < 1 || n_loops > (1 << 24))
+    return fail(ctx, WLN_EINVAL, "n_loops must be in [1, 2^24]");
+  return WLN_OK;
+}
+
+wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64, wln_ensemble** out) {
+  wln_ensemble* en = new (std::nothrow) wln_ensemble();
+  if (!en) return fail(ctx, WLN_ENOMEM, "host allocation");
+  en->device = ctx->device;
+  en->e.n_loops = n_loops;
+  en->e.ppl = ppl;
+  en->e.n_blocks = (n_loops + 31) / 32;
+  const size_t n4 = static_cast<size_t>(en->e.n_blocks) * (ppl / 2) * 32;
+  cudaError_t err = cudaMalloc(&en->e.blocks, n4 * sizeof(float4));
+  if (err == cudaSuccess && fp64)
+    err = cudaMalloc(&en->e.xy64, static_cast<size_t>(n_loops) * 2 * ppl * sizeof(double));
+  if (err != cudaSuccess) {
+    if (en->e.blocks) cudaFree(en->e.blocks);
+    delete en;
+    return cuda_fail(ctx, err, "cudaMalloc ensemble");
+  }
+  *out = en;
+  return WLN_OK;
+}
+
+wln_status finish_ensemble(wln_ctx* ctx, wln_ensemble* en, int* d_deg, wln_ensemble** out) {
+  int deg = 0;
+  cudaError_t err = cudaMemcpyAsync(&deg, d_deg, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    wln_free_ensemble(ctx, en);
+    return cuda_fail(ctx, err, "loop generation");
+  }
+  if (deg) {
+    wln_free_ensemble(ctx, en);
+    return fail(ctx, WLN_EINVAL, "two consecutive loop points coincide (zero-length segment)");
+  }
+  *out = en;
+  return WLN_OK;
+}
+
+// A caller's output array: written directly when on the device, through a
+// scratch buffer and a copy back when on the host.
+struct Out {
+  void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  size_t off = 0;
+  bool host = false;
+};
+
+template <class T>
+Out plan_out(Carve& cv, T* user, size_t n) {
+  Out o;
+  o.user = user;
+  o.bytes = n * sizeof(T);
+  o.host = user && !is_device_ptr(user);
+  if (o.host) o.off = cv.take<T>(n);
+  return o;
+}
+
+void bind_out(Out& o, void* base) { o.dev = o.host ? at<void>(base, o.off) : o.user; }
+
+cudaError_t copy_back(const Out& o, cudaStream_t s) {
+  if (!o.host || !o.user) return cudaSuccess;
+  return cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, s);
+}
+
+struct Batch {
+  std::vector<Tile> tiles;
+  std::vector<ProfileDev> profs;
+  std::vector<double> rho;
+  int64_t n_points = 0;
+};
+
+wln_status check_batch(wln_ctx* ctx, const wln_profile* profiles, int32_t n_profiles,
+                       const double* rho_cm, const int32_t* rho_off, const double* T,
+                       const int32_t* T_off) {
+  if (n_profiles < 1 || !profiles || !rho_cm || !rho_off || !T || !T_off)
+    return fail(ctx, WLN_EINVAL, "profiles, grids and offsets are required");
+  if (rho_off[0] != 0 || T_off[0] != 0) return fail(ctx, WLN_EINVAL, "offsets must start at 0");
+  for (int q = 0; q < n_profiles; ++q) {
+    const wln_profile& pr = profiles[q];
+    if (pr.kind != WLN_PROFILE_FLUX_TUBE && pr.kind != WLN_PROFILE_CONST_B)
+      return fail(ctx, WLN_EINVAL, "unknown profile kind");
+    if (pr.kind == WLN_PROFILE_FLUX_TUBE && !(pr.lambda > 0.0 && std::isfinite(pr.lambda) && std::isfinite(pr.F)))
+      return fail(ctx, WLN_EINVAL, "flux tube needs finite F and lambda > 0");
+    if (pr.kind == WLN_PROFILE_CONST_B && !std::isfinite(pr.B))
+      return fail(ctx, WLN_EINVAL, "constant field needs finite B");
+    if (rho_off[q + 1] <= rho_off[q] || T_off[q + 1] <= T_off[q])
+      return fail(ctx, WLN_EINVAL, "every profile needs at least one rho and one T");
+    for (int i = rho_off[q]; i < rho_off[q + 1]; ++i)
+      if (!(rho_cm[i] >= 0.0 && std::isfinite(rho_cm[i]))) return fail(ctx, WLN_EINVAL, "rho_cm must be finite and >= 0");
+    for (int i = T_off[q]; i < T_off[q + 1]; ++i)
+      if (!(T[i] > 0.0 && std::isfinite(T[i]))) return fail(ctx, WLN_EINVAL, "T must be finite and > 0");
+  }
+  return WLN_OK;
+}
+
+void build_batch(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                 const int32_t* rho_off, const double* T, const int32_t* T_off, int ppl, int P,
+                 Batch& bt) {
+  bt.rho.assign(rho_cm, rho_cm + rho_off[n_profiles]);
+  int64_t base = 0;
+  for (int q = 0; q < n_profiles; ++q) {
+    const wln_profile& pr = profiles[q];
+    ProfileDev pd{};
+    pd.kind = pr.kind;
+    if (pr.kind == WLN_PROFILE_FLUX_TUBE) {
+      pd.l2 = pr.lambda * pr.lambda;
+      pd.turns_per = pr.F / (4.0 * kPi * kPi);                       // calF / (2 pi)
+      pd.spin_per = (pr.F / (2.0 * kPi)) * pd.l2 / ppl;              // calF lambda^2 / N
+    } else {
+      pd.l2 = 1.0;
+      pd.turns_per = pr.B / (4.0 * kPi);
+      pd.spin_per = pr.B;
+    }
+    bt.profs.push_back(pd);
+    const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
+    for (int it = 0; it < nt; ++it)
+      for (int a = 0; a < nr; a += P) {
+        Tile t{};
+        t.profile = q;
+        t.n_valid = nr - a < P ? nr - a : P;
+        t.rho0 = rho_off[q] + a;
+        t.p0 = static_cast<int32_t>(base + static_cast<int64_t>(it) * nr + a);
+        t.T = T[T_off[q] + it];
+        bt.tiles.push_back(t);
+      }
+    base += static_cast<int64_t>(nr) * nt;
+  }
+  bt.n_points = base;
+}
+
+}  // namespace
+}  // namespace wln
+
+using namespace wln;
+
+extern "C" {
+
+wln_status wln_create(wln_ctx** out, int device, void* cuda_stream) {
+  if (!out) return WLN_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t err = cudaGetDeviceCount(&n);
+  if (err != cudaSuccess || n == 0) {
+    (void)cudaGetLastError();
+    return WLN_ECUDA;
+  }
+  if (device < 0 || device >= n) return WLN_EINVAL;
+  wln_ctx* ctx = new (std::nothrow) wln_ctx();
+  if (!ctx) return WLN_ENOMEM;
+  DeviceGuard guard(device);
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  err = cudaMalloc(&ctx->d_flag, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(ctx->d_flag, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    delete ctx;
+    return WLN_ECUDA;
+  }
+  *out = ctx;
+  return WLN_OK;
+}
+
+wln_status wln_destroy(wln_ctx* ctx) {
+  if (!ctx) return WLN_EINVAL;
+  DeviceGuard guard(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->scratch.ptr) cudaFree(ctx->scratch.ptr);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->d_flag) cudaFree(ctx->d_flag);
+  if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  delete ctx;
+  return WLN_OK;
+}
+
+wln_status wln_set_stream(wln_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return WLN_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return WLN_OK;
+}
+
+wln_status wln_synchronize(wln_ctx* ctx) {
+  if (!ctx) return WLN_EINVAL;
+  DeviceGuard guard(ctx->device);
+  return check_flag(ctx);
+}
+
+const char* wln_last_error(const wln_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int64_t wln_launch_count(const wln_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int32_t n_loops, int32_t ppl,
+                         int32_t keep_fp64, wln_ensemble** out) {
+  if (!ctx || !out) return fail(ctx, WLN_EINVAL, "null argument");
+  *out = nullptr;
+  wln_status st = check_loops(ctx, n_loops, ppl);
+  if (st != WLN_OK) return st;
+  DeviceGuard guard(ctx->device);
+  wln_ensemble* en = nullptr;
+  if ((st = alloc_ensemble(ctx, n_loops, ppl, keep_fp64 != 0, &en)) != WLN_OK) return st;
+  if ((st = ensure_scratch(ctx, sizeof(int))) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
+  int* d_deg = static_cast<int*>(ctx->scratch.ptr);
+  cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
+  if (err == cudaSuccess) err = launch_gen_loops(ctx->stream, seed, en->e, d_deg);
+  ctx->launches += 2;
+  if (err != cudaSuccess) {
+    wln_free_ensemble(ctx, en);
+    return cuda_fail(ctx, err, "launch loop generation");
+  }
+  return finish_ensemble(ctx, en, d_deg, out);
+}
+
+wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops, int32_t ppl,
+                                  wln_ensemble** out) {
+  if (!ctx || !out || !xy) return fail(ctx, WLN_EINVAL, "null argument");
+  *out = nullptr;
+  wln_status st = check_loops(ctx, n_loops, ppl);
+  if (st != WLN_OK) return st;
+  DeviceGuard guard(ctx->device);
+  wln_ensemble* en = nullptr;
+  if ((st = alloc_ensemble(ctx, n_loops, ppl, false, &en)) != WLN_OK) return st;
+  const size_t n = static_cast<size_t>(n_loops) * 2 * ppl;
+  const bool dev = is_device_ptr(xy);
+  Carve cv;
+  const size_t o_deg = cv.take<int>(1);
+  const size_t o_xy = dev ? 0 : cv.take<float>(n);
+  if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
+  int* d_deg = at<int>(ctx->scratch.ptr, o_deg);
+  const float* src = xy;
+  cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
+  if (!dev && err == cudaSuccess) {
+    float* d_xy = at<float>(ctx->scratch.ptr, o_xy);
+    err = cudaMemcpyAsync(d_xy, xy, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    src = d_xy;
+  }
+  if (err == cudaSuccess) err = launch_pack_loops(ctx->stream, src, en->e, d_deg);
+  ctx->launches += 2;
+  if (err != cudaSuccess) {
+    wln_free_ensemble(ctx, en);
+    return cuda_fail(ctx, err, "pack loops");
+  }
+  return finish_ensemble(ctx, en, d_deg, out);
+}
+
+wln_status wln_free_ensemble(wln_ctx* ctx, wln_ensemble* ens) {
+  if (!ens) return fail(ctx, WLN_EINVAL, "null ensemble");
+  DeviceGuard guard(ens->device);
+  if (ctx) cudaStreamSynchronize(ctx->stream);
+  if (ens->e.blocks) cudaFree(ens->e.blocks);
+  if (ens->e.xy64) cudaFree(ens->e.xy64);
+  delete ens;
+  return WLN_OK;
+}
+
+wln_status wln_ensemble_info(const wln_ensemble* ens, int32_t* n_loops, int32_t* ppl,
+                             int32_t* has_fp64) {
+  if (!ens) return WLN_EINVAL;
+  if (n_loops) *n_loops = ens->e.n_loops;
+  if (ppl) *ppl = ens->e.ppl;
+  if (has_fp64) *has_fp64 = ens->e.xy64 != nullptr;
+  return WLN_OK;
+}
+
+wln_status wln_loops_copy(wln_ctx* ctx, const wln_ensemble* ens, float* xy_f32, double* xy_f64) {
+  if (!ctx || !ens) return fail(ctx, WLN_EINVAL, "null argument");
+  if (xy_f64 && !ens->e.xy64) return fail(ctx, WLN_EINVAL, "ensemble has no double copy");
+  DeviceGuard guard(ctx->device);
+  const size_t n = static_cast<size_t>(ens->e.n_loops) * 2 * ens->e.ppl;
+  cudaError_t err = cudaSuccess;
+  if (xy_f32) {
+    Carve cv;
+    Out o = plan_out(cv, xy_f32, n);
+    wln_status st = ensure_scratch(ctx, cv.off + 256);
+    if (st != WLN_OK) return st;
+    bind_out(o, ctx->scratch.ptr);
+    err = launch_unpack_loops(ctx->stream, ens->e, static_cast<float*>(o.dev));
+    ++ctx->launches;
+    if (err == cudaSuccess) err = copy_back(o, ctx->stream);
+  }
+  if (err == cudaSuccess && xy_f64)
+    err = cudaMemcpyAsync(xy_f64, ens->e.xy64, n * sizeof(double), cudaMemcpyDefault, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "copy loops");
+  return WLN_OK;
+}
+
+wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                             int32_t n_calls, uint32_t* out) {
+  if (!ctx || !out || n_loops < 0 || n_calls < 0 || loop0 < 0 ||
+      loop0 + n_loops > (int64_t(1) << 32))
+    return fail(ctx, WLN_EINVAL, "bad Philox stream arguments");
+  DeviceGuard guard(ctx->device);
+  const size_t n = static_cast<size_t>(n_loops) * n_calls * 4;
+  Carve cv;
+  Out o = plan_out(cv, out, n);
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(o, ctx->scratch.ptr);
+  cudaError_t err = launch_philox_stream(ctx->stream, seed, loop0, n_loops, n_calls,
+                                         static_cast<uint32_t*>(o.dev));
+  ++ctx->launches;
+  if (err == cudaSuccess) err = copy_back(o, ctx->stream);
+  if (err == cudaSuccess && o.host) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "Philox stream");
+  return WLN_OK;
+}
+
+wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                          int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                          const double* T, const int32_t* T_off, int32_t n_groups,
+                          wln_prec prec, double* group_sums) {
+  if (!ctx || !ens || !group_sums) return fail(ctx, WLN_EINVAL, "null argument");
+  if (prec != WLN_PREC_FP64 && prec != WLN_PREC_FP32_COMP && prec != WLN_PREC_FP32_NAIVE)
+    return fail(ctx, WLN_EINVAL, "unknown precision");
+  if (ens->device != ctx->device) return fail(ctx, WLN_EINVAL, "ensemble lives on another device");
+  if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
+    return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
+  wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
+  if (st != WLN_OK) return st;
+  DeviceGuard guard(ctx->device);
+
+  Batch bt;
+  const int P = plan_points_per_lane(ctx, prec);
+  build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl, P, bt);
+  if (bt.n_points > (int64_t(1) << 31) - 1) return fail(ctx, WLN_EINVAL, "too many points");
+  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec);
+
+  // Device layout of this call: work list | profiles | radii | partials | (host output)
+  Carve cv;
+  const size_t o_tiles = cv.take<Tile>(bt.tiles.size());
+  const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
+  const size_t o_rho = cv.take<double>(bt.rho.size());
+  const size_t upload = cv.off;
+  const size_t n_partial = static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * WLN_K;
+  const size_t o_part = cv.take<double>(n_partial);
+  Out out = plan_out(cv, group_sums, static_cast<size_t>(bt.n_points) * n_groups * WLN_K);
+  if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) return st;
+  if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
+  bind_out(out, ctx->scratch.ptr);
+
+  char* h = static_cast<char*>(ctx->pinned);
+  std::memcpy(h + o_tiles, bt.tiles.data(), bt.tiles.size() * sizeof(Tile));
+  std::memcpy(h + o_profs, bt.profs.data(), bt.profs.size() * sizeof(ProfileDev));
+  std::memcpy(h + o_rho, bt.rho.data(), bt.rho.size() * sizeof(double));
+  char* d = static_cast<char*>(ctx->scratch.ptr);
+  cudaError_t err = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "upload work list");
+
+  const int32_t lpg = ens->e.n_loops / n_groups;
+  int64_t launches = 0;
+  err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles), at<ProfileDev>(d, o_profs),
+                      at<double>(d, o_rho), n_groups, lpg, prec, at<double>(d, o_part),
+                      bt.n_points, ctx->d_flag, &launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+  err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
+                               n_groups, lpg, static_cast<double*>(out.dev));
+  ++launches;
+  ctx->launches += launches;
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "group reduction");
+  if (out.host) {
+    if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy group sums");
+    return check_flag(ctx);
+  }
+  return WLN_OK;
+}
+
+wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                         int32_t n_groups, int32_t loops_per_group, int32_t comp, double* mean,
+                         double* sem, double* jk_var, double* cov) {
+  if (!ctx || !group_sums || !mean || !sem) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_points < 1 || n_groups < 2 || loops_per_group < 1 || comp < 0 || comp >= WLN_K)
+    return fail(ctx, WLN_EINVAL, "bad jackknife sizes");
+  if (cov && static_cast<int64_t>(n_points) * n_points > (int64_t(1) << 33))
+    return fail(ctx, WLN_EINVAL, "covariance too large");
+  DeviceGuard guard(ctx->device);
+  const size_t nS = static_cast<size_t>(n_points) * n_groups * WLN_K;
+  const bool s_dev = is_device_ptr(group_sums);
+  Carve cv;
+  const size_t o_S = s_dev ? 0 : cv.take<double>(nS);
+  const size_t o_dev = cov ? cv.take<double>(static_cast<size_t>(n_groups) * n_points) : 0;
+  Out om = plan_out(cv, mean, n_points), os = plan_out(cv, sem, n_points);
+  Out oj = plan_out(cv, jk_var, n_points);
+  Out oc = plan_out(cv, cov, cov ? static_cast<size_t>(n_points) * n_points : 0);
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(om, ctx->scratch.ptr); bind_out(os, ctx->scratch.ptr);
+  bind_out(oj, ctx->scratch.ptr); bind_out(oc, ctx->scratch.ptr);
+  const double* S = group_sums;
+  cudaError_t err = cudaSuccess;
+  if (!s_dev) {
+    double* dS = at<double>(ctx->scratch.ptr, o_S);
+    err = cudaMemcpyAsync(dS, group_sums, nS * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    S = dS;
+  }
+  int64_t launches = 0;
+  if (err == cudaSuccess)
+    err = launch_jackknife(ctx->stream, S, n_points, n_groups, loops_per_group, comp,
+                           static_cast<double*>(om.dev), static_cast<double*>(os.dev),
+                           static_cast<double*>(oj.dev),
+                           cov ? at<double>(ctx->scratch.ptr, o_dev) : nullptr,
+                           static_cast<double*>(oc.dev), &launches);
+  ctx->launches += launches;
+  for (const Out* o : {&om, &os, &oj, &oc})
+    if (err == cudaSuccess) err = copy_back(*o, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "jackknife");
+  if (om.host || os.host || oj.host || oc.host || !s_dev) return check_flag(ctx);
+  return WLN_OK;
+}
+
+wln_status wln_loop_sem(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                        int32_t n_groups, int32_t n_loops, int32_t comp_sum, int32_t comp_sq,
+                        double* out) {
+  if (!ctx || !group_sums || !out) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_points < 1 || n_groups < 1 || n_loops < 2 || comp_sum < 0 || comp_sum >= WLN_K ||
+      comp_sq < 0 || comp_sq >= WLN_K)
+    return fail(ctx, WLN_EINVAL, "bad loop-SEM sizes");
+  DeviceGuard guard(ctx->device);
+  const size_t nS = static_cast<size_t>(n_points) * n_groups * WLN_K;
+  const bool s_dev = is_device_ptr(group_sums);
+  Carve cv;
+  const size_t o_S = s_dev ? 0 : cv.take<double>(nS);
+  Out o = plan_out(cv, out, n_points);
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(o, ctx->scratch.ptr);
+  const double* S = group_sums;
+  cudaError_t err = cudaSuccess;
+  if (!s_dev) {
+    double* dS = at<double>(ctx->scratch.ptr, o_S);
+    err = cudaMemcpyAsync(dS, group_sums, nS * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    S = dS;
+  }
+  if (err == cudaSuccess)
+    err = launch_loop_sem(ctx->stream, S, n_points, n_groups, n_loops, comp_sum, comp_sq,
+                          static_cast<double*>(o.dev));
+  ++ctx->launches;
+  if (err == cudaSuccess) err = copy_back(o, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "loop SEM");
+  if (o.host || !s_dev) return check_flag(ctx);
+  return WLN_OK;
+}
+
+wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles, int32_t n_profiles,
+                                const double* rho_cm, const int32_t* rho_off, const double* T,
+                                const int32_t* T_off, const double* group_sums, int32_t n_groups,
+                                int32_t loops_per_group, int32_t spinor, double* gamma_groups,
+                                double* gamma_mean_sem) {
+  if (!ctx || !group_sums || !gamma_mean_sem) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_groups < 2 || loops_per_group < 1) return fail(ctx, WLN_EINVAL, "bad group sizes");
+  wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
+  if (st != WLN_OK) return st;
+  std::vector<QuadProfile> qp(n_profiles);
+  int64_t base = 0;
+  for (int q = 0; q < n_profiles; ++q) {
+    const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
+    const double* r = rho_cm + rho_off[q];
+    const double* t = T + T_off[q];
+    QuadProfile& x = qp[q];
+    x.kind = profiles[q].kind;
+    x.n_rho = nr; x.n_T = nt; x.rho_base = rho_off[q]; x.T_base = T_off[q];
+    x.p0 = base;
+    x.h_rho = nr > 1 ? (r[nr - 1] - r[0]) / (nr - 1) : 0.0;
+    x.h_u = nt > 1 ? std::log(t[nt - 1] / t[0]) / (nt - 1) : 0.0;
+    for (int i = 1; i < nr; ++i)
+      if (std::fabs((r[i] - r[i - 1]) - x.h_rho) > 1e-9 * (std::fabs(x.h_rho) + std::fabs(r[i])))
+        return fail(ctx, WLN_EINVAL, "rho_cm must be evenly spaced");
+    for (int i = 1; i < nt; ++i)
+      if (std::fabs(std::log(t[i] / t[i - 1]) - x.h_u) > 1e-9 * (std::fabs(x.h_u) + 1.0))
+        return fail(ctx, WLN_EINVAL, "T must be geometrically spaced");
+    if (x.kind == WLN_PROFILE_FLUX_TUBE) {
+      x.l2 = profiles[q].lambda * profiles[q].lambda;
+      x.eB_scale = profiles[q].F * x.l2 / kPi;            // 2 calF lambda^2
+    } else {
+      x.l2 = 1.0;
+      x.eB_scale = profiles[q].B;
+    }
+    base += static_cast<int64_t>(nr) * nt;
+  }
+  DeviceGuard guard(ctx->device);
+  const size_t nS = static_cast<size_t>(base) * n_groups * WLN_K;
+  const bool s_dev = is_device_ptr(group_sums);
+  Carve cv;
+  const size_t o_qp = cv.take<QuadProfile>(qp.size());
+  const size_t o_r = cv.take<double>(rho_off[n_profiles]);
+  const size_t o_t = cv.take<double>(T_off[n_profiles]);
+  const size_t upload = cv.off;
+  const size_t o_S = s_dev ? 0 : cv.take<double>(nS);
+  const size_t o_gg = cv.take<double>(static_cast<size_t>(n_profiles) * n_groups);
+  Out og = plan_out(cv, gamma_groups, static_cast<size_t>(n_profiles) * n_groups);
+  Out om = plan_out(cv, gamma_mean_sem, static_cast<size_t>(n_profiles) * 2);
+  if ((st = ensure_scratch(ctx, cv.off + 256)) != WLN_OK) return st;
+  if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
+  bind_out(og, ctx->scratch.ptr);
+  bind_out(om, ctx->scratch.ptr);
+  char* h = static_cast<char*>(ctx->pinned);
+  std::memcpy(h + o_qp, qp.data(), qp.size() * sizeof(QuadProfile));
+  std::memcpy(h + o_r, rho_cm, rho_off[n_profiles] * sizeof(double));
+  std::memcpy(h + o_t, T, T_off[n_profiles] * sizeof(double));
+  char* d = static_cast<char*>(ctx->scratch.ptr);
+  cudaError_t err = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
+  const double* S = group_sums;
+  if (err == cudaSuccess && !s_dev) {
+    err = cudaMemcpyAsync(d + o_S, group_sums, nS * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    S = at<double>(d, o_S);
+  }
+  double* gg = gamma_groups ? static_cast<double*>(og.dev) : at<double>(d, o_gg);
+  int64_t launches = 0;
+  if (err == cudaSuccess)
+    err = launch_effective_action(ctx->stream, at<QuadProfile>(d, o_qp), n_profiles,
+                                  at<double>(d, o_r), at<double>(d, o_t), S, n_groups,
+                                  loops_per_group, spinor, gg, static_cast<double*>(om.dev),
+                                  &launches);
+  ctx->launches += launches;
+  if (err == cudaSuccess) err = copy_back(og, ctx->stream);
+  if (err == cudaSuccess) err = copy_back(om, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "effective action");
+  if (og.host || om.host || !s_dev) return check_flag(ctx);
+  return WLN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Unit-loop generation on the device (paper Sec. "Loop Generation").
+//
+// Each loop is a closed, centre-of-mass-centred polygon of N points whose
+// increments follow the discretised free action: Gaussian, variance 2/N per
+// component, conditioned on closing.  The increments come from
+// Philox-4x32-10 (Salmon et al., SC'11) through Box-Muller, with counter
+// (j, loop, 0, 0) and key (seed_lo, seed_hi), so any loop can be regenerated
+// on its own.  Arithmetic after the integer stream is in double precision;
+// points are stored as float in the blocked layout described in
+// wln_internal.cuh.
+#include "wln_internal.cuh"
+
+namespace wln {
+namespace {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// u in (0, 1): centre of the k-th of 2^32 cells (exact in double).
+__device__ __forceinline__ double uniform_open(uint32_t k) {
+  return (static_cast<double>(k) + 0.5) * 0x1p-32;
+}
+
+// Four increments xi_x[2j], xi_y[2j], xi_x[2j+1], xi_y[2j+1] of one loop.
+__device__ __forceinline__ void increments(uint64_t seed, uint32_t loop, uint32_t j,
+                                           double scale, double& x0, double& y0, double& x1,
+                                           double& y1) {
+  const uint4 u = philox4x32_10(make_uint4(j, loop, 0u, 0u), static_cast<uint32_t>(seed),
+                                static_cast<uint32_t>(seed >> 32));
+  double s, c;
+  const double ra = scale * sqrt(-2.0 * log(uniform_open(u.x)));
+  sincospi(2.0 * uniform_open(u.y), &s, &c);
+  x0 = ra * c;
+  y0 = ra * s;
+  const double rb = scale * sqrt(-2.0 * log(uniform_open(u.z)));
+  sincospi(2.0 * uniform_open(u.w), &s, &c);
+  x1 = rb * c;
+  y1 = rb * s;
+}
+
+__global__ void philox_stream_kernel(uint64_t seed, int64_t loop0, int32_t n_loops,
+                                     int32_t n_calls, uint4* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<int64_t>(n_loops) * n_calls) return;
+  const uint32_t loop = static_cast<uint32_t>(loop0 + i / n_calls);
+  const uint32_t j = static_cast<uint32_t>(i % n_calls);
+  out[i] = philox4x32_10(make_uint4(j, loop, 0u, 0u), static_cast<uint32_t>(seed),
+                         static_cast<uint32_t>(seed >> 32));
+}
+
+// One CTA per block of 32 loops: lane = loop, warp w = chunk w of the points.
+// Pass 1 sums the raw increments xi_k and k * xi_k per chunk; a scan over
+// the chunks gives each chunk's starting partial sum.  With mu = mean(xi),
+// the closed positions are p_k = S_k - k mu (S_k = sum_{j<k} xi_j) and their
+// mean is ((N-1)/2) sum xi / N - sum k xi / N - ... folded below.  Pass 2
+// regenerates the chunk's increments and writes y_k = p_k - mean(p).
+template <int WG>
+__global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int32_t ppl,
+                                                            float4* blocks, double* xy64,
+                                                            int32_t n_loops) {
+  __shared__ double part[WG][32][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t loop = blockIdx.x * 32u + lane;
+  const int M = ppl / WG;           // points per chunk (even)
+  const int k0 = w * M;
+  const double scale = sqrt(2.0 / ppl);
+
+  double sx = 0.0, sy = 0.0, wx = 0.0, wy = 0.0;
+  for (int k = k0; k < k0 + M; k += 2) {
+    double x0, y0, x1, y1;
+    increments(seed, loop, k >> 1, scale, x0, y0, x1, y1);
+    sx += x0; sy += y0;
+    wx += k * x0; wy += k * y0;
+    sx += x1; sy += y1;
+    wx += (k + 1) * x1; wy += (k + 1) * y1;
+  }
+  part[w][lane][0] = sx; part[w][lane][1] = sy;
+  part[w][lane][2] = wx; part[w][lane][3] = wy;
+  __syncthreads();
+  double tx = 0.0, ty = 0.0, twx = 0.0, twy = 0.0, px = 0.0, py = 0.0;
+  for (int v = 0; v < WG; ++v) {
+    if (v == w) { px = tx; py = ty; }
+    tx += part[v][lane][0]; ty += part[v][lane][1];
+    twx += part[v][lane][2]; twy += part[v][lane][3];
+  }
+  const double N = ppl;
+  const double mux = tx / N, muy = ty / N;
+  // mean_k p_k = (1/N) sum_k (S_k - k mu) = (1/N) sum_j xi_j (N-1-j) - mu (N-1)/2
+  const double cmx = ((N - 1.0) * tx - twx) / N - mux * (N - 1.0) * 0.5;
+  const double cmy = ((N - 1.0) * ty - twy) / N - muy * (N - 1.0) * 0.5;
+  double pxk = px - k0 * mux, pyk = py - k0 * muy;
+
+  float4* row = blocks + (static_cast<size_t>(blockIdx.x) * (ppl / 2) + k0 / 2) * 32 + lane;
+  double* ox = xy64 ? xy64 + static_cast<size_t>(loop) * 2 * ppl : nullptr;
+  const bool real = static_cast<int32_t>(loop) < n_loops;
+  for (int k = k0; k < k0 + M; k += 2) {
+    double x0, y0, x1, y1;
+    increments(seed, loop, k >> 1, scale, x0, y0, x1, y1);
+    const double ax = pxk - cmx, ay = pyk - cmy;
+    pxk += x0 - mux; pyk += y0 - muy;
+    const double bx = pxk - cmx, by = pyk - cmy;
+    pxk += x1 - mux; pyk += y1 - muy;
+    *row = make_float4(__double2float_rn(ax), __double2float_rn(ay), __double2float_rn(bx),
+                       __double2float_rn(by));
+    row += 32;
+    if (ox && real) {
+      ox[k] = ax; ox[k + 1] = bx;
+      ox[ppl + k] = ay; ox[ppl + k + 1] = by;
+    }
+  }
+}
+
+// float xy[l][2][N] -> blocks; padding lanes are zero.
+__global__ void pack_kernel(const float* xy, float4* blocks, int32_t n_loops, int32_t ppl,
+                            int32_t n_blocks) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t rows = ppl / 2;
+  if (i >= static_cast<int64_t>(n_blocks) * rows * 32) return;
+  const int lane = static_cast<int>(i & 31);
+  const int64_t r = (i >> 5) % rows;
+  const int64_t b = (i >> 5) / rows;
+  const int64_t loop = b * 32 + lane;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (loop < n_loops) {
+    const float* p = xy + loop * 2 * ppl;
+    v = make_float4(p[2 * r], p[ppl + 2 * r], p[2 * r + 1], p[ppl + 2 * r + 1]);
+  }
+  blocks[i] = v;
+}
+
+__global__ void unpack_kernel(const float4* blocks, float* xy, int32_t n_loops, int32_t ppl) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t rows = ppl / 2;
+  if (i >= static_cast<int64_t>(n_loops) * rows) return;
+  const int64_t loop = i / rows, r = i % rows;
+  const float4 v = blocks[((loop >> 5) * rows + r) * 32 + (loop & 31)];
+  float* p = xy + loop * 2 * ppl;
+  p[2 * r] = v.x; p[2 * r + 1] = v.z;
+  p[ppl + 2 * r] = v.y; p[ppl + 2 * r + 1] = v.w;
+}
+
+// Flags a loop with two cyclically consecutive equal points.
+__global__ void degenerate_kernel(const float4* blocks, int32_t n_loops, int32_t ppl,
+                                  int* flag) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t rows = ppl / 2;
+  if (i >= static_cast<int64_t>(n_loops) * rows) return;
+  const int64_t loop = i / rows, r = i % rows;
+  const float4* base = blocks + (loop >> 5) * rows * 32 + (loop & 31);
+  const float4 a = base[r * 32];
+  const float4 b = base[((r + 1) % rows) * 32];
+  const bool same01 = a.x == a.z && a.y == a.w;
+  const bool same12 = a.z == b.x && a.w == b.y;
+  if (same01 || same12) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
+                                 int32_t n_calls, uint32_t* out) {
+  const int64_t n = static_cast<int64_t>(n_loops) * n_calls;
+  if (n == 0) return cudaSuccess;
+  philox_stream_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      seed, loop0, n_loops, n_calls, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate) {
+  const int wg = e.ppl >= 16 ? 8 : e.ppl / 2;
+  switch (wg) {
+    case 8: gen_loops_kernel<8><<<e.n_blocks, 256, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    case 2: gen_loops_kernel<2><<<e.n_blocks, 64, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    case 4: gen_loops_kernel<4><<<e.n_blocks, 128, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
+  degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
+                                                                          e.ppl, d_degenerate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate) {
+  const int64_t n = static_cast<int64_t>(e.n_blocks) * (e.ppl / 2) * 32;
+  pack_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(xy, e.blocks, e.n_loops,
+                                                                   e.ppl, e.n_blocks);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t m = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
+  degenerate_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
+                                                                          e.ppl, d_degenerate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy) {
+  const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
+  unpack_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, xy, e.n_loops,
+                                                                     e.ppl);
+  return cudaGetLastError();
+}
+
+}  // namespace wln

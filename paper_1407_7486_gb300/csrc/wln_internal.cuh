@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units of libwln.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "wln.h"
+
+namespace wln {
+
+// Loops are stored in blocks of 32 (one loop per warp lane).  Within a block,
+// row i2 holds points 2*i2 and 2*i2+1 of each loop as one float4
+// (x0, y0, x1, y1); lane l of the block is loop 32*b + l.  A block is
+// therefore ppl/2 rows of 32 float4 (512 bytes per row), contiguous, so a
+// range of rows is one bulk (TMA) copy and a warp reads a row with one
+// conflict-free 16-byte load per lane.
+constexpr int kLanes = 32;
+
+// Device error flag values (bounded waits that ran out).
+constexpr int kErrTimeoutFull = 1;
+constexpr int kErrTimeoutEmpty = 2;
+
+struct Ensemble {
+  int32_t n_loops = 0;
+  int32_t ppl = 0;
+  int32_t n_blocks = 0;       // ceil(n_loops / 32)
+  float4* blocks = nullptr;   // [n_blocks][ppl/2][32]
+  double* xy64 = nullptr;     // optional [n_loops][2][ppl]
+};
+
+// Per-profile constants used by the Wilson kernels.
+struct ProfileDev {
+  int32_t kind;
+  int32_t pad;
+  double l2;          // lambda^2
+  double turns_per;   // flux tube: calF/(2 pi) = F/(4 pi^2), phase in turns per unit sum X*J1
+                      // constant field: B/(4 pi), turns per unit sum of X (twice the area)
+  double spin_per;    // flux tube: calF lambda^2 / N per unit T per unit sum of j2;
+                      // constant field: B (spin = B T)
+};
+
+// A tile: P consecutive radii of one profile at one proper time.
+struct Tile {
+  int32_t profile;
+  int32_t n_valid;    // radii in this tile (1..P)
+  int32_t rho0;       // index of the first radius in the flattened rho array
+  int32_t p0;         // point index of the first radius
+  double T;
+};
+
+// Geometry of one Wilson launch.
+struct WilsonPlan {
+  int P;              // points (radii) per lane
+  int warps;          // warps (tiles) per CTA
+  int rows;           // float4 rows per staged chunk
+  int stages;         // staged chunks in flight
+  int chain;          // 32-loop blocks per work item
+  int n_tiles;
+  int n_tile_groups;  // ceil(n_tiles / warps)
+  int n_chains;       // ceil(n_blocks / chain)
+  int64_t n_items;    // n_chains * n_tile_groups
+  int grid;           // persistent CTAs
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace wln
+
+struct wln_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int num_sms = 0;
+  int64_t launches = 0;
+  int* d_flag = nullptr;          // device error flag
+  wln::Scratch scratch;           // partial sums, work lists (device)
+  void* pinned = nullptr;         // host staging for work lists
+  size_t pinned_bytes = 0;
+  cudaEvent_t staging_done = nullptr;
+  // tuning overrides (0 = automatic)
+  int tune_P = 0, tune_warps = 0, tune_rows = 0, tune_stages = 0, tune_chain = 0;
+};
+
+struct wln_ensemble {
+  wln::Ensemble e;
+  int device = 0;
+};
+
+namespace wln {
+
+// Status helpers (wln_api.cu).
+wln_status fail(wln_ctx* ctx, wln_status st, const std::string& msg);
+wln_status cuda_fail(wln_ctx* ctx, cudaError_t err, const char* what);
+bool is_device_ptr(const void* p);
+wln_status ensure_scratch(wln_ctx* ctx, size_t bytes);
+wln_status ensure_pinned(wln_ctx* ctx, size_t bytes);
+
+// Generation (wln_gen.cu).
+cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
+                                 int32_t n_calls, uint32_t* out);
+cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate);
+cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
+cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
+
+// Wilson loops (wln_wilson.cu).
+WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec);
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec);
+cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                          const Tile* tiles, const ProfileDev* profs, const double* rho,
+                          int32_t n_groups, int32_t loops_per_group, wln_prec prec,
+                          double* partial, int64_t n_points, int* d_flag, int64_t* launches);
+cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                                   const double* partial, int64_t n_points, int32_t n_groups,
+                                   int32_t loops_per_group, double* group_sums);
+
+// Statistics (wln_stats.cu).
+cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
+                             int32_t lpg, int32_t comp, double* mean, double* sem,
+                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches);
+cudaError_t launch_loop_sem(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
+                            int32_t n_loops, int32_t comp_sum, int32_t comp_sq, double* out);
+
+struct QuadProfile {
+  int32_t kind;
+  int32_t n_rho, n_T;
+  int32_t rho_base;  // first radius in the flattened radii
+  int32_t T_base;    // first proper time in the flattened times
+  int32_t pad;
+  int64_t p0;        // first point of the profile
+  double h_rho;      // radius spacing
+  double h_u;        // spacing of ln T
+  double eB_scale;   // flux tube: 2 calF lambda^2 = F lambda^2 / pi; constant: B
+  double l2;
+};
+cudaError_t launch_effective_action(cudaStream_t s, const QuadProfile* qp, int32_t n_profiles,
+                                    const double* rho, const double* T, const double* S,
+                                    int32_t G, int32_t lpg, int32_t spinor, double* gamma_groups,
+                                    double* gamma_mean_sem, int64_t* launches);
+
+}  // namespace wln

@@ -1,0 +1,210 @@
+// Group statistics and effective-action quadrature on the device, in double
+// precision (paper Sec. "Grouping Worldlines"; Eq. cylEA; Sec. "Computing an
+// Effective Action").  Every sum runs in a fixed order, so results do not
+// depend on scheduling.
+#include "wln_internal.cuh"
+
+namespace wln {
+namespace {
+
+constexpr int kComps = WLN_K;
+
+// Group means m_g = S_g / loops_per_group, their mean, the group standard
+// error and the delete-one-group jackknife variance; the deviations
+// m_g - mean go to dev[g][p] for the covariance.
+__global__ void jackknife_kernel(const double* S, int32_t n_points, int32_t G, int32_t lpg,
+                                 int32_t comp, double* mean, double* sem, double* jk_var,
+                                 double* dev) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n_points) return;
+  const double* s = S + p * G * kComps + comp;
+  const double inv = 1.0 / lpg;
+  double m = 0.0;
+  for (int g = 0; g < G; ++g) m += s[g * kComps] * inv;
+  m /= G;
+  double ss = 0.0, jj = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double mg = s[g * kComps] * inv;
+    const double d = mg - m;
+    ss += d * d;
+    const double loo = (G * m - mg) / (G - 1);
+    jj += (loo - m) * (loo - m);
+    if (dev) dev[static_cast<int64_t>(g) * n_points + p] = d;
+  }
+  mean[p] = m;
+  sem[p] = sqrt(ss / (static_cast<double>(G) * (G - 1)));
+  if (jk_var) jk_var[p] = (G - 1.0) / G * jj;
+}
+
+// cov[p][q] = sum_g dev[g][p] dev[g][q] / (G (G - 1)).  64x64 tiles, only
+// tiles on or above the diagonal are computed; the mirror image is written
+// through a shared-memory transpose so both stores are coalesced.
+constexpr int kTile = 64, kKc = 16;
+__global__ void __launch_bounds__(256) covariance_kernel(const double* dev, int32_t n_points,
+                                                         int32_t G, double* cov) {
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  __shared__ double a[kKc][kTile], b[kKc][kTile];
+  __shared__ double tr[kTile][kTile + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int g0 = 0; g0 < G; g0 += kKc) {
+    for (int i = threadIdx.x; i < kKc * kTile; i += 256) {
+      const int gg = g0 + i / kTile, c = i % kTile;
+      const int pa = ti * kTile + c, pb = tj * kTile + c;
+      a[i / kTile][c] = (gg < G && pa < n_points) ? dev[static_cast<int64_t>(gg) * n_points + pa] : 0.0;
+      b[i / kTile][c] = (gg < G && pb < n_points) ? dev[static_cast<int64_t>(gg) * n_points + pb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKc; ++kk) {
+      double ra[4], rb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) ra[r] = a[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rb[c] = b[kk][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(ra[r], rb[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  const double scale = 1.0 / (static_cast<double>(G) * (G - 1));
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int p = ti * kTile + ty * 4 + r;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = tj * kTile + tx * 4 + c;
+      acc[r][c] *= scale;
+      if (p < n_points && q < n_points) cov[static_cast<int64_t>(p) * n_points + q] = acc[r][c];
+      tr[ty * 4 + r][tx * 4 + c] = acc[r][c];
+    }
+  }
+  if (ti == tj) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTile * kTile; i += 256) {
+    const int row = i / kTile, col = i % kTile;  // output row in tile tj, column in tile ti
+    const int p = tj * kTile + row, q = ti * kTile + col;
+    if (p < n_points && q < n_points) cov[static_cast<int64_t>(p) * n_points + q] = tr[col][row];
+  }
+}
+
+__global__ void loop_sem_kernel(const double* S, int32_t n_points, int32_t G, int32_t n_loops,
+                                int32_t cs, int32_t cq, double* out) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n_points) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int g = 0; g < G; ++g) {
+    s1 += S[(p * G + g) * kComps + cs];
+    s2 += S[(p * G + g) * kComps + cq];
+  }
+  const double ss = s2 - s1 * s1 / n_loops;
+  out[p] = sqrt((ss > 0.0 ? ss : 0.0) / (static_cast<double>(n_loops) * (n_loops - 1)));
+}
+
+// Composite Simpson weight of point j of n evenly spaced points (spacing h);
+// an even n ends with a 3/8 panel over the last three intervals.
+__device__ double simpson_weight(int j, int n, double h) {
+  if (n == 1) return 0.0;
+  if (n == 2) return 0.5 * h;
+  const int m = (n & 1) ? n : n - 3;
+  double w = 0.0;
+  if (m >= 3 && j < m) w += (j == 0 || j == m - 1) ? h / 3.0 : ((j & 1) ? 4.0 * h / 3.0 : 2.0 * h / 3.0);
+  if (!(n & 1) && j >= n - 4) {
+    const int t = j - (n - 4);
+    w += 3.0 * h / 8.0 * ((t == 0 || t == 3) ? 1.0 : 3.0);
+  }
+  return w;
+}
+
+// One CTA per (profile, group): Gamma_g = (1/4 pi) sum_ab w_a rho_a w_b T_b
+// e^{-T_b}/T_b^3 (m_g(a, b) - c (eB(rho_a) T_b)^2), m_g the group mean of W - 1.
+__global__ void __launch_bounds__(256) effective_action_kernel(
+    const QuadProfile* qp, const double* rho, const double* T, const double* S, int32_t G,
+    int32_t lpg, int32_t spinor, double* gamma_groups) {
+  const int q = blockIdx.y, g = blockIdx.x;
+  const QuadProfile pr = qp[q];
+  const int comp = spinor ? WLN_C_FERM : WLN_C_SCAL;
+  const double c_ct = spinor ? 1.0 / 3.0 : -1.0 / 6.0;
+  const int n = pr.n_rho * pr.n_T;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int it = i / pr.n_rho, ir = i % pr.n_rho;
+    const double r = rho[pr.rho_base + ir], t = T[pr.T_base + it];
+    const double wr = simpson_weight(ir, pr.n_rho, pr.h_rho) * r;
+    const double wt = simpson_weight(it, pr.n_T, pr.h_u) * t;
+    double eB;
+    if (pr.kind == WLN_PROFILE_CONST_B) {
+      eB = pr.eB_scale;
+    } else {
+      const double q2 = pr.l2 + r * r;
+      eB = pr.eB_scale / (q2 * q2);
+    }
+    const double m = S[((pr.p0 + i) * G + g) * kComps + comp] / lpg;
+    const double et = eB * t;
+    acc += wr * wt * exp(-t) / (t * t * t) * (m - c_ct * et * et);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gamma_groups[q * G + g] = red[0] / (4.0 * 3.14159265358979323846);
+}
+
+__global__ void group_mean_sem_kernel(const double* x, int32_t n_rows, int32_t G, double* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_rows) return;
+  double m = 0.0;
+  for (int g = 0; g < G; ++g) m += x[q * G + g];
+  m /= G;
+  double ss = 0.0;
+  for (int g = 0; g < G; ++g) ss += (x[q * G + g] - m) * (x[q * G + g] - m);
+  out[2 * q] = m;
+  out[2 * q + 1] = sqrt(ss / (static_cast<double>(G) * (G - 1)));
+}
+
+}  // namespace
+
+cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
+                             int32_t lpg, int32_t comp, double* mean, double* sem,
+                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches) {
+  const unsigned blocks = static_cast<unsigned>((n_points + 255) / 256);
+  jackknife_kernel<<<blocks, 256, 0, s>>>(S, n_points, G, lpg, comp, mean, sem, jk_var,
+                                          cov ? dev_scratch : nullptr);
+  ++*launches;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || !cov) return err;
+  const unsigned nt = static_cast<unsigned>((n_points + kTile - 1) / kTile);
+  covariance_kernel<<<dim3(nt, nt), 256, 0, s>>>(dev_scratch, n_points, G, cov);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_sem(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
+                            int32_t n_loops, int32_t comp_sum, int32_t comp_sq, double* out) {
+  loop_sem_kernel<<<static_cast<unsigned>((n_points + 255) / 256), 256, 0, s>>>(
+      S, n_points, G, n_loops, comp_sum, comp_sq, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_effective_action(cudaStream_t s, const QuadProfile* qp, int32_t n_profiles,
+                                    const double* rho, const double* T, const double* S,
+                                    int32_t G, int32_t lpg, int32_t spinor, double* gamma_groups,
+                                    double* gamma_mean_sem, int64_t* launches) {
+  effective_action_kernel<<<dim3(G, n_profiles), 256, 0, s>>>(qp, rho, T, S, G, lpg, spinor,
+                                                              gamma_groups);
+  ++*launches;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  group_mean_sem_kernel<<<(n_profiles + 127) / 128, 128, 0, s>>>(gamma_groups, n_profiles, G,
+                                                                 gamma_mean_sem);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace wln

@@ -1,0 +1,673 @@
+// Wilson-loop kernel: for every (loop, point) the phase e * closed line
+// integral of A and the spin integral e int B dtau of the scaled, shifted loop
+// (paper Sec. "Wilson Loop", Eqs. rhoi-Ci; Sec. "Fermion Part", Eq.
+// Wfermfpl), then W and its group sums (Sec. "Grouping Worldlines").
+//
+// Segment k of a loop runs from r_k to r_{k+1}, r = (rho_cm, 0) + sqrt(T) y.
+// With d = r_{k+1} - r_k, Q(t) = lambda^2 + |r + t d|^2 = C t^2 + 2 B t + Q0:
+//   C = |d|^2, B = r.d, X = r x d, D = lambda^2 C + X^2 (the discriminant,
+//   by the Lagrange identity |r|^2 |d|^2 - (r.d)^2 = X^2),
+//   int_0^1 dt/Q   = theta / sqrt(D),  theta = atan2(C sqrt(D), D + B (B + C)),
+//   int_0^1 dt/Q^2 = [(C + B)/Q1 - B/Q0 + C int dt/Q] / (2 D), where
+//   (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1) since Q1 = Q0 + 2B + C.
+// The flux tube f = rho^2/(lambda^2 + rho^2) has f/rho^2 = 1/Q, so the phase
+// of the segment is calF X int dt/Q, and e B = 2 calF lambda^2 / Q^2, so the
+// segment's spin integral is (T/N) 2 calF lambda^2 int dt/Q^2.  Both are
+// exact along the straight segment.  A constant field B gives phase B * area
+// (half the sum of X) and spin B T.
+//
+// Work decomposition (GB300): a warp owns P radii at one T ("tile") and its
+// 32 lanes are 32 loops (one "block" of the blocked ensemble).  A CTA of
+// `warps` warps shares each staged block: TMA bulk copies bring chunks of
+// the block's rows into a shared-memory ring guarded by mbarriers, and every
+// warp walks them for its own tile, so each staged byte is used by
+// warps * P points.  A work item is (chain of consecutive blocks, group of
+// tiles); persistent CTAs take items round-robin so concurrent CTAs share a
+// chain in L2.  W terms are reduced over lanes (and blocks) in FP64 in a
+// fixed order into per-(chain, group) partials; a second kernel sums the
+// partials of each group in chain order.
+#include <cfloat>
+
+#include "wln_internal.cuh"
+
+namespace wln {
+namespace {
+
+constexpr int kComps = WLN_K;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of wall time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ------------------------------------------------------ arithmetic flavours
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+struct F32Comp {
+  using F = float;
+  static constexpr bool kCompensated = true;
+  __device__ static float rcp(float x) { return rcp_approx(x); }
+  __device__ static float rsq(float x) { return rsqrtf(x); }
+  __device__ static float at2(float y, float x) { return atan2f(y, x); }
+};
+struct F32Naive {
+  using F = float;
+  static constexpr bool kCompensated = false;
+  __device__ static float rcp(float x) { return rcp_approx(x); }
+  __device__ static float rsq(float x) { return rsqrtf(x); }
+  __device__ static float at2(float y, float x) { return atan2f(y, x); }
+};
+struct F64 {
+  using F = double;
+  static constexpr bool kCompensated = false;
+  __device__ static double rcp(double x) { return 1.0 / x; }
+  __device__ static double rsq(double x) { return rsqrt(x); }
+  __device__ static double at2(double y, double x) { return atan2(y, x); }
+};
+
+template <class F, bool kComp>
+struct Acc {
+  F s, c;  // running sum and (compensated) the rounding error already folded in
+  __device__ void zero() { s = F(0); c = F(0); }
+  __device__ void add(F x) {
+    if (kComp) {  // Kahan: c holds the amount by which s exceeds the true sum
+      const F y = x - c;
+      const F t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ double value() const {
+    return kComp ? static_cast<double>(s) - static_cast<double>(c) : static_cast<double>(s);
+  }
+};
+
+// ----------------------------------------------------------- kernel params
+struct KParams {
+  const float4* blocks;
+  int32_t n_blocks, ppl, n_loops;
+  const Tile* tiles;
+  int32_t n_tiles;
+  const ProfileDev* profs;
+  const double* rho;
+  int32_t lpg, G;
+  double* partial;       // [(n_chains + G)][n_points][K]
+  int64_t n_points;
+  int32_t rows;          // float4 rows per chunk
+  int32_t stages;
+  int32_t chain;
+  int32_t n_tile_groups, n_chains;
+  int64_t n_items;
+  int* flag;
+};
+
+// Per-lane walk of one loop for the P radii of a tile (flux tube).
+template <class A, int P>
+struct Walk {
+  using F = typename A::F;
+  F s, l2;           // sqrt(T), lambda^2
+  F rho[P];
+  // state at the current point
+  F ux, uy;          // unit-loop point
+  F ry;              // scaled y (shared by the radii)
+  F rx[P];           // shifted, scaled x
+  F rq[P];           // 1/Q at the current point
+  Acc<F, A::kCompensated> ph[P], sp[P];
+
+  __device__ __forceinline__ void start(F x0, F y0) {
+    ux = x0; uy = y0;
+    ry = s * y0;
+    const F e0 = fma(ry, ry, l2);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      rx[p] = fma(s, x0, rho[p]);
+      rq[p] = A::rcp(fma(rx[p], rx[p], e0));
+      ph[p].zero();
+      sp[p].zero();
+    }
+  }
+
+  // Advance along the straight segment to unit-loop point (x1, y1).
+  __device__ __forceinline__ void step(F x1, F y1) {
+    const F dx = s * (x1 - ux), dy = s * (y1 - uy);
+    const F C = fma(dx, dx, dy * dy);
+    const F l2C = l2 * C;
+    const F ry1 = s * y1;
+    const F e1 = fma(ry1, ry1, l2);
+    const F rydy = ry * dy, rydx = ry * dx;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const F rx1 = fma(s, x1, rho[p]);
+      const F rq1 = A::rcp(fma(rx1, rx1, e1));
+      const F B = fma(rx[p], dx, rydy);
+      const F X = fma(rx[p], dy, -rydx);
+      const F D = fma(X, X, l2C);
+      const F rsD = A::rsq(D);
+      const F BC = B + C;
+      const F theta = A::at2(C * (D * rsD), fma(B, BC, D));
+      const F J1 = theta * rsD;
+      ph[p].add(X * J1);
+      // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
+      // cancellation between the two quotients.
+      const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
+      sp[p].add(br * (rsD * rsD));
+      rx[p] = rx1;
+      rq[p] = rq1;
+    }
+    ux = x1; uy = y1; ry = ry1;
+  }
+
+  // Raw phase and spin sums of radius p (sum and compensation terms).
+  __device__ __forceinline__ void raw(int p, double& ps, double& pc, double& ss,
+                                      double& sc) const {
+    ps = ph[p].s; pc = ph[p].c; ss = sp[p].s; sc = sp[p].c;
+  }
+};
+
+// Constant field: only the area is needed, half the sum of X = r x d.
+template <class A, int P>
+struct WalkB {
+  using F = typename A::F;
+  F s, l2;
+  F rho[P];
+  F ux, uy, ry;
+  F rx[P];
+  Acc<F, A::kCompensated> ph[P];
+  __device__ __forceinline__ void start(F x0, F y0) {
+    ux = x0; uy = y0; ry = s * y0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) { rx[p] = fma(s, x0, rho[p]); ph[p].zero(); }
+  }
+  __device__ __forceinline__ void step(F x1, F y1) {
+    const F dx = s * (x1 - ux), dy = s * (y1 - uy);
+    const F rydx = ry * dx;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      ph[p].add(fma(rx[p], dy, -rydx));
+      rx[p] = fma(s, x1, rho[p]);
+    }
+    ux = x1; uy = y1; ry = s * y1;
+  }
+  // The spin integral of a constant field is B T: a unit "sum" times B T.
+  __device__ __forceinline__ void raw(int p, double& ps, double& pc, double& ss,
+                                      double& sc) const {
+    ps = ph[p].s; pc = ph[p].c; ss = 1.0; sc = 0.0;
+  }
+};
+
+// Split of a double into two floats (hi + lo) for double-float products.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 split(double x) {
+  const float h = static_cast<float>(x);
+  return F2{h, static_cast<float>(x - static_cast<double>(h))};
+}
+
+// (s - c) * k for a compensated float sum (s, c) and k = k.hi + k.lo, as
+// hi + lo with hi = fl(s k.hi) and lo the rounding error plus the small
+// terms: accurate to a few units in the last place of the double result.
+__device__ __forceinline__ F2 scaled(float s, float c, F2 k) {
+  const float hi = s * k.hi;
+  const float e = fmaf(s, k.hi, -hi);
+  return F2{hi, e + fmaf(s, k.lo, -c * k.hi)};
+}
+
+// cosh(x) - 1 = 2 sinh^2(x/2): no cancellation at small x, +inf (not NaN)
+// once cosh(x) leaves the double range.
+__device__ __forceinline__ double cosh_m1_f64(double x) {
+  const double h = sinh(0.5 * x);
+  return 2.0 * h * h;
+}
+
+// The five per-loop terms (see WLN_C_*).
+//  FP64: phase reduced in turns in double, everything in double.
+//  FP32 compensated: phase and spin arrive as compensated sums times a
+//   double scale, formed as double-float; the fractional turn is exact to
+//   float rounding, so sin/cos are taken on |frac| <= 1/2 with sinpi/cospi.
+//   cosh(spin) - 1 uses expm1f plus the first-order term of the low part;
+//   spins above 80 (cosh beyond float range) go through double.
+//  FP32 naive: plain float phase in radians, cosf and coshf.
+template <class A>
+__device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp_s, double sp_c,
+                                             F2 tp, F2 st, double tp_d, double st_d,
+                                             double* w) {
+  if constexpr (sizeof(typename A::F) == 8) {
+    const double turns = ph_s * tp_d;
+    const double fr = turns - rint(turns);
+    const double h = sinpi(fr);
+    const double scal_m1 = -2.0 * h * h;
+    double sn, cs;
+    sincospi(2.0 * fr, &sn, &cs);
+    const double ferm_m1 = cs * cosh_m1_f64(sp_s * st_d) + scal_m1;
+    w[0] = scal_m1; w[1] = ferm_m1; w[2] = sn;
+    w[3] = scal_m1 * scal_m1; w[4] = ferm_m1 * ferm_m1;
+  } else if constexpr (A::kCompensated) {
+    const F2 t = scaled(static_cast<float>(ph_s), static_cast<float>(ph_c), tp);
+    const float fr = (t.hi - rintf(t.hi)) + t.lo;
+    const float h = sinpif(fr);
+    const float scal_m1 = -2.0f * h * h;
+    float sn, cs;
+    sincospif(2.0f * fr, &sn, &cs);
+    const F2 sv = scaled(static_cast<float>(sp_s), static_cast<float>(sp_c), st);
+    double ferm_m1;
+    if (sv.hi < 80.0f) {
+      const float em1 = expm1f(sv.hi);
+      const float inv = 1.0f / (em1 + 1.0f);
+      const float sinh_v = 0.5f * (em1 + em1 * inv);
+      const float cm1 = fmaf(sinh_v, sv.lo, 0.5f * em1 * (em1 * inv));
+      ferm_m1 = static_cast<double>(fmaf(cs, cm1, scal_m1));
+    } else {
+      ferm_m1 = static_cast<double>(cs) *
+                    cosh_m1_f64(static_cast<double>(sv.hi) + static_cast<double>(sv.lo)) +
+                static_cast<double>(scal_m1);
+    }
+    const double sm = scal_m1;
+    w[0] = sm; w[1] = ferm_m1; w[2] = sn;
+    w[3] = sm * sm; w[4] = ferm_m1 * ferm_m1;
+  } else {
+    const float ph = static_cast<float>(ph_s) * static_cast<float>(6.283185307179586 * tp_d);
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    const float scal_m1 = cs - 1.0f;
+    const float ferm_m1 = cs * coshf(static_cast<float>(sp_s) * static_cast<float>(st_d)) - 1.0f;
+    w[0] = scal_m1; w[1] = ferm_m1; w[2] = sn;
+    w[3] = static_cast<double>(scal_m1) * scal_m1;
+    w[4] = static_cast<double>(ferm_m1) * ferm_m1;
+  }
+}
+
+// Shared pipeline state of a CTA: a ring of staged chunks with full/empty
+// mbarriers; thread 0 also refills it.
+struct Pipe {
+  float4* ring;
+  uint64_t* full;
+  uint64_t* empty;
+  int stages, chunk_rows, chunks_per_block, rows_per_block;
+  uint32_t chunk_bytes;
+  int32_t kc = 0, issued = 0, total = 0;
+  int32_t prod_item = 0;
+  int prod_blk = 0, prod_chunk = 0;
+};
+
+__device__ __forceinline__ int blocks_in_item(const KParams& k, int64_t item) {
+  const int c = static_cast<int>(item / k.n_tile_groups);
+  const int b0 = c * k.chain;
+  return min(b0 + k.chain, k.n_blocks) - b0;
+}
+
+__device__ __forceinline__ void issue_next(const KParams& k, Pipe& pp, int slot) {
+  const int c = static_cast<int>(pp.prod_item / k.n_tile_groups);
+  const int b = c * k.chain + pp.prod_blk;
+  const float4* src = k.blocks + (static_cast<size_t>(b) * pp.rows_per_block +
+                                  static_cast<size_t>(pp.prod_chunk) * pp.chunk_rows) * 32;
+  mbar_arrive_expect_tx(&pp.full[slot], pp.chunk_bytes);
+  bulk_load(pp.ring + static_cast<size_t>(slot) * pp.chunk_rows * 32, src, pp.chunk_bytes,
+            &pp.full[slot]);
+  ++pp.issued;
+  if (++pp.prod_chunk == pp.chunks_per_block) {
+    pp.prod_chunk = 0;
+    if (++pp.prod_blk == blocks_in_item(k, pp.prod_item)) {
+      pp.prod_blk = 0;
+      pp.prod_item += gridDim.x;
+    }
+  }
+}
+
+// One work item for one warp: its tile against every loop of the chain.
+// Per-lane W terms are added into the warp's shared-memory accumulators
+// acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
+// flush sums each row over the lanes in lane order and writes the partial
+// of (chain, group).
+template <class A, int P, class WalkT>
+__device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const Tile& tile,
+                         const ProfileDev& prof, bool active, volatile int* abort_flag,
+                         int lane) {
+  using F = typename A::F;
+  constexpr int V = P * kComps;
+  WalkT wk;
+  wk.s = static_cast<F>(sqrt(tile.T));
+  wk.l2 = static_cast<F>(prof.l2);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int i = p < tile.n_valid ? p : tile.n_valid - 1;
+    wk.rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
+  }
+  const double st_d = prof.spin_per * tile.T;
+  const F2 tp = split(prof.turns_per), st = split(st_d);
+  const int b0 = c * k.chain;
+  const int b1 = min(b0 + k.chain, k.n_blocks);
+  int g_cur = (b0 * 32) / k.lpg;
+
+  auto flush = [&](int g) {
+    __syncwarp();
+    if (active) {
+      double* dst = k.partial + (static_cast<size_t>(c + g) * k.n_points + tile.p0) * kComps;
+      for (int j = lane; j < V; j += 32) {
+        double sum = 0.0;
+        const double* row = acc + j * 33;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) sum += row[l];
+        if (j / kComps < tile.n_valid) dst[j] = sum;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < V; ++j) acc[j * 33 + lane] = 0.0;
+    __syncwarp();
+  };
+
+  for (int b = b0; b < b1; ++b) {
+    const int loop = b * 32 + lane;
+    const bool valid = loop < k.n_loops;
+    float fx = 0.f, fy = 0.f;  // the loop's first point, for the closing segment
+    for (int ch = 0; ch < pp.chunks_per_block; ++ch) {
+      const int slot = static_cast<int>(pp.kc % pp.stages);
+      const uint32_t parity = static_cast<uint32_t>((pp.kc / pp.stages) & 1);
+      if (!mbar_wait(&pp.full[slot], parity)) {
+        atomicExch(k.flag, kErrTimeoutFull);
+        *abort_flag = 1;
+        return false;
+      }
+      const float4* rowp = pp.ring + static_cast<size_t>(slot) * pp.chunk_rows * 32 + lane;
+      if (active) {
+        int r = 0;
+        if (ch == 0) {
+          const float4 v = rowp[0];
+          fx = v.x; fy = v.y;
+          wk.start(v.x, v.y);
+          wk.step(v.z, v.w);
+          r = 1;
+        }
+        for (; r < pp.chunk_rows; ++r) {
+          const float4 v = rowp[r * 32];
+          wk.step(v.x, v.y);
+          wk.step(v.z, v.w);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pp.empty[slot]);
+      if (threadIdx.x == 0 && pp.issued < pp.total) {
+        // The slot just released is the next one to refill.
+        if (!mbar_wait(&pp.empty[slot], parity)) {
+          atomicExch(k.flag, kErrTimeoutEmpty);
+          *abort_flag = 1;
+        } else {
+          issue_next(k, pp, slot);
+        }
+      }
+      ++pp.kc;
+      if (*abort_flag) return false;
+    }
+    if (!active) continue;
+    wk.step(fx, fy);  // closing segment r_{N-1} -> r_0
+    const int g_lane = valid ? loop / k.lpg : -1;
+    const int g_lo = (b * 32) / k.lpg;
+    const int g_hi = min(b * 32 + 31, k.n_loops - 1) / k.lpg;
+    for (int g = g_lo; g <= g_hi; ++g) {
+      if (g != g_cur) { flush(g_cur); g_cur = g; }
+      const bool mine = g_lane == g;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        double ps, pc, ss, sc, w[kComps];
+        wk.raw(p, ps, pc, ss, sc);
+        wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, w);
+#pragma unroll
+        for (int q = 0; q < kComps; ++q)
+          if (mine) acc[(p * kComps + q) * 33 + lane] += w[q];
+      }
+    }
+  }
+  flush(g_cur);
+  return true;
+}
+
+template <class A, int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(const KParams k) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int abort_flag;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Pipe pp;
+  pp.rows_per_block = k.ppl / 2;
+  pp.chunk_rows = k.rows < pp.rows_per_block ? k.rows : pp.rows_per_block;
+  pp.chunks_per_block = pp.rows_per_block / pp.chunk_rows;
+  pp.chunk_bytes = static_cast<uint32_t>(pp.chunk_rows) * 512u;
+  pp.stages = k.stages;
+  pp.ring = reinterpret_cast<float4*>(smem);
+  const size_t ring_bytes = static_cast<size_t>(k.stages) * pp.chunk_rows * 512;
+  double* acc = reinterpret_cast<double*>(smem + ring_bytes) + warp * (P * kComps * 33);
+  pp.full = reinterpret_cast<uint64_t*>(smem + ring_bytes + WARPS * P * kComps * 33 * sizeof(double));
+  pp.empty = pp.full + k.stages;
+  for (int j = 0; j < P * kComps; ++j) acc[j * 33 + lane] = 0.0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < k.stages; ++s) {
+      mbar_init(&pp.full[s], 1);
+      mbar_init(&pp.empty[s], WARPS);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  for (int64_t it = blockIdx.x; it < k.n_items; it += gridDim.x)
+    pp.total += blocks_in_item(k, it) * pp.chunks_per_block;
+  pp.prod_item = blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < k.stages && pp.issued < pp.total; ++s) issue_next(k, pp, s);
+  }
+
+  bool ok = true;
+  for (int64_t item = blockIdx.x; item < k.n_items && ok; item += gridDim.x) {
+    const int c = static_cast<int>(item / k.n_tile_groups);
+    const int tg = static_cast<int>(item % k.n_tile_groups);
+    const int t = tg * WARPS + warp;
+    const bool active = t < k.n_tiles;
+    const Tile tile = k.tiles[active ? t : 0];
+    const ProfileDev prof = k.profs[tile.profile];
+    if (prof.kind == WLN_PROFILE_CONST_B)
+      ok = run_item<A, P, WalkB<A, P>>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+    else
+      ok = run_item<A, P, Walk<A, P>>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+  }
+
+  if (!ok && threadIdx.x == 0) {
+    // Let copies already in flight land before the CTA's shared memory goes away.
+    for (int32_t q = pp.kc; q < pp.issued; ++q)
+      (void)mbar_wait(&pp.full[q % pp.stages], static_cast<uint32_t>((q / pp.stages) & 1));
+  }
+}
+
+// Sum the partials of each group over its chains, in chain order.
+__global__ void reduce_partials_kernel(const double* partial, int64_t n_points, int32_t G,
+                                       int32_t lpg, int32_t chain_loops, double* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n_points * G * kComps) return;
+  const int q = static_cast<int>(i % kComps);
+  const int g = static_cast<int>((i / kComps) % G);
+  const int64_t p = i / (static_cast<int64_t>(kComps) * G);
+  const int c_lo = static_cast<int>((static_cast<int64_t>(g) * lpg) / chain_loops);
+  const int c_hi = static_cast<int>((static_cast<int64_t>(g + 1) * lpg - 1) / chain_loops);
+  double s = 0.0;
+  for (int c = c_lo; c <= c_hi; ++c)
+    s += partial[(static_cast<size_t>(c + g) * n_points + p) * kComps + q];
+  out[i] = s;
+}
+
+template <class A, int P, int WARPS>
+cudaError_t launch_t(cudaStream_t s, const KParams& kp, int grid, size_t smem) {
+  auto kern = wilson_kernel<A, P, WARPS>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  kern<<<grid, WARPS * 32, smem, s>>>(kp);
+  return cudaGetLastError();
+}
+
+template <class A, int P, int WARPS>
+int occupancy(size_t smem) {
+  int n = 0;
+  auto kern = wilson_kernel<A, P, WARPS>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, WARPS * 32, smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+size_t smem_bytes(const WilsonPlan& p, int ppl) {
+  const int chunk_rows = p.rows < ppl / 2 ? p.rows : ppl / 2;
+  return static_cast<size_t>(p.stages) * chunk_rows * 512 +
+         static_cast<size_t>(p.warps) * p.P * kComps * 33 * sizeof(double) +
+         2 * p.stages * sizeof(uint64_t);
+}
+
+}  // namespace
+
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec) {
+  if (ctx->tune_P) return ctx->tune_P;
+  return prec == WLN_PREC_FP64 ? 2 : 4;
+}
+
+WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec) {
+  WilsonPlan p{};
+  p.P = plan_points_per_lane(ctx, prec);
+  p.warps = ctx->tune_warps ? ctx->tune_warps : (prec == WLN_PREC_FP64 ? 4 : 8);
+  p.rows = ctx->tune_rows ? ctx->tune_rows : 32;
+  p.stages = ctx->tune_stages ? ctx->tune_stages : 3;
+  p.n_tiles = n_tiles;
+  p.n_tile_groups = (n_tiles + p.warps - 1) / p.warps;
+  if (ctx->tune_chain) {
+    p.chain = ctx->tune_chain;
+  } else {
+    // Enough items to keep every SM busy with a small tail, few partials.
+    const int64_t target = static_cast<int64_t>(ctx->num_sms) * 32;
+    int chain = e.n_blocks;
+    while (chain > 1 && static_cast<int64_t>((e.n_blocks + chain - 1) / chain) * p.n_tile_groups < target)
+      chain = (chain + 1) / 2;
+    p.chain = chain;
+  }
+  p.n_chains = (e.n_blocks + p.chain - 1) / p.chain;
+  p.n_items = static_cast<int64_t>(p.n_chains) * p.n_tile_groups;
+  return p;
+}
+
+cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble& e,
+                          const Tile* tiles, const ProfileDev* profs, const double* rho,
+                          int32_t n_groups, int32_t loops_per_group, wln_prec prec,
+                          double* partial, int64_t n_points, int* d_flag, int64_t* launches) {
+  WilsonPlan plan = plan_in;
+  KParams kp{};
+  kp.blocks = e.blocks; kp.n_blocks = e.n_blocks; kp.ppl = e.ppl; kp.n_loops = e.n_loops;
+  kp.tiles = tiles; kp.n_tiles = plan.n_tiles; kp.profs = profs; kp.rho = rho;
+  kp.lpg = loops_per_group; kp.G = n_groups; kp.partial = partial; kp.n_points = n_points;
+  kp.rows = plan.rows; kp.stages = plan.stages; kp.chain = plan.chain;
+  kp.n_tile_groups = plan.n_tile_groups; kp.n_chains = plan.n_chains; kp.n_items = plan.n_items;
+  kp.flag = d_flag;
+  const size_t smem = smem_bytes(plan, e.ppl);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+#define WLN_CASE(A, P_, W_)                                                          \
+  if (plan.P == P_ && plan.warps == W_) {                                            \
+    const int occ = occupancy<A, P_, W_>(smem);                                      \
+    const int64_t g = static_cast<int64_t>(sms) * occ;                               \
+    const int grid = static_cast<int>(g < plan.n_items ? g : plan.n_items);          \
+    ++*launches;                                                                     \
+    return launch_t<A, P_, W_>(s, kp, grid, smem);                                   \
+  }
+  switch (prec) {
+    case WLN_PREC_FP32_COMP:
+      WLN_CASE(F32Comp, 4, 8)
+      WLN_CASE(F32Comp, 2, 8)
+      break;
+    case WLN_PREC_FP32_NAIVE:
+      WLN_CASE(F32Naive, 4, 8)
+      WLN_CASE(F32Naive, 2, 8)
+      break;
+    case WLN_PREC_FP64:
+      WLN_CASE(F64, 2, 4)
+      WLN_CASE(F64, 1, 4)
+      break;
+  }
+#undef WLN_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                                   const double* partial, int64_t n_points, int32_t n_groups,
+                                   int32_t loops_per_group, double* group_sums) {
+  (void)e;
+  const int64_t n = n_points * n_groups * kComps;
+  if (n == 0) return cudaSuccess;
+  reduce_partials_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      partial, n_points, n_groups, loops_per_group, plan.chain * 32, group_sums);
+  return cudaGetLastError();
+}
+
+}  // namespace wln

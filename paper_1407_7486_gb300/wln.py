@@ -1,0 +1,278 @@
+"""Python binding of libwln (ctypes): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module turns
+numpy arrays and torch tensors into pointers and sizes, and turns status
+codes into exceptions.  There is no fallback: if ``libwln.so`` is missing or
+no GPU is present, the calls raise.
+
+The method names are the C entry points without the ``wln_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from .inputs import Profile
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwln.so")
+
+WLN_K = 5
+C_SCAL, C_FERM, C_SIN, C_SCAL_SQ, C_FERM_SQ = range(5)
+PREC = {"fp64": 0, "fp32": 1, "fp32_comp": 1, "fp32_naive": 2}
+STATUS = {0: "WLN_OK", 1: "WLN_EINVAL", 2: "WLN_ENOMEM", 3: "WLN_ECUDA",
+          4: "WLN_ETIMEOUT", 5: "WLN_EBUSY"}
+
+# Every entry point declared in include/wln.h, with its ctypes signature.
+_P, _I32, _I64, _U64, _D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                            ctypes.c_double)
+SIGNATURES = {
+    "wln_create": ([ctypes.POINTER(_P), ctypes.c_int, _P], ctypes.c_int),
+    "wln_destroy": ([_P], ctypes.c_int),
+    "wln_set_stream": ([_P, _P], ctypes.c_int),
+    "wln_synchronize": ([_P], ctypes.c_int),
+    "wln_last_error": ([_P], ctypes.c_char_p),
+    "wln_launch_count": ([_P], _I64),
+    "wln_gen_loops": ([_P, _U64, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "wln_ensemble_from_host": ([_P, _P, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "wln_free_ensemble": ([_P, _P], ctypes.c_int),
+    "wln_ensemble_info": ([_P, _P, _P, _P], ctypes.c_int),
+    "wln_loops_copy": ([_P, _P, _P, _P], ctypes.c_int),
+    "wln_philox_stream": ([_P, _U64, _I64, _I32, _I32, _P], ctypes.c_int),
+    "wln_wilson_avg": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
+    "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
+    "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
+                             ctypes.c_int),
+}
+
+
+class WlnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _CProfile(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("F", ctypes.c_double),
+                ("lam", ctypes.c_double), ("B", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwln.so (built by ``paper_1407_7486_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1407_7486_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a torch tensor or numpy array (None for None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _profiles(profiles: Sequence[Profile]):
+    arr = (_CProfile * len(profiles))()
+    for i, p in enumerate(profiles):
+        arr[i] = _CProfile(int(p.kind), 0, float(p.F), float(p.lam), float(p.B))
+    return arr
+
+
+def _csr(grids: Sequence[Sequence[float]]):
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(g, np.float64) for g in grids]))
+    off = np.zeros(len(grids) + 1, np.int32)
+    off[1:] = np.cumsum([len(g) for g in grids])
+    return flat, off
+
+
+class Ensemble:
+    """Device-resident loop ensemble owned by the library."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self._ctx = ctx
+        self.handle = handle
+        n, ppl, f64 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ctx._check(load().wln_ensemble_info(handle, ctypes.byref(n), ctypes.byref(ppl),
+                                            ctypes.byref(f64)))
+        self.n_loops, self.ppl, self.has_fp64 = n.value, ppl.value, bool(f64.value)
+
+    def free(self):
+        if self.handle:
+            load().wln_free_ensemble(self._ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and self._ctx.handle:
+                self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One device and one CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = ctypes.c_void_p()
+        st = lib.wln_create(ctypes.byref(h), device, raw)
+        if st != 0:
+            raise WlnError(st, "wln_create failed (is a CUDA device present?)")
+        self.handle = h.value
+
+    # ----------------------------------------------------------- plumbing
+    def _check(self, st: int):
+        if st != 0:
+            msg = load().wln_last_error(self.handle)
+            raise WlnError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().wln_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        self._check(load().wln_synchronize(self.handle))
+
+    def set_stream(self, stream):
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.stream = stream
+        self._check(load().wln_set_stream(self.handle, raw))
+
+    @property
+    def launch_count(self) -> int:
+        return int(load().wln_launch_count(self.handle))
+
+    def _empty(self, shape, dtype, where: str):
+        import torch
+        if where == "host":
+            return np.empty(shape, dtype)
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint32: torch.int32}[dtype]
+        return torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
+
+    # ---------------------------------------------------------- ensembles
+    def gen_loops(self, seed: int, n_loops: int, ppl: int, keep_fp64: bool = False) -> Ensemble:
+        h = ctypes.c_void_p()
+        self._check(load().wln_gen_loops(self.handle, seed, n_loops, ppl, int(keep_fp64),
+                                         ctypes.byref(h)))
+        return Ensemble(self, h.value)
+
+    def ensemble_from_host(self, xy) -> Ensemble:
+        """xy: float32 [n_loops][2][ppl] (numpy or torch, host or device)."""
+        if isinstance(xy, np.ndarray):
+            xy = np.ascontiguousarray(xy, np.float32)
+        n_loops, _, ppl = xy.shape
+        h = ctypes.c_void_p()
+        self._check(load().wln_ensemble_from_host(self.handle, _ptr(xy), n_loops, ppl,
+                                                  ctypes.byref(h)))
+        return Ensemble(self, h.value)
+
+    def loops_copy(self, ens: Ensemble, f32=True, f64=False, where: str = "host"):
+        shape = (ens.n_loops, 2, ens.ppl)
+        a = self._empty(shape, np.float32, where) if f32 else None
+        b = self._empty(shape, np.float64, where) if f64 else None
+        self._check(load().wln_loops_copy(self.handle, ens.handle, _ptr(a), _ptr(b)))
+        return a, b
+
+    def philox_stream(self, seed: int, loop0: int, n_loops: int, n_calls: int,
+                      where: str = "host"):
+        out = self._empty((n_loops, n_calls, 4), np.uint32, where)
+        self._check(load().wln_philox_stream(self.handle, seed, loop0, n_loops, n_calls,
+                                             _ptr(out)))
+        return out
+
+    # ------------------------------------------------------- Wilson loops
+    def wilson_avg(self, ens: Ensemble, profiles: Sequence[Profile], rho: Sequence, T: Sequence,
+                   n_groups: int, prec: str = "fp32", out=None, where: str = "device"):
+        """Group sums [n_points][n_groups][5]; points ordered profile, T, rho."""
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
+        if out is None:
+            out = self._empty((n_points, n_groups, WLN_K), np.float64, where)
+        profs = _profiles(profiles)
+        self._check(load().wln_wilson_avg(self.handle, ens.handle, profs, len(profiles),
+                                          _ptr(rho_f), _ptr(rho_off), _ptr(T_f), _ptr(T_off),
+                                          n_groups, PREC[prec], _ptr(out)))
+        return out
+
+    # --------------------------------------------------------- statistics
+    def jackknife(self, group_sums, n_groups: int, loops_per_group: int, comp: int,
+                  jk_var: bool = True, cov: bool = False, where: str = "device"):
+        n_points = group_sums.shape[0]
+        mean = self._empty((n_points,), np.float64, where)
+        sem = self._empty((n_points,), np.float64, where)
+        jv = self._empty((n_points,), np.float64, where) if jk_var else None
+        cv = self._empty((n_points, n_points), np.float64, where) if cov else None
+        self._check(load().wln_jackknife(self.handle, _ptr(group_sums), n_points, n_groups,
+                                         loops_per_group, comp, _ptr(mean), _ptr(sem), _ptr(jv),
+                                         _ptr(cv)))
+        return {"mean": mean, "sem": sem, "jk_var": jv, "cov": cv}
+
+    def loop_sem(self, group_sums, n_groups: int, n_loops: int, comp_sum: int, comp_sq: int,
+                 where: str = "device"):
+        n_points = group_sums.shape[0]
+        out = self._empty((n_points,), np.float64, where)
+        self._check(load().wln_loop_sem(self.handle, _ptr(group_sums), n_points, n_groups,
+                                        n_loops, comp_sum, comp_sq, _ptr(out)))
+        return out
+
+    def effective_action(self, profiles: Sequence[Profile], rho: Sequence, T: Sequence,
+                         group_sums, n_groups: int, loops_per_group: int, spinor: bool = True,
+                         where: str = "device"):
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        gg = self._empty((len(profiles), n_groups), np.float64, where)
+        ms = self._empty((len(profiles), 2), np.float64, where)
+        profs = _profiles(profiles)
+        self._check(load().wln_effective_action(self.handle, profs, len(profiles), _ptr(rho_f),
+                                                _ptr(rho_off), _ptr(T_f), _ptr(T_off),
+                                                _ptr(group_sums), n_groups, loops_per_group,
+                                                int(spinor), _ptr(gg), _ptr(ms)))
+        return gg, ms
+
+
+def header_symbols(header: Optional[str] = None) -> List[str]:
+    """Names of the functions declared in include/wln.h."""
+    import re
+    if header is None:
+        header = os.path.join(os.path.dirname(_HERE), "include", "wln.h")
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(wln_[a-z_0-9]+)\s*\(", text)))

@@ -1,0 +1,46 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports
+every function that include/wln.h declares (no compute calls here)."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1407_7486_gb300 import build, wln
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build.build()
+    assert os.path.exists(path)
+    return wln.load(path)
+
+
+def test_header_and_binding_agree():
+    assert wln.header_symbols() == sorted(wln.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in wln.header_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm103a():
+    log = open(os.path.join(os.path.dirname(build.LIB), "ptxas.log")).read()
+    assert "sm_103a" in log
+    assert "wilson_kernel" in log
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.wln_create(ctypes.byref(h), 0, None)
+    assert st == 3 and not h.value           # WLN_ECUDA, no context
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    assert lib.wln_destroy(None) == 1
+    assert lib.wln_synchronize(None) == 1
+    assert lib.wln_last_error(None) == b"no context"
+    assert lib.wln_ensemble_info(None, None, None, None) == 1
