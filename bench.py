@@ -36,16 +36,18 @@ METRIC = "loop-point evals/s (Wilson loops, FP32-compensated, |d<W>| <= 1e-6)"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # Algorithmic FP32 operations per (segment, point) of the compensated walk,
-# counted from the formula in csrc/wln_wilson.cu (FMA = 1 operation): 22
-# for the geometry, closed-form integrals and products, 8 for the two
-# compensated (Kahan) additions, about 12 for the arctangent's reduction and
-# polynomial, and 11 per segment shared by the P = 4 radii of a lane (11/4).
-N_ALG_FP32 = 22 + 8 + 12 + 11 / 4
+# counted from the formulas in csrc/wln_wilson.cu (an FMA, a min/max or a
+# select each count 1): 19 per radius for the geometry, the closed-form
+# integrals, the products and the two partial sums; 17 for the arctangent
+# (range fold 2, quotient 1, square 1, polynomial 8, octant unfolding 4,
+# plus t*s 1); 11 per segment shared by the lane's P = 4 radii (11/4); and
+# two Kahan folds of 4 operations every 8 segments (1).
+N_ALG_FP32 = 19 + 17 + 11 / 4 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 
 
 def _workload(name: str) -> I.Workload:
-    return {"paper": I.paper, "small": I.small}[name]()
+    return {"paper": I.paper, "small": I.small, "paper_slice": I.paper_slice}[name]()
 
 
 def _peaks():
@@ -196,13 +198,12 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     rho = wl.rho[q][::8]
     T = wl.T[q][::8]
     lpg = wl.n_loops // wl.n_groups
-    # calibrate on one group
+    # calibrate on one group at every sampled point (enough (point, group) pairs for all threads)
     y = oracle.gen_loops(wl.seed, lpg, wl.ppl).astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.group_sums(y, prof, rho[:1], T[:1], 1, threads=threads)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    per_lp = dt / lpg
-    n_groups = int(max(1, min(wl.n_groups, budget_s / (per_lp * lpg * len(rho) * len(T)))))
+    oracle.group_sums(y, prof, rho, T, 1, threads=threads)
+    per_group = max(time.perf_counter() - t0, 1e-6)
+    n_groups = int(max(1, min(wl.n_groups, budget_s / per_group)))
     y = oracle.gen_loops(wl.seed, n_groups * lpg, wl.ppl).astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     ref = oracle.group_sums(y, prof, rho, T, n_groups, threads=threads)
@@ -215,7 +216,9 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
         S = gpu_ctx.wilson_avg(ens, [prof], [rho], [T], wl.n_groups, prec=prec, where="host")
         S = S[:, :n_groups]
         d = np.abs(S - ref) / lpg
-        err[prec] = {"scal_max_abs": float(d[:, :, 0].max()), "ferm_max_abs": float(d[:, :, 1].max())}
+        rel = np.abs(S - ref)[:, :, 1] / np.maximum(np.abs(ref[:, :, 1]), lpg)
+        err[prec] = {"scal_max_abs": float(d[:, :, 0].max()),
+                     "ferm_max_rel_to_max(1,|<W>-1|)": float(rel.max())}
     ens.free()
     return {"value": lp / dt, "unit": "loop-point evals/s", "cores": threads, "kind": "oracle",
             "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every 8th), "
@@ -265,7 +268,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wln", choices=["wln", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "paper_slice"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -379,19 +382,20 @@ def main():
     }
     # FP64 GPU path on one profile and a sparse subset of points (it is ~10^2 slower)
     if args.prec == "fp32":
-        sub_rho = [wl.rho[1][::8]]
-        sub_T = [wl.T[1][::4]]
+        q = 1 if len(wl.profiles) > 1 else 0
+        sub_rho = [wl.rho[q][::8]]
+        sub_T = [wl.T[q][::4]]
         ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
-        ctx.wilson_avg(ens, [wl.profiles[1]], sub_rho, sub_T, wl.n_groups, prec="fp64")
+        ctx.wilson_avg(ens, [wl.profiles[q]], sub_rho, sub_T, wl.n_groups, prec="fp64")
         stream.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx.wilson_avg(ens, [wl.profiles[1]], sub_rho, sub_T, wl.n_groups, prec="fp64")
+        ctx.wilson_avg(ens, [wl.profiles[q]], sub_rho, sub_T, wl.n_groups, prec="fp64")
         b.record(stream)
         stream.synchronize()
         n_lp = wl.n_loops * len(sub_rho[0]) * len(sub_T[0])
         line["fp64_gpu"] = {"value": n_lp / (a.elapsed_time(b) / 1e3), "unit": "loop-point evals/s",
-                            "sample": f"F={wl.profiles[1].F}, {len(sub_rho[0])} rho x "
+                            "sample": f"F={wl.profiles[q].F}, {len(sub_rho[0])} rho x "
                                       f"{len(sub_T[0])} T, all loops, Wilson kernel only"}
         ens.free()
     if not args.no_cpu_baseline and ws == 1:

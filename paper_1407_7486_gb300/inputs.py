@@ -105,6 +105,17 @@ def paper(fluxes: Sequence[float] = (1.0, 10.0, 50.0), n_loops: int = 10240,
                     T=[log_grid(1e-3, 20.0, n_T) for _ in profs])
 
 
+def paper_slice() -> Workload:
+    """The paper-scale ensemble against one flux tube (F = 10) on every 4th
+    proper time and radius (16 x 32 points): a launch of ~1/50 the size, for
+    profiling the Wilson kernel."""
+    return Workload("paper slice: 10240 loops x 2048 ppl, F=10 lam=1, 16 T in [1e-3,20] x "
+                    "32 rho in [0,8], G=32",
+                    seed=1, n_loops=10240, ppl=2048, n_groups=32,
+                    profiles=[Profile(PROFILE_FLUX_TUBE, F=10.0, lam=1.0)],
+                    rho=[lin_grid(0.0, 8.0, 128)[::4]], T=[log_grid(1e-3, 20.0, 64)[::4]])
+
+
 def sweep(ppl: int) -> Workload:
     profs, rhos, Ts = [], [], []
     for F in (1.0, 100.0):
