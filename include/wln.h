@@ -180,6 +180,35 @@ wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
                           const double* T, const int32_t* T_off,
                           int32_t n_groups, wln_prec prec, double* group_sums);
 
+/*
+ * wln_wilson_avg without any allocation: the same group sums, with the same
+ * arguments and results, but the call allocates no device or pinned host
+ * memory.  The paper has no counterpart; this entry point exists for callers
+ * that cannot allocate device memory themselves or through the library: a
+ * host framework whose own caching allocator owns the device memory and
+ * forbids direct cudaMalloc, a latency-bound loop that must not take the
+ * implicit device synchronisation of cudaMalloc/cudaFree, or a service that
+ * reserved the device memory up front.
+ *
+ * Working memory (inputs copied from the host, the work list, the partial
+ * sums, and the group sums when group_sums is host memory) comes from one
+ * 64 MiB array compiled into the library.  Every GPU on which the library is
+ * used holds that array until the process exits.  A problem that needs more
+ * than 64 MiB returns WLN_EINVAL with the size it needed: the partial sums take
+ * (chains + n_groups) * n_points * WLN_K * 8 bytes.
+ * The first call on a device looks up the array's device address (and may load
+ * the library's device code); make that first call before any CUDA stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * every word a call reads is written by that call first, so nothing needs
+ * clearing, but calls whose GPU work overlaps in time (other streams, other
+ * threads) race on it and must be serialised by the caller.
+ */
+wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* ens,
+                                  const wln_profile* profiles, int32_t n_profiles,
+                                  const double* rho_cm, const int32_t* rho_off,
+                                  const double* T, const int32_t* T_off,
+                                  int32_t n_groups, wln_prec prec, double* group_sums);
+
 /* -------------------------------------------------------------- statistics */
 
 /*

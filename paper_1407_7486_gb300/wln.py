@@ -43,6 +43,8 @@ SIGNATURES = {
     "wln_loops_copy": ([_P, _P, _P, _P], ctypes.c_int),
     "wln_philox_stream": ([_P, _U64, _I64, _I32, _I32, _P], ctypes.c_int),
     "wln_wilson_avg": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
+    "wln_wilson_avg_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
+                               ctypes.c_int),
     "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
@@ -231,6 +233,22 @@ class Context:
         self._check(load().wln_wilson_avg(self.handle, ens.handle, profs, len(profiles),
                                           _ptr(rho_f), _ptr(rho_off), _ptr(T_f), _ptr(T_off),
                                           n_groups, PREC[prec], _ptr(out)))
+        return out
+
+    def wilson_avg_noalloc(self, ens: Ensemble, profiles: Sequence[Profile], rho: Sequence,
+                           T: Sequence, n_groups: int, prec: str = "fp32", out=None,
+                           where: str = "device"):
+        """wilson_avg through the entry point that allocates no device memory
+        (working memory from the library's fixed 64 MiB array)."""
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
+        if out is None:
+            out = self._empty((n_points, n_groups, WLN_K), np.float64, where)
+        profs = _profiles(profiles)
+        self._check(load().wln_wilson_avg_noalloc(self.handle, ens.handle, profs, len(profiles),
+                                                  _ptr(rho_f), _ptr(rho_off), _ptr(T_f),
+                                                  _ptr(T_off), n_groups, PREC[prec], _ptr(out)))
         return out
 
     # --------------------------------------------------------- statistics
