@@ -262,6 +262,91 @@ wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles,
                                 int32_t n_groups, int32_t loops_per_group, int32_t spinor,
                                 double* gamma_groups, double* gamma_mean_sem);
 
+/* ------------------------------------------------------- runtime: tuning */
+
+/*
+ * Work decomposition of later Wilson launches on this context (0 = automatic):
+ * points_per_lane (radii held by one lane: 2 or 4), warps per CTA (8), rows
+ * (float4 rows of loop data per staged chunk, a power of two), stages (chunks
+ * in flight, 2..8) and chain_blocks (consecutive 32-loop blocks per work
+ * item).  The paper has no counterpart (its kernel used one thread per loop
+ * and one launch per point); the autotuner sets these.
+ */
+wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, int32_t rows,
+                          int32_t stages, int32_t chain_blocks);
+
+/* -------------------------------------------------------- runtime: batches */
+
+/*
+ * A batch fixes a set of profiles and grids against one ensemble (arguments
+ * as wln_wilson_avg) and keeps its work list, quadrature tables and results
+ * in device memory it owns.  The paper has no counterpart: its host loop
+ * launched one kernel per (rho_cm, T) point.
+ * wln_batch_run enqueues one pass: the Wilson group sums, the mean and group
+ * SEM of W_scal - 1 and W_ferm - 1 per point, and (when every profile's radii
+ * are evenly spaced and its times geometric) the per-group effective action
+ * of the spinor and the scalar loop.  use_graph != 0 records the pass into a
+ * CUDA graph on the first call and replays the graph afterwards (the context
+ * stream must not be the legacy default stream).  The ensemble must outlive
+ * the batch.
+ * wln_batch_results copies the results out (each pointer may be NULL; host or
+ * device): group_sums double[n_points][G][WLN_K]; stats double[4][n_points]
+ * = mean and SEM of W_scal - 1, mean and SEM of W_ferm - 1; gamma
+ * double[2][n_profiles][2] = (mean, SEM) of the spinor, then of the scalar
+ * effective action (WLN_EINVAL if the grids do not allow it).
+ */
+typedef struct wln_batch wln_batch;
+wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                            int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                            const double* T, const int32_t* T_off, int32_t n_groups,
+                            wln_prec prec, wln_batch** out);
+wln_status wln_batch_run(wln_ctx* ctx, wln_batch* batch, int32_t use_graph);
+wln_status wln_batch_results(wln_ctx* ctx, const wln_batch* batch, double* group_sums,
+                             double* stats, double* gamma);
+/* Sizes and decomposition of a batch; any output may be NULL. */
+wln_status wln_batch_info(const wln_batch* batch, int64_t* n_points, int32_t* n_tiles,
+                          int32_t* points_per_lane, int32_t* chain_blocks,
+                          int64_t* kernels_per_run);
+wln_status wln_batch_free(wln_ctx* ctx, wln_batch* batch);
+
+/* --------------------------------------------------------- runtime: server */
+
+/*
+ * Continuous-batching request server over one device-resident ensemble.  The
+ * paper has no counterpart.  A request is one profile with its own radii and
+ * proper times.  Its working memory (partial sums, results) comes from a
+ * device arena of arena_bytes owned by the server; requests are admitted in
+ * arrival order as arena space frees up.  Each wln_server_step launches one
+ * Wilson kernel over up to tile_groups_per_step tile groups (8 tiles of 4
+ * radii each), taken from the oldest admitted requests first, so work of
+ * several requests shares a launch; at most two steps are in flight.  When
+ * all of a request's tile groups are done, its group sums, statistics and
+ * effective action are computed on a second stream and copied to pinned host
+ * memory.  A request's sums are accumulated in the same order whatever it
+ * shares its steps with, so its results do not depend on the mix.
+ * wln_server_submit fails with WLN_EINVAL if the request could never fit the
+ * arena.  wln_server_poll sets *state (0 queued, 1 running, 2 finishing,
+ * 3 done, 4 cancelled) and, when done, copies the results (layouts as
+ * wln_batch_results, n_profiles = 1; any pointer may be NULL; host memory).
+ * wln_server_release drops a done or cancelled request's host results.
+ * wln_server_step waits only when two steps are already in flight.  The server
+ * is not thread-safe: drive it from one thread.
+ */
+typedef struct wln_server wln_server;
+wln_status wln_server_create(wln_ctx* ctx, const wln_ensemble* ens, int32_t n_groups,
+                             wln_prec prec, int64_t arena_bytes, int32_t tile_groups_per_step,
+                             wln_server** out);
+wln_status wln_server_submit(wln_server* server, const wln_profile* profile, const double* rho_cm,
+                             int32_t n_rho, const double* T, int32_t n_T, int64_t* request_id);
+wln_status wln_server_step(wln_server* server, int32_t* n_active, int32_t* n_queued);
+wln_status wln_server_poll(wln_server* server, int64_t request_id, int32_t* state,
+                           double* group_sums, double* stats, double* gamma);
+wln_status wln_server_cancel(wln_server* server, int64_t request_id);
+wln_status wln_server_release(wln_server* server, int64_t request_id);
+wln_status wln_server_info(const wln_server* server, int64_t* steps, int64_t* arena_free_bytes,
+                           int32_t* n_active, int32_t* n_queued);
+wln_status wln_server_free(wln_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,22 +61,20 @@ wln_status ensure_pinned(wln_ctx* ctx, size_t bytes) {
   return WLN_OK;
 }
 
+// Restores the caller's current device on scope exit.
+DeviceGuard::DeviceGuard(int dev) {
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != dev) cudaSetDevice(dev);
+}
+
+DeviceGuard::~DeviceGuard() {
+  int cur = -1;
+  if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
@@ -184,12 +182,8 @@ cudaError_t copy_back(const Out& o, cudaStream_t s) {
   return cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, s);
 }
 
-struct Batch {
-  std::vector<Tile> tiles;
-  std::vector<ProfileDev> profs;
-  std::vector<double> rho;
-  int64_t n_points = 0;
-};
+}  // namespace
+
 
 wln_status check_batch(wln_ctx* ctx, const wln_profile* profiles, int32_t n_profiles,
                        const double* rho_cm, const int32_t* rho_off, const double* T,
@@ -215,25 +209,66 @@ wln_status check_batch(wln_ctx* ctx, const wln_profile* profiles, int32_t n_prof
   return WLN_OK;
 }
 
+bool build_quad(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                const int32_t* rho_off, const double* T, const int32_t* T_off,
+                std::vector<QuadProfile>& qp, std::string* why) {
+  qp.assign(n_profiles, QuadProfile{});
+  int64_t base = 0;
+  for (int q = 0; q < n_profiles; ++q) {
+    const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
+    const double* r = rho_cm + rho_off[q];
+    const double* t = T + T_off[q];
+    QuadProfile& x = qp[q];
+    x.kind = profiles[q].kind;
+    x.n_rho = nr; x.n_T = nt; x.rho_base = rho_off[q]; x.T_base = T_off[q];
+    x.p0 = base;
+    x.h_rho = nr > 1 ? (r[nr - 1] - r[0]) / (nr - 1) : 0.0;
+    x.h_u = nt > 1 ? std::log(t[nt - 1] / t[0]) / (nt - 1) : 0.0;
+    for (int i = 1; i < nr; ++i)
+      if (std::fabs((r[i] - r[i - 1]) - x.h_rho) > 1e-9 * (std::fabs(x.h_rho) + std::fabs(r[i]))) {
+        if (why) *why = "rho_cm must be evenly spaced";
+        return false;
+      }
+    for (int i = 1; i < nt; ++i)
+      if (std::fabs(std::log(t[i] / t[i - 1]) - x.h_u) > 1e-9 * (std::fabs(x.h_u) + 1.0)) {
+        if (why) *why = "T must be geometrically spaced";
+        return false;
+      }
+    if (x.kind == WLN_PROFILE_FLUX_TUBE) {
+      x.l2 = profiles[q].lambda * profiles[q].lambda;
+      x.eB_scale = profiles[q].F * x.l2 / 3.14159265358979323846;   // 2 calF lambda^2
+    } else {
+      x.l2 = 1.0;
+      x.eB_scale = profiles[q].B;
+    }
+    base += static_cast<int64_t>(nr) * nt;
+  }
+  return true;
+}
+
+ProfileDev profile_constants(const wln_profile& pr, int ppl) {
+  const double pi = 3.14159265358979323846;
+  ProfileDev pd{};
+  pd.kind = pr.kind;
+  if (pr.kind == WLN_PROFILE_FLUX_TUBE) {
+    pd.l2 = pr.lambda * pr.lambda;
+    pd.turns_per = pr.F / (4.0 * pi * pi);                        // calF / (2 pi)
+    pd.spin_per = (pr.F / (2.0 * pi)) * pd.l2 / ppl;               // calF lambda^2 / N
+  } else {
+    pd.l2 = 1.0;
+    pd.turns_per = pr.B / (4.0 * pi);
+    pd.spin_per = pr.B;
+  }
+  return pd;
+}
+
 void build_batch(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
                  const int32_t* rho_off, const double* T, const int32_t* T_off, int ppl, int P,
                  Batch& bt) {
   bt.rho.assign(rho_cm, rho_cm + rho_off[n_profiles]);
   int64_t base = 0;
   for (int q = 0; q < n_profiles; ++q) {
-    const wln_profile& pr = profiles[q];
-    ProfileDev pd{};
-    pd.kind = pr.kind;
-    if (pr.kind == WLN_PROFILE_FLUX_TUBE) {
-      pd.l2 = pr.lambda * pr.lambda;
-      pd.turns_per = pr.F / (4.0 * kPi * kPi);                       // calF / (2 pi)
-      pd.spin_per = (pr.F / (2.0 * kPi)) * pd.l2 / ppl;              // calF lambda^2 / N
-    } else {
-      pd.l2 = 1.0;
-      pd.turns_per = pr.B / (4.0 * kPi);
-      pd.spin_per = pr.B;
-    }
-    bt.profs.push_back(pd);
+    bt.profs.push_back(profile_constants(profiles[q], ppl));
     const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
     for (int it = 0; it < nt; ++it)
       for (int a = 0; a < nr; a += P) {
@@ -248,9 +283,12 @@ void build_batch(const wln_profile* profiles, int32_t n_profiles, const double* 
     base += static_cast<int64_t>(nr) * nt;
   }
   bt.n_points = base;
+  for (Tile& t : bt.tiles) {
+    t.part_base = 0;
+    t.part_stride = static_cast<int32_t>(base);
+  }
 }
 
-}  // namespace
 }  // namespace wln
 
 using namespace wln;
@@ -575,33 +613,11 @@ wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles, int32
   if (n_groups < 2 || loops_per_group < 1) return fail(ctx, WLN_EINVAL, "bad group sizes");
   wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
   if (st != WLN_OK) return st;
-  std::vector<QuadProfile> qp(n_profiles);
-  int64_t base = 0;
-  for (int q = 0; q < n_profiles; ++q) {
-    const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
-    const double* r = rho_cm + rho_off[q];
-    const double* t = T + T_off[q];
-    QuadProfile& x = qp[q];
-    x.kind = profiles[q].kind;
-    x.n_rho = nr; x.n_T = nt; x.rho_base = rho_off[q]; x.T_base = T_off[q];
-    x.p0 = base;
-    x.h_rho = nr > 1 ? (r[nr - 1] - r[0]) / (nr - 1) : 0.0;
-    x.h_u = nt > 1 ? std::log(t[nt - 1] / t[0]) / (nt - 1) : 0.0;
-    for (int i = 1; i < nr; ++i)
-      if (std::fabs((r[i] - r[i - 1]) - x.h_rho) > 1e-9 * (std::fabs(x.h_rho) + std::fabs(r[i])))
-        return fail(ctx, WLN_EINVAL, "rho_cm must be evenly spaced");
-    for (int i = 1; i < nt; ++i)
-      if (std::fabs(std::log(t[i] / t[i - 1]) - x.h_u) > 1e-9 * (std::fabs(x.h_u) + 1.0))
-        return fail(ctx, WLN_EINVAL, "T must be geometrically spaced");
-    if (x.kind == WLN_PROFILE_FLUX_TUBE) {
-      x.l2 = profiles[q].lambda * profiles[q].lambda;
-      x.eB_scale = profiles[q].F * x.l2 / kPi;            // 2 calF lambda^2
-    } else {
-      x.l2 = 1.0;
-      x.eB_scale = profiles[q].B;
-    }
-    base += static_cast<int64_t>(nr) * nt;
-  }
+  std::vector<QuadProfile> qp;
+  std::string why;
+  if (!build_quad(profiles, n_profiles, rho_cm, rho_off, T, T_off, qp, &why))
+    return fail(ctx, WLN_EINVAL, why);
+  const int64_t base = qp.back().p0 + static_cast<int64_t>(qp.back().n_rho) * qp.back().n_T;
   DeviceGuard guard(ctx->device);
   const size_t nS = static_cast<size_t>(base) * n_groups * WLN_K;
   const bool s_dev = is_device_ptr(group_sums);

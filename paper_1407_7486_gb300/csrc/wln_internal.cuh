@@ -42,13 +42,19 @@ struct ProfileDev {
                       // constant field: B (spin = B T)
 };
 
-// A tile: P consecutive radii of one profile at one proper time.
+// A tile: P consecutive radii of one profile at one proper time.  Its
+// partial sums go to partial[part_base + ((c + g) * part_stride + p0 + i) * K]:
+// one launch can serve several independent batches (requests), each with its
+// own partial buffer and point count.
 struct Tile {
   int32_t profile;
   int32_t n_valid;    // radii in this tile (1..P)
   int32_t rho0;       // index of the first radius in the flattened rho array
-  int32_t p0;         // point index of the first radius
+  int32_t p0;         // point index of the first radius within its batch
   double T;
+  int64_t part_base;  // offset (in doubles) of its batch's partial buffer
+  int32_t part_stride;  // points in its batch
+  int32_t pad;
 };
 
 // Geometry of one Wilson launch.
@@ -101,6 +107,28 @@ bool is_device_ptr(const void* p);
 wln_status ensure_scratch(wln_ctx* ctx, size_t bytes);
 wln_status ensure_pinned(wln_ctx* ctx, size_t bytes);
 
+// Restores the caller's current device on scope exit (wln_api.cu).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+};
+
+// Host-side work list of one batch of profiles (wln_api.cu).
+struct Batch {
+  std::vector<Tile> tiles;
+  std::vector<ProfileDev> profs;
+  std::vector<double> rho;
+  int64_t n_points = 0;
+};
+wln_status check_batch(wln_ctx* ctx, const wln_profile* profiles, int32_t n_profiles,
+                       const double* rho_cm, const int32_t* rho_off, const double* T,
+                       const int32_t* T_off);
+void build_batch(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                 const int32_t* rho_off, const double* T, const int32_t* T_off, int ppl, int P,
+                 Batch& bt);
+ProfileDev profile_constants(const wln_profile& pr, int ppl);
+
 // Generation (wln_gen.cu).
 cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
                                  int32_t n_calls, uint32_t* out);
@@ -138,6 +166,11 @@ struct QuadProfile {
   double eB_scale;   // flux tube: 2 calF lambda^2 = F lambda^2 / pi; constant: B
   double l2;
 };
+// Quadrature tables of a batch of profiles; false (with a reason) when a
+// profile's radii are not evenly spaced or its times not geometric (wln_api.cu).
+bool build_quad(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                const int32_t* rho_off, const double* T, const int32_t* T_off,
+                std::vector<QuadProfile>& qp, std::string* why);
 cudaError_t launch_effective_action(cudaStream_t s, const QuadProfile* qp, int32_t n_profiles,
                                     const double* rho, const double* T, const double* S,
                                     int32_t G, int32_t lpg, int32_t spinor, double* gamma_groups,

@@ -99,6 +99,8 @@ __global__ void noalloc_tiles_kernel(int32_t n_tiles, int32_t n_profiles, const 
   x.rho0 = rho_off[q] + a;
   x.p0 = static_cast<int32_t>(point_base[q] + static_cast<int64_t>(it) * nr + a);
   x.T = T[T_off[q] + it];
+  x.part_base = 0;
+  x.part_stride = static_cast<int32_t>(point_base[n_profiles]);
   tiles[t] = x;
 }
 

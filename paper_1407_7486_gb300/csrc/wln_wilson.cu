@@ -434,7 +434,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   wk.l2 = static_cast<F>(prof.l2);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const int i = p < tile.n_valid ? p : tile.n_valid - 1;
+    const int i = p < tile.n_valid ? p : (tile.n_valid > 0 ? tile.n_valid - 1 : 0);
     wk.rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
   }
   const double st_d = prof.spin_per * tile.T;
@@ -446,7 +446,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   auto flush = [&](int g) {
     __syncwarp();
     if (active) {
-      double* dst = k.partial + (static_cast<size_t>(c + g) * k.n_points + tile.p0) * kComps;
+      double* dst = k.partial + tile.part_base +
+                    (static_cast<size_t>(c + g) * tile.part_stride + tile.p0) * kComps;
       for (int j = lane; j < V; j += 32) {
         double sum = 0.0;
         const double* row = acc + j * 33;
@@ -569,8 +570,8 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(
     const int c = static_cast<int>(item / k.n_tile_groups);
     const int tg = static_cast<int>(item % k.n_tile_groups);
     const int t = tg * WARPS + warp;
-    const bool active = t < k.n_tiles;
-    const Tile tile = k.tiles[active ? t : 0];
+    const Tile tile = k.tiles[t < k.n_tiles ? t : 0];
+    const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
     const ProfileDev prof = k.profs[tile.profile];
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);

@@ -49,6 +49,23 @@ SIGNATURES = {
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
                              ctypes.c_int),
+    "wln_set_tuning": ([_P, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
+    "wln_batch_create": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int,
+                          ctypes.POINTER(_P)], ctypes.c_int),
+    "wln_batch_run": ([_P, _P, _I32], ctypes.c_int),
+    "wln_batch_results": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "wln_batch_info": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "wln_batch_free": ([_P, _P], ctypes.c_int),
+    "wln_server_create": ([_P, _P, _I32, ctypes.c_int, _I64, _I32, ctypes.POINTER(_P)],
+                          ctypes.c_int),
+    "wln_server_submit": ([_P, _P, _P, _I32, _P, _I32, ctypes.POINTER(_I64)], ctypes.c_int),
+    "wln_server_step": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "wln_server_poll": ([_P, _I64, ctypes.POINTER(_I32), _P, _P, _P], ctypes.c_int),
+    "wln_server_cancel": ([_P, _I64], ctypes.c_int),
+    "wln_server_release": ([_P, _I64], ctypes.c_int),
+    "wln_server_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                         ctypes.POINTER(_I32)], ctypes.c_int),
+    "wln_server_free": ([_P], ctypes.c_int),
 }
 
 
@@ -178,6 +195,11 @@ class Context:
         self.stream = stream
         self._check(load().wln_set_stream(self.handle, raw))
 
+    def set_tuning(self, points_per_lane: int = 0, warps: int = 0, rows: int = 0,
+                   stages: int = 0, chain_blocks: int = 0):
+        self._check(load().wln_set_tuning(self.handle, points_per_lane, warps, rows, stages,
+                                          chain_blocks))
+
     @property
     def launch_count(self) -> int:
         return int(load().wln_launch_count(self.handle))
@@ -285,6 +307,127 @@ class Context:
                                                 _ptr(group_sums), n_groups, loops_per_group,
                                                 int(spinor), _ptr(gg), _ptr(ms)))
         return gg, ms
+
+
+class Batch:
+    """A fixed set of profiles and grids whose runs can be replayed from a CUDA
+    graph (wln_batch_*)."""
+
+    def __init__(self, ctx: "Context", ens: Ensemble, profiles: Sequence[Profile], rho: Sequence,
+                 T: Sequence, n_groups: int, prec: str = "fp32"):
+        self._ctx = ctx
+        self.ens = ens
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        h = ctypes.c_void_p()
+        ctx._check(load().wln_batch_create(ctx.handle, ens.handle, _profiles(profiles),
+                                           len(profiles), _ptr(rho_f), _ptr(rho_off), _ptr(T_f),
+                                           _ptr(T_off), n_groups, PREC[prec], ctypes.byref(h)))
+        self.handle = h.value
+        self.n_groups = n_groups
+        self.n_profiles = len(profiles)
+        npts, nt, P, ch, kpr = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(),
+                                ctypes.c_int32(), ctypes.c_int64())
+        load().wln_batch_info(self.handle, ctypes.byref(npts), ctypes.byref(nt), ctypes.byref(P),
+                              ctypes.byref(ch), ctypes.byref(kpr))
+        self.n_points, self.n_tiles, self.P, self.chain = npts.value, nt.value, P.value, ch.value
+
+    @property
+    def kernels_per_run(self) -> int:
+        k = ctypes.c_int64()
+        load().wln_batch_info(self.handle, None, None, None, None, ctypes.byref(k))
+        return k.value
+
+    def run(self, graph: bool = True):
+        self._ctx._check(load().wln_batch_run(self._ctx.handle, self.handle, int(graph)))
+
+    def results(self, sums: bool = True, stats: bool = True, gamma: bool = True,
+                where: str = "host"):
+        S = self._ctx._empty((self.n_points, self.n_groups, WLN_K), np.float64, where) if sums else None
+        st = self._ctx._empty((4, self.n_points), np.float64, where) if stats else None
+        g = self._ctx._empty((2, self.n_profiles, 2), np.float64, where) if gamma else None
+        self._ctx._check(load().wln_batch_results(self._ctx.handle, self.handle, _ptr(S), _ptr(st),
+                                                  _ptr(g)))
+        return S, st, g
+
+    def free(self):
+        if self.handle:
+            load().wln_batch_free(self._ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (wln_server_*)."""
+
+    QUEUED, RUNNING, FINISHING, DONE, CANCELLED = range(5)
+
+    def __init__(self, ctx: "Context", ens: Ensemble, n_groups: int, prec: str = "fp32",
+                 arena_bytes: int = 4 << 30, tile_groups_per_step: int = 64):
+        self._ctx = ctx
+        self.ens = ens
+        self.n_groups = n_groups
+        h = ctypes.c_void_p()
+        ctx._check(load().wln_server_create(ctx.handle, ens.handle, n_groups, PREC[prec],
+                                            arena_bytes, tile_groups_per_step, ctypes.byref(h)))
+        self.handle = h.value
+        self._npts = {}
+
+    def submit(self, profile: Profile, rho, T) -> int:
+        rho = np.ascontiguousarray(rho, np.float64)
+        T = np.ascontiguousarray(T, np.float64)
+        rid = ctypes.c_int64()
+        self._ctx._check(load().wln_server_submit(self.handle, _profiles([profile]), _ptr(rho),
+                                                  len(rho), _ptr(T), len(T), ctypes.byref(rid)))
+        self._npts[rid.value] = len(rho) * len(T)
+        return rid.value
+
+    def step(self):
+        a, q = ctypes.c_int32(), ctypes.c_int32()
+        self._ctx._check(load().wln_server_step(self.handle, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, rid: int, results: bool = True):
+        st = ctypes.c_int32()
+        n = self._npts[rid]
+        S = np.empty((n, self.n_groups, WLN_K)) if results else None
+        stats = np.empty((4, n)) if results else None
+        gamma = np.empty((2, 1, 2)) if results else None
+        self._ctx._check(load().wln_server_poll(self.handle, rid, ctypes.byref(st), _ptr(S),
+                                                _ptr(stats), _ptr(gamma)))
+        if st.value != self.DONE:
+            return st.value, None
+        return st.value, (S, stats, gamma)
+
+    def cancel(self, rid: int):
+        self._ctx._check(load().wln_server_cancel(self.handle, rid))
+
+    def release(self, rid: int):
+        self._ctx._check(load().wln_server_release(self.handle, rid))
+        self._npts.pop(rid, None)
+
+    def info(self):
+        steps, free_b, a, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        load().wln_server_info(self.handle, ctypes.byref(steps), ctypes.byref(free_b),
+                               ctypes.byref(a), ctypes.byref(q))
+        return {"steps": steps.value, "arena_free_bytes": free_b.value, "active": a.value,
+                "queued": q.value}
+
+    def free(self):
+        if self.handle:
+            load().wln_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def header_symbols(header: Optional[str] = None) -> List[str]:
