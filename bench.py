@@ -47,7 +47,8 @@ N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 
 
 def _workload(name: str) -> I.Workload:
-    return {"paper": I.paper, "small": I.small, "paper_slice": I.paper_slice}[name]()
+    return {"paper": I.paper, "small": I.small, "paper_slice": I.paper_slice,
+            "batched": I.batched}[name]()
 
 
 def _peaks():
@@ -268,7 +269,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wln", choices=["wln", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "paper_slice"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "paper_slice", "batched"])
+    ap.add_argument("--serve", action="store_true",
+                    help="replay the seed-7 Poisson request stream against the serving ensemble")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rate-scales", default="sat",
+                    help="comma list: 'sat' (2000 req/s) and/or fractions of measured capacity")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -279,6 +285,11 @@ def main():
 
     import torch
     from paper_1407_7486_gb300 import build, wln
+
+    if args.serve:
+        return run_serve(args)
+    if args.workload == "batched":
+        return run_batched(args, wl)
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -405,6 +416,135 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _common_line(metric, value, unit, steps, warmup, ms, dtype, config):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+def run_batched(args, wl: I.Workload):
+    """64 flux tubes with uneven grids against one ensemble: the autotuner picks
+    the kernel shape, then the whole pass (Wilson sums, statistics, per-group
+    effective action) is recorded once into a CUDA graph and replayed."""
+    import torch
+    from paper_1407_7486_gb300 import autotune, build, wln
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+    with torch.cuda.stream(stream):
+        tuned = autotune.tune(ctx, ens, wl.profiles, wl.rho, wl.T, wl.n_groups, use_cache=False)
+        b = wln.Batch(ctx, ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+        for _ in range(args.warmup):
+            b.run(graph=True)
+        stream.synchronize()
+        n0 = ctx.launch_count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                b.run(graph=True)
+            e1.record(stream)
+            stream.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    S, st, g = b.results()
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    seg = wl.segment_evals
+    achieved = N_ALG_FP32 * seg / (ms / 1e3) / 1e12
+    line = _common_line(METRIC, wl.loop_points / (ms / 1e3), "loop-point evals/s", args.steps,
+                        args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
+                        {"workload": wl.name, "n_points": wl.n_points, "n_profiles": len(wl.profiles),
+                         "graph": "one CUDA graph per pass (Wilson, reduction, statistics, action)",
+                         "tiles": {"P": b.P, "chain_blocks": b.chain, "rows": tuned["rows"],
+                                   "stages": tuned["stages"], "tuner": tuned["source"]}})
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                        "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": None,
+                        "kernel_ms": ms, "note": "whole graph pass timed (Wilson > 99%)"}
+    line["gpu_launches"] = int(ctx.launch_count - n0)
+    line["clocks"] = clk.summary()
+    line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
+    line["autotune_candidates"] = tuned.get("candidates")
+    line["finite_gamma"] = bool(np.isfinite(g).all())
+    b.free(); ens.free(); ctx.close()
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """Continuous batching: replay the seed-7 Poisson stream (2000 req/s) of
+    single-profile queries against the serving ensemble (32768 x 4096); each
+    request's latency runs from its arrival to its results on the host."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    cfg = I.serving_ensemble()
+    ens = ctx.gen_loops(cfg["seed"], cfg["n_loops"], cfg["ppl"])
+    reqs = I.request_stream(args.requests)
+    runs = []
+    capacity = None
+    for scale in args.rate_scales.split(","):
+        if scale == "sat":
+            times = [r.arrival_s for r in reqs]
+            label = "2000 req/s (saturated)"
+        else:
+            if capacity is None:
+                continue
+            rate = float(scale) * capacity
+            times = list(np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(reqs))))
+            label = f"{scale} x capacity = {rate:.3f} req/s"
+        sv = wln.Server(ctx, ens, cfg["n_groups"], prec=args.prec, arena_bytes=16 << 30,
+                        tile_groups_per_step=64)
+        t0 = time.perf_counter()
+        pending = list(range(len(reqs)))
+        ids, done_at = {}, {}
+        with ClockSampler(0) as clk:
+            while len(done_at) < len(reqs):
+                now = time.perf_counter() - t0
+                while pending and times[pending[0]] <= now:
+                    i = pending.pop(0)
+                    r = reqs[i]
+                    ids[i] = sv.submit(r.profile, r.rho, r.T)
+                outstanding = len(ids) - len(done_at)
+                if outstanding == 0:
+                    if pending:
+                        time.sleep(max(0.0, times[pending[0]] - (time.perf_counter() - t0)))
+                    continue
+                n_active, n_queued = sv.step()
+                for i, rid in list(ids.items()):
+                    if i in done_at:
+                        continue
+                    state, _ = sv.poll(rid, results=False)
+                    if state == sv.DONE:
+                        done_at[i] = time.perf_counter() - t0
+                        sv.release(rid)
+                if n_active == 0 and n_queued == 0:
+                    time.sleep(0.0005)          # only finalisations in flight
+        makespan = max(done_at.values()) - min(times)
+        lat = np.array([done_at[i] - times[i] for i in range(len(reqs))]) * 1e3
+        lp = sum(r.n_points for r in reqs) * cfg["n_loops"]
+        thr = lp / makespan
+        if scale == "sat":
+            capacity = len(reqs) / makespan
+        runs.append({"rate": label, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "loop_point_evals_per_s": thr,
+                     "makespan_s": makespan, "steps": sv.info()["steps"], "clocks": clk.summary()})
+        sv.free()
+    line = _common_line("serve p50/p99 latency (ms) and loop-point evals/s", runs[0]["loop_point_evals_per_s"],
+                        "loop-point evals/s", len(reqs), 0, None, "f32",
+                        {"workload": f"serving: {cfg['n_loops']} loops x {cfg['ppl']} ppl, G={cfg['n_groups']}, "
+                                     f"first {len(reqs)} requests of the seed-7 Poisson stream",
+                         "arena": "16 GiB", "tile_groups_per_step": 64})
+    line["serve"] = runs
+    line["capacity_req_per_s"] = capacity
+    ens.free(); ctx.close()
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

@@ -633,20 +633,23 @@ size_t smem_bytes(const WilsonPlan& p, int ppl) {
 
 }  // namespace
 
+// Tuning applies to the float flavours; the FP64 comparison path keeps its
+// own shape (2 radii per lane, 4 warps).
 int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec) {
-  if (ctx->tune_P) return ctx->tune_P;
-  return prec == WLN_PREC_FP64 ? 2 : 4;
+  if (prec == WLN_PREC_FP64) return 2;
+  return ctx->tune_P ? ctx->tune_P : 4;
 }
 
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec) {
   WilsonPlan p{};
   p.P = plan_points_per_lane(ctx, prec);
-  p.warps = ctx->tune_warps ? ctx->tune_warps : (prec == WLN_PREC_FP64 ? 4 : 8);
-  p.rows = ctx->tune_rows ? ctx->tune_rows : 32;
-  p.stages = ctx->tune_stages ? ctx->tune_stages : 3;
+  const bool f64 = prec == WLN_PREC_FP64;
+  p.warps = f64 ? 4 : (ctx->tune_warps ? ctx->tune_warps : 8);
+  p.rows = (!f64 && ctx->tune_rows) ? ctx->tune_rows : 32;
+  p.stages = (!f64 && ctx->tune_stages) ? ctx->tune_stages : 3;
   p.n_tiles = n_tiles;
   p.n_tile_groups = (n_tiles + p.warps - 1) / p.warps;
-  if (ctx->tune_chain) {
+  if (ctx->tune_chain && !f64) {
     p.chain = ctx->tune_chain;
   } else {
     // Enough items to keep every SM busy with a small tail, few partials.
