@@ -102,10 +102,21 @@ const char* wln_last_error(const wln_ctx* ctx);
 /* Number of kernel launches this context has issued since creation. */
 int64_t wln_launch_count(const wln_ctx* ctx);
 
+/*
+ * Failure-detection self-test (no counterpart in the paper): one kernel waits
+ * on a device barrier that nothing completes, using the bounded wait of the
+ * Wilson kernel with a limit of timeout_ms (1..2000).  The wait runs out, the
+ * kernel records it and returns, and this call reports WLN_ETIMEOUT; the
+ * context stays usable.  Anything else means the timeout path is broken.
+ */
+wln_status wln_selftest_wait(wln_ctx* ctx, int32_t timeout_ms);
+
 /* --------------------------------------------------------------- ensembles */
 
 /*
- * Draw n_loops closed unit loops of ppl points (Sec. "Loop Generation").
+ * Draw n_loops closed unit loops of ppl points (Sec. "Loop Generation"):
+ * loops loop0 .. loop0 + n_loops - 1 of the ensemble defined by seed, so
+ * ranks can hold disjoint slices of one ensemble (loop0 + n_loops < 2^32).
  * Loop l uses Philox-4x32-10 (Salmon et al., SC'11) with counter (j, l, 0, 0),
  * j = 0 .. ppl/2 - 1, and key (seed & 0xffffffff, seed >> 32).  The four
  * words u0..u3 of call j map to u = (k + 1/2) 2^-32, and Box-Muller gives
@@ -119,8 +130,8 @@ int64_t wln_launch_count(const wln_ctx* ctx);
  * The call synchronises.  It returns WLN_EINVAL if two consecutive stored
  * points coincide (a zero-length segment), which has negligible probability.
  */
-wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int32_t n_loops, int32_t ppl,
-                         int32_t keep_fp64, wln_ensemble** out);
+wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                         int32_t ppl, int32_t keep_fp64, wln_ensemble** out);
 
 /*
  * Make an ensemble from given loops, e.g. a saved one.  xy is

@@ -103,8 +103,9 @@ wln_status check_flag(wln_ctx* ctx) {
     cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     return fail(ctx, WLN_ETIMEOUT,
-                h == kErrTimeoutFull ? "a staged-copy wait ran out (device)"
-                                     : "a buffer-release wait ran out (device)");
+                h == kErrTimeoutFull    ? "a staged-copy wait ran out (device)"
+                : h == kErrTimeoutEmpty ? "a buffer-release wait ran out (device)"
+                                        : "the self-test wait ran out (device), as intended");
   }
   return WLN_OK;
 }
@@ -352,15 +353,30 @@ const char* wln_last_error(const wln_ctx* ctx) { return ctx ? ctx->last_error.c_
 
 int64_t wln_launch_count(const wln_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int32_t n_loops, int32_t ppl,
-                         int32_t keep_fp64, wln_ensemble** out) {
+wln_status wln_selftest_wait(wln_ctx* ctx, int32_t timeout_ms) {
+  if (!ctx) return WLN_EINVAL;
+  if (timeout_ms < 1 || timeout_ms > 2000)
+    return fail(ctx, WLN_EINVAL, "timeout_ms must be in [1, 2000]");
+  DeviceGuard guard(ctx->device);
+  cudaError_t err = launch_selftest_wait(ctx->stream, ctx->d_flag,
+                                         static_cast<uint64_t>(timeout_ms) * 1000000ull);
+  ++ctx->launches;
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "self-test launch");
+  return check_flag(ctx);
+}
+
+wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                         int32_t ppl, int32_t keep_fp64, wln_ensemble** out) {
   if (!ctx || !out) return fail(ctx, WLN_EINVAL, "null argument");
   *out = nullptr;
   wln_status st = check_loops(ctx, n_loops, ppl);
   if (st != WLN_OK) return st;
+  if (loop0 < 0 || loop0 + ((n_loops + 31) / 32) * 32 > (int64_t(1) << 32))
+    return fail(ctx, WLN_EINVAL, "loop0 + n_loops must stay below 2^32 (the Philox counter word)");
   DeviceGuard guard(ctx->device);
   wln_ensemble* en = nullptr;
   if ((st = alloc_ensemble(ctx, n_loops, ppl, keep_fp64 != 0, &en)) != WLN_OK) return st;
+  en->e.loop0 = loop0;
   if ((st = ensure_scratch(ctx, sizeof(int))) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
   int* d_deg = static_cast<int*>(ctx->scratch.ptr);
   cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);

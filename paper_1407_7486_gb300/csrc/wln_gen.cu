@@ -66,17 +66,19 @@ __global__ void philox_stream_kernel(uint64_t seed, int64_t loop0, int32_t n_loo
 
 // One CTA per block of 32 loops: lane = loop, warp w = chunk w of the points.
 // Pass 1 sums the raw increments xi_k and k * xi_k per chunk; a scan over
-// the chunks gives each chunk's starting partial sum.  With mu = mean(xi),
-// the closed positions are p_k = S_k - k mu (S_k = sum_{j<k} xi_j) and their
-// mean is ((N-1)/2) sum xi / N - sum k xi / N - ... folded below.  Pass 2
-// regenerates the chunk's increments and writes y_k = p_k - mean(p).
+// the chunks gives each chunk's starting partial sum S_{k0}.  With
+// mu = mean(xi), the closed positions are p_k = S_k - k mu
+// (S_k = sum_{j<k} xi_j), and their mean is
+// (1/N) sum_j xi_j (N - 1 - j) - mu (N - 1)/2.  Pass 2 regenerates the
+// chunk's increments and writes y_k = p_k - mean(p).
 template <int WG>
-__global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int32_t ppl,
-                                                            float4* blocks, double* xy64,
-                                                            int32_t n_loops) {
+__global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int64_t loop0,
+                                                            int32_t ppl, float4* blocks,
+                                                            double* xy64, int32_t n_loops) {
   __shared__ double part[WG][32][4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t loop = blockIdx.x * 32u + lane;
+  const int32_t local = static_cast<int32_t>(blockIdx.x * 32u + lane);
+  const uint32_t loop = static_cast<uint32_t>(loop0 + local);   // Philox counter word 1
   const int M = ppl / WG;           // points per chunk (even)
   const int k0 = w * M;
   const double scale = sqrt(2.0 / ppl);
@@ -107,8 +109,8 @@ __global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int32
   double pxk = px - k0 * mux, pyk = py - k0 * muy;
 
   float4* row = blocks + (static_cast<size_t>(blockIdx.x) * (ppl / 2) + k0 / 2) * 32 + lane;
-  double* ox = xy64 ? xy64 + static_cast<size_t>(loop) * 2 * ppl : nullptr;
-  const bool real = static_cast<int32_t>(loop) < n_loops;
+  double* ox = xy64 ? xy64 + static_cast<size_t>(local) * 2 * ppl : nullptr;
+  const bool real = local < n_loops;
   for (int k = k0; k < k0 + M; k += 2) {
     double x0, y0, x1, y1;
     increments(seed, loop, k >> 1, scale, x0, y0, x1, y1);
@@ -184,9 +186,9 @@ cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, i
 cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate) {
   const int wg = e.ppl >= 16 ? 8 : e.ppl / 2;
   switch (wg) {
-    case 8: gen_loops_kernel<8><<<e.n_blocks, 256, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
-    case 2: gen_loops_kernel<2><<<e.n_blocks, 64, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
-    case 4: gen_loops_kernel<4><<<e.n_blocks, 128, 0, s>>>(seed, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    case 8: gen_loops_kernel<8><<<e.n_blocks, 256, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    case 2: gen_loops_kernel<2><<<e.n_blocks, 64, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
+    case 4: gen_loops_kernel<4><<<e.n_blocks, 128, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t err = cudaGetLastError();

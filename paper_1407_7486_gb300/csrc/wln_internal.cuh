@@ -22,8 +22,10 @@ constexpr int kLanes = 32;
 // Device error flag values (bounded waits that ran out).
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
+constexpr int kErrTimeoutSelfTest = 3;
 
 struct Ensemble {
+  int64_t loop0 = 0;          // global index of the first loop (Philox counter word 1)
   int32_t n_loops = 0;
   int32_t ppl = 0;
   int32_t n_blocks = 0;       // ceil(n_loops / 32)
@@ -143,6 +145,7 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                           double* partial, int64_t n_points, int* d_flag, int64_t* launches);
+cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns);
 cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                                    const double* partial, int64_t n_points, int32_t n_groups,
                                    int32_t loops_per_group, double* group_sums);

@@ -77,13 +77,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2 s of wall time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase: gives up after limit_ns of wall time
+// (2 s by default), or after 2^26 polls whatever the clock says.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -586,6 +588,19 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(
   }
 }
 
+// Failure-detection self-test: wait on an mbarrier phase that nothing will
+// complete, with the same bounded wait the Wilson kernel uses; when the wait
+// runs out the kernel records it in the device error flag and returns.
+__global__ void selftest_wait_kernel(int* flag, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(flag, kErrTimeoutSelfTest);
+}
+
 // Sum the partials of each group over its chains, in chain order.
 __global__ void reduce_partials_kernel(const double* partial, int64_t n_points, int32_t G,
                                        int32_t lpg, int32_t chain_loops, double* out) {
@@ -704,6 +719,11 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensem
   }
 #undef WLN_CASE
   return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns) {
+  selftest_wait_kernel<<<1, 32, 0, s>>>(d_flag, limit_ns);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,

@@ -36,7 +36,8 @@ SIGNATURES = {
     "wln_synchronize": ([_P], ctypes.c_int),
     "wln_last_error": ([_P], ctypes.c_char_p),
     "wln_launch_count": ([_P], _I64),
-    "wln_gen_loops": ([_P, _U64, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "wln_selftest_wait": ([_P, _I32], ctypes.c_int),
+    "wln_gen_loops": ([_P, _U64, _I64, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
     "wln_ensemble_from_host": ([_P, _P, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
     "wln_free_ensemble": ([_P, _P], ctypes.c_int),
     "wln_ensemble_info": ([_P, _P, _P, _P], ctypes.c_int),
@@ -187,6 +188,10 @@ class Context:
         except Exception:
             pass
 
+    def selftest_wait(self, timeout_ms: int = 50) -> int:
+        """Run the bounded-wait self-test; returns the status (WLN_ETIMEOUT = 4)."""
+        return int(load().wln_selftest_wait(self.handle, timeout_ms))
+
     def synchronize(self):
         self._check(load().wln_synchronize(self.handle))
 
@@ -212,9 +217,10 @@ class Context:
         return torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
 
     # ---------------------------------------------------------- ensembles
-    def gen_loops(self, seed: int, n_loops: int, ppl: int, keep_fp64: bool = False) -> Ensemble:
+    def gen_loops(self, seed: int, n_loops: int, ppl: int, keep_fp64: bool = False,
+                  loop0: int = 0) -> Ensemble:
         h = ctypes.c_void_p()
-        self._check(load().wln_gen_loops(self.handle, seed, n_loops, ppl, int(keep_fp64),
+        self._check(load().wln_gen_loops(self.handle, seed, loop0, n_loops, ppl, int(keep_fp64),
                                          ctypes.byref(h)))
         return Ensemble(self, h.value)
 
