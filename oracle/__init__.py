@@ -58,6 +58,8 @@ def _load():
     lib.wln_oracle_raw_increments.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, f64p]
     lib.wln_oracle_gen_loops.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_int32, f64p, ctypes.c_int32]
+    lib.wln_oracle_gen_dloops.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int32, f64p, ctypes.c_int32]
     lib.wln_oracle_loop_phase_spin.argtypes = [f64p, ctypes.c_int32, ctypes.POINTER(_Profile),
                                                ctypes.c_double, ctypes.c_double,
                                                ctypes.POINTER(ctypes.c_double),
@@ -124,6 +126,13 @@ def gen_loops(seed: int, n_loops: int, ppl: int, loop0: int = 0, threads: int = 
     """CM-centred closed unit loops y[l][c][k] (c = 0: x, 1: y)."""
     y = np.zeros((n_loops, 2, ppl), np.float64)
     _load().wln_oracle_gen_loops(seed, loop0, n_loops, ppl, y, threads or max_threads())
+    return y
+
+
+def gen_dloops(seed: int, n_loops: int, ppl: int, loop0: int = 0, threads: int = 0) -> np.ndarray:
+    """d-loops (Eqs. yn2, ynk), CM-centred: y[l][c][k]."""
+    y = np.zeros((n_loops, 2, ppl), np.float64)
+    _load().wln_oracle_gen_dloops(seed, loop0, n_loops, ppl, y, threads or max_threads())
     return y
 
 

@@ -159,6 +159,60 @@ void wln_oracle_gen_loops(uint64_t seed, int64_t loop0, int64_t n_loops, int32_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* d-loops (Sec. "Loop Generation", Eqs. yn2 and ynk).  Start from one point  */
+/* y_N (taken as the origin; index N is index 0 of the closed loop).  Level 1 */
+/* adds y_{N/2}, Gaussian about y_N with variance 1/N_1 = 1/2 per component.  */
+/* Level k (N_k = 2^k) adds the points q N/N_k, q = 1, 3, ..., N_k - 1, each  */
+/* Gaussian about the mean of its two neighbours of the previous level with   */
+/* variance 1/N_k.  The last level has N_k = N; then the centre of mass is    */
+/* removed (step 5).                                                           */
+/* Gaussian number m (m = 0 for level 1; level k uses m = 2^(k-1) - 1 +       */
+/* (q-1)/2) comes from Philox call j = m/2 with counter (j, loop, 1, 0):      */
+/* (u0,u1) give the x and y of even m, (u2,u3) those of odd m (Box-Muller).   */
+/* ------------------------------------------------------------------------ */
+static void dloop_gaussian(uint64_t seed, int64_t loop, int32_t m, double* gx, double* gy) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)(m / 2), (uint32_t)loop, 1u, 0u}, u[4];
+  wln_oracle_philox4x32(ctr, key, 10, u);
+  if (m % 2 == 0) box_muller(uniform_open(u[0]), uniform_open(u[1]), gx, gy);
+  else box_muller(uniform_open(u[2]), uniform_open(u[3]), gx, gy);
+}
+
+void wln_oracle_dloop(uint64_t seed, int64_t loop, int32_t N, double* y) {
+  double* yx = y;
+  double* yy = y + N;
+  yx[0] = 0.0;
+  yy[0] = 0.0;
+  int32_t m = 0;
+  for (int32_t Nk = 2; Nk <= N; Nk *= 2) {
+    const int32_t stride = N / Nk;          /* index distance between neighbours at this level */
+    const double sigma = sqrt(1.0 / (double)Nk);
+    for (int32_t q = 1; q < Nk; q += 2) {
+      const int32_t i = q * stride;
+      const int32_t left = (q - 1) * stride, right = ((q + 1) * stride) % N;
+      double gx, gy;
+      dloop_gaussian(seed, loop, m++, &gx, &gy);
+      yx[i] = 0.5 * (yx[left] + yx[right]) + sigma * gx;
+      yy[i] = 0.5 * (yy[left] + yy[right]) + sigma * gy;
+    }
+  }
+  for (int c = 0; c < 2; ++c) {
+    double* p = y + (size_t)c * N;
+    double cm = 0.0;
+    for (int32_t k = 0; k < N; ++k) cm += p[k];
+    cm /= (double)N;
+    for (int32_t k = 0; k < N; ++k) p[k] -= cm;
+  }
+}
+
+void wln_oracle_gen_dloops(uint64_t seed, int64_t loop0, int64_t n_loops, int32_t N,
+                           double* y, int32_t threads) {
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+  for (int64_t l = 0; l < n_loops; ++l)
+    wln_oracle_dloop(seed, loop0 + l, N, y + (size_t)l * 2 * N);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Wilson loop of one discretised loop at one (rho_cm, T).                  */
 /* ------------------------------------------------------------------------ */
 typedef struct {

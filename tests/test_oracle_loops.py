@@ -24,6 +24,10 @@ from scipy import stats as sst
 
 import oracle
 
+# Both generators must give the law of the discretised closed loop: the
+# increment construction of the hot path and the paper's d-loop (Eqs. yn2, ynk).
+GENERATORS = {"increments": oracle.gen_loops, "dloop": oracle.gen_dloops}
+
 
 def _z_from_raw(seed, n_loops, ppl):
     xi = np.stack([oracle.raw_increments(seed, l, ppl) for l in range(n_loops)])
@@ -43,27 +47,30 @@ def test_box_muller_is_standard_normal():
     assert abs(r) < 5 / math.sqrt(zz[:, 0, :].size)
 
 
+@pytest.mark.parametrize("gen", list(GENERATORS))
 @pytest.mark.parametrize("ppl", [4, 64, 1024])
-def test_loops_closed_and_centred(ppl):
-    y = oracle.gen_loops(3, 50, ppl)
+def test_loops_closed_and_centred(ppl, gen):
+    y = GENERATORS[gen](3, 50, ppl)
     d = np.roll(y, -1, axis=2) - y
     assert np.abs(d.sum(axis=2)).max() < 1e-13
     assert np.abs(y.sum(axis=2)).max() < 1e-15 * ppl * 10
 
 
-def test_two_point_loop_variance():
+@pytest.mark.parametrize("gen", list(GENERATORS))
+def test_two_point_loop_variance(gen):
     # Eq. yn2: with N_1 = 2 the separation has weight exp(-(2/4) 2 dy^2), variance 1/2.
-    y = oracle.gen_loops(5, 40000, 2)
+    y = GENERATORS[gen](5, 40000, 2)
     sep = y[:, :, 1] - y[:, :, 0]
     n = sep.size
     assert abs(sep.var() - 0.5) < 5 * 0.5 * math.sqrt(2.0 / n)
     assert np.allclose(y[:, :, 0], -y[:, :, 1])
 
 
+@pytest.mark.parametrize("gen", list(GENERATORS))
 @pytest.mark.parametrize("ppl", [16, 128])
-def test_midpoint_law_matches_dloop(ppl):
+def test_midpoint_law_matches_dloop(ppl, gen):
     # Eq. ynk at the finest level: y_{2m+1} ~ N((y_{2m} + y_{2m+2})/2, 1/N).
-    y = oracle.gen_loops(9, 8000, ppl)
+    y = GENERATORS[gen](9, 8000, ppl)
     even = y[:, :, 0::2]
     odd = y[:, :, 1::2]
     nxt = np.roll(even, -1, axis=2)
@@ -85,11 +92,12 @@ def _area(y):
     return 0.5 * (x * np.roll(yy, -1, axis=1) - yy * np.roll(x, -1, axis=1)).sum(axis=1)
 
 
+@pytest.mark.parametrize("gen", list(GENERATORS))
 @pytest.mark.parametrize("ppl", [8, 64, 256])
-def test_bridge_moments(ppl):
+def test_bridge_moments(ppl, gen):
     N = ppl
     n_loops = 20000 if ppl <= 64 else 6000
-    y = oracle.gen_loops(21, n_loops, ppl)
+    y = GENERATORS[gen](21, n_loops, ppl)
     d = np.roll(y, -1, axis=2) - y
     v_d = (2.0 / N) * (1.0 - 1.0 / N)
     nd = d.size
@@ -106,9 +114,10 @@ def test_bridge_moments(ppl):
     assert abs(a.mean()) < 5 * math.sqrt(v_a / a.size)
 
 
-def test_every_other_point_is_half_loop():
+@pytest.mark.parametrize("gen", list(GENERATORS))
+def test_every_other_point_is_half_loop(gen):
     N, M = 128, 64
-    y = oracle.gen_loops(31, 10000, N)[:, :, 0::2]
+    y = GENERATORS[gen](31, 10000, N)[:, :, 0::2]
     d = np.roll(y, -1, axis=2) - y
     v_d = (2.0 / M) * (1.0 - 1.0 / M)
     assert abs(d.var() - v_d) < 10 * v_d * math.sqrt(2.0 / d.size)
@@ -123,3 +132,24 @@ def test_loops_are_counter_based():
     assert np.array_equal(a[5:8], b)
     c = oracle.gen_loops(78, 3, 32, loop0=105)
     assert not np.allclose(b, c)
+
+
+def test_dloop_coarse_levels_follow_eq_ynk():
+    # Level k of the d-loop: the points q N/N_k (q odd) about their level-(k-1)
+    # neighbours, residual variance 1/N_k per component.
+    N = 64
+    y = oracle.gen_dloops(41, 8000, N)
+    for Nk in (4, 8, 16):
+        st = N // Nk
+        mid = y[:, :, st::2 * st]
+        nb = y[:, :, 0::2 * st]
+        resid = mid - 0.5 * (nb + np.roll(nb, -1, axis=2))
+        v = resid.var()
+        assert abs(v - 1.0 / Nk) < 5 * (1.0 / Nk) * math.sqrt(2.0 / resid.size)
+
+
+def test_generators_give_the_same_area_law():
+    # two-sample KS of the loop areas of the two constructions
+    a = _area(oracle.gen_loops(51, 6000, 128))
+    b = _area(oracle.gen_dloops(52, 6000, 128))
+    assert sst.ks_2samp(a, b).pvalue > 1e-3
