@@ -134,6 +134,21 @@ wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_l
                          int32_t ppl, int32_t keep_fp64, wln_ensemble** out);
 
 /*
+ * The paper's own generator, d-loops (Sec. "Loop Generation", Eqs. yn2 and
+ * ynk): from the point y_N = y_0, level k (N_k = 2^k points) adds the points
+ * q N/N_k (q odd), each Gaussian about the mean of its two level-(k-1)
+ * neighbours with variance 1/N_k per component; at N_k = ppl the common
+ * centre of mass is removed (step 5).  Same joint law as wln_gen_loops,
+ * different draws: Gaussian number m in creation order (level 1 first, then
+ * q increasing within a level) uses Philox call m/2 with counter
+ * (m/2, loop, 1, 0), (u0,u1) for even m and (u2,u3) for odd m, through the
+ * same Box-Muller.  Arguments, rules and result as wln_gen_loops; the call
+ * needs 16 * 32 * ceil(n_loops/32) * ppl bytes of scratch.
+ */
+wln_status wln_gen_dloops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                          int32_t ppl, int32_t keep_fp64, wln_ensemble** out);
+
+/*
  * Make an ensemble from given loops, e.g. a saved one.  xy is
  * float[n_loops][2][ppl] (x block, then y block of each loop).  It may be host
  * or device memory.  Same rules as wln_gen_loops, and no two consecutive points

@@ -389,6 +389,34 @@ wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_l
   return finish_ensemble(ctx, en, d_deg, out);
 }
 
+wln_status wln_gen_dloops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
+                          int32_t ppl, int32_t keep_fp64, wln_ensemble** out) {
+  if (!ctx || !out) return fail(ctx, WLN_EINVAL, "null argument");
+  *out = nullptr;
+  wln_status st = check_loops(ctx, n_loops, ppl);
+  if (st != WLN_OK) return st;
+  if (loop0 < 0 || loop0 + ((n_loops + 31) / 32) * 32 > (int64_t(1) << 32))
+    return fail(ctx, WLN_EINVAL, "loop0 + n_loops must stay below 2^32 (the Philox counter word)");
+  DeviceGuard guard(ctx->device);
+  wln_ensemble* en = nullptr;
+  if ((st = alloc_ensemble(ctx, n_loops, ppl, keep_fp64 != 0, &en)) != WLN_OK) return st;
+  en->e.loop0 = loop0;
+  Carve cv;
+  const size_t o_deg = cv.take<int>(1);
+  const size_t o_work = cv.take<double>(static_cast<size_t>(en->e.n_blocks) * 32 * 2 * ppl);
+  if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
+  int* d_deg = at<int>(ctx->scratch.ptr, o_deg);
+  cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
+  if (err == cudaSuccess)
+    err = launch_gen_dloops(ctx->stream, seed, en->e, at<double>(ctx->scratch.ptr, o_work), d_deg);
+  ctx->launches += 2;
+  if (err != cudaSuccess) {
+    wln_free_ensemble(ctx, en);
+    return cuda_fail(ctx, err, "launch d-loop generation");
+  }
+  return finish_ensemble(ctx, en, d_deg, out);
+}
+
 wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops, int32_t ppl,
                                   wln_ensemble** out) {
   if (!ctx || !out || !xy) return fail(ctx, WLN_EINVAL, "null argument");

@@ -128,6 +128,62 @@ __global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int64
   }
 }
 
+// d-loops (paper Sec. "Loop Generation", Eqs. yn2 and ynk): from the point
+// y_N = y_0 = 0, level k (N_k = 2^k) adds the points q N/N_k, q odd, each
+// Gaussian about the mean of its two neighbours of the previous level with
+// variance 1/N_k per component; then the centre of mass is removed.
+// Gaussian number m (in creation order) comes from Philox call m/2 with
+// counter (m/2, loop, 1, 0): (u0,u1) for even m, (u2,u3) for odd m.
+// One warp per 32 loops, lane = loop, positions in double in `work`
+// ([block][point][x|y][lane], coalesced); each lane builds its loop level by
+// level (every parent it reads was written by the same lane earlier).
+__global__ void __launch_bounds__(32) gen_dloops_kernel(uint64_t seed, int64_t loop0, int32_t ppl,
+                                                       double* work, float4* blocks, double* xy64,
+                                                       int32_t n_loops) {
+  const int lane = threadIdx.x;
+  const int32_t local = static_cast<int32_t>(blockIdx.x * 32u + lane);
+  const uint32_t loop = static_cast<uint32_t>(loop0 + local);
+  double* W = work + static_cast<size_t>(blockIdx.x) * ppl * 2 * 32 + lane;
+  auto X = [&](int i) -> double& { return W[(2 * i) * 32]; };
+  auto Y = [&](int i) -> double& { return W[(2 * i + 1) * 32]; };
+  X(0) = 0.0;
+  Y(0) = 0.0;
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  int32_t m = 0;
+  uint4 u = make_uint4(0, 0, 0, 0);
+  for (int32_t Nk = 2; Nk <= ppl; Nk *= 2) {
+    const int32_t stride = ppl / Nk;
+    const double sigma = sqrt(1.0 / Nk);
+    for (int32_t q = 1; q < Nk; q += 2, ++m) {
+      if ((m & 1) == 0) u = philox4x32_10(make_uint4(static_cast<uint32_t>(m >> 1), loop, 1u, 0u), k0, k1);
+      const uint32_t ua = (m & 1) ? u.z : u.x, ub = (m & 1) ? u.w : u.y;
+      double sn, cs;
+      const double r = sqrt(-2.0 * log(uniform_open(ua)));
+      sincospi(2.0 * uniform_open(ub), &sn, &cs);
+      const int32_t i = q * stride, left = (q - 1) * stride, right = ((q + 1) * stride) % ppl;
+      X(i) = 0.5 * (X(left) + X(right)) + sigma * (r * cs);
+      Y(i) = 0.5 * (Y(left) + Y(right)) + sigma * (r * sn);
+    }
+  }
+  double cmx = 0.0, cmy = 0.0;
+  for (int32_t i = 0; i < ppl; ++i) cmx += X(i);
+  for (int32_t i = 0; i < ppl; ++i) cmy += Y(i);
+  cmx /= ppl;
+  cmy /= ppl;
+  float4* row = blocks + static_cast<size_t>(blockIdx.x) * (ppl / 2) * 32 + lane;
+  double* ox = xy64 ? xy64 + static_cast<size_t>(local) * 2 * ppl : nullptr;
+  const bool real = local < n_loops;
+  for (int32_t k = 0; k < ppl; k += 2) {
+    const double ax = X(k) - cmx, ay = Y(k) - cmy, bx = X(k + 1) - cmx, by = Y(k + 1) - cmy;
+    row[(k / 2) * 32] = make_float4(__double2float_rn(ax), __double2float_rn(ay),
+                                    __double2float_rn(bx), __double2float_rn(by));
+    if (ox && real) {
+      ox[k] = ax; ox[k + 1] = bx;
+      ox[ppl + k] = ay; ox[ppl + k + 1] = by;
+    }
+  }
+}
+
 // float xy[l][2][N] -> blocks; padding lanes are zero.
 __global__ void pack_kernel(const float* xy, float4* blocks, int32_t n_loops, int32_t ppl,
                             int32_t n_blocks) {
@@ -191,6 +247,17 @@ cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, i
     case 4: gen_loops_kernel<4><<<e.n_blocks, 128, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
     default: return cudaErrorInvalidValue;
   }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
+  degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
+                                                                          e.ppl, d_degenerate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
+                              int* d_degenerate) {
+  gen_dloops_kernel<<<e.n_blocks, 32, 0, s>>>(seed, e.loop0, e.ppl, work, e.blocks, e.xy64, e.n_loops);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);

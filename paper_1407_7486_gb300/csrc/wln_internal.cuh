@@ -135,6 +135,8 @@ ProfileDev profile_constants(const wln_profile& pr, int ppl);
 cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
                                  int32_t n_calls, uint32_t* out);
 cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate);
+cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
+                              int* d_degenerate);
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
 

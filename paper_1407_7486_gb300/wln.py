@@ -38,6 +38,7 @@ SIGNATURES = {
     "wln_launch_count": ([_P], _I64),
     "wln_selftest_wait": ([_P, _I32], ctypes.c_int),
     "wln_gen_loops": ([_P, _U64, _I64, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "wln_gen_dloops": ([_P, _U64, _I64, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
     "wln_ensemble_from_host": ([_P, _P, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
     "wln_free_ensemble": ([_P, _P], ctypes.c_int),
     "wln_ensemble_info": ([_P, _P, _P, _P], ctypes.c_int),
@@ -222,6 +223,14 @@ class Context:
         h = ctypes.c_void_p()
         self._check(load().wln_gen_loops(self.handle, seed, loop0, n_loops, ppl, int(keep_fp64),
                                          ctypes.byref(h)))
+        return Ensemble(self, h.value)
+
+    def gen_dloops(self, seed: int, n_loops: int, ppl: int, keep_fp64: bool = False,
+                   loop0: int = 0) -> Ensemble:
+        """The paper's d-loop construction (same law, other draws)."""
+        h = ctypes.c_void_p()
+        self._check(load().wln_gen_dloops(self.handle, seed, loop0, n_loops, ppl, int(keep_fp64),
+                                          ctypes.byref(h)))
         return Ensemble(self, h.value)
 
     def ensemble_from_host(self, xy) -> Ensemble:

@@ -127,6 +127,21 @@ def test_generated_loops_match_oracle(ctx, n_loops, ppl):
     ens.free()
 
 
+@pytest.mark.parametrize("n_loops,ppl", [(40, 4), (96, 64), (33, 512), (32, 16384)])
+def test_generated_dloops_match_oracle(ctx, n_loops, ppl):
+    ens = ctx.gen_dloops(8, n_loops, ppl, keep_fp64=True, loop0=5)
+    f32, f64 = ctx.loops_copy(ens, f32=True, f64=True)
+    ref = oracle.gen_dloops(8, n_loops, ppl, loop0=5)
+    assert np.abs(f64 - ref).max() < 1e-13
+    ref32 = ref.astype(np.float32)
+    diff = f32 != ref32
+    assert diff.mean() < 1e-4
+    if diff.any():
+        ulp = np.spacing(np.abs(ref32[diff]))
+        assert np.all(np.abs(f32[diff] - ref32[diff]) <= ulp)
+    ens.free()
+
+
 CASES = [
     # (n_loops, ppl, G, profile, rho, T)
     (96, 64, 3, I.Profile(0, F=10.0, lam=1.0), I.lin_grid(0.0, 5.0, 7), I.log_grid(0.01, 10.0, 5)),
