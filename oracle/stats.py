@@ -144,3 +144,57 @@ def effective_action(S, loops_per_group, profile, rho, T, spinor=True):
     g = effective_action_groups(S, loops_per_group, profile, rho, T, spinor)
     G = len(g)
     return g.mean(), math.sqrt(((g - g.mean()) ** 2).sum() / (G * (G - 1)))
+
+
+# --------------------------------------------------------------------------
+# Discretisation levels (Sec. "Estimating the Discretization Uncertainties").
+# --------------------------------------------------------------------------
+EXTRAPOLATION = (8.0 / 3.0, -2.0, 1.0 / 3.0)   # weights of W_N, W_N/2, W_N/4
+
+
+def level_terms(phase_o, spin_o, phase_sq, spin_sq, phase_tr, spin_tr):
+    """Per-loop W - 1 (scalar, spinor) at the paper's three levels from the
+    integrals over the three interleaved sub-loops (circle: even points, N/2;
+    square: points 1 mod 4, N/4; triangle: points 3 mod 4, N/4):
+      W_N/4 = e^{i (tri + sq)/2},  W_N/2 = e^{i circ},
+      W_N   = e^{i circ/2} e^{i sq/4} e^{i tri/4};
+    the spin integrals are combined with the same weights.  Returns
+    [n][6] = (scal_N, ferm_N, scal_N/2, ferm_N/2, scal_N/4, ferm_N/4)."""
+    lv = [(phase_o / 2 + phase_sq / 4 + phase_tr / 4, spin_o / 2 + spin_sq / 4 + spin_tr / 4),
+          (phase_o, spin_o),
+          ((phase_sq + phase_tr) / 2, (spin_sq + spin_tr) / 2)]
+    out = []
+    for ph, sp in lv:
+        h = np.sin(0.5 * ph)
+        scal = -2.0 * h * h
+        sh = np.sinh(0.5 * sp)
+        out += [scal, np.cos(ph) * 2.0 * sh * sh + scal]
+    return np.stack(out, axis=-1)
+
+
+def level_sums(oracle_mod, y, profile, rho, T, n_groups, threads=0):
+    """Group sums [n_T * n_rho][G][6] of level_terms (rho fastest), with the
+    sub-loop integrals from the oracle's closed-form phase and spin of each
+    sub-loop (a closed polygon through its points, each segment taking proper
+    time T/N', N' its point count)."""
+    y = np.ascontiguousarray(y, np.float64)
+    subs = [np.ascontiguousarray(y[:, :, 0::2]), np.ascontiguousarray(y[:, :, 1::4]),
+            np.ascontiguousarray(y[:, :, 3::4])]
+    n = y.shape[0]
+    lpg = n // n_groups
+    out = np.zeros((len(T) * len(rho), n_groups, 6))
+    for b, t in enumerate(T):
+        for a, r in enumerate(rho):
+            ps = [oracle_mod.phase_spin(sub, profile, r, t, threads) for sub in subs]
+            w = level_terms(ps[0][0], ps[0][1], ps[1][0], ps[1][1], ps[2][0], ps[2][1])
+            out[b * len(rho) + a] = w.reshape(n_groups, lpg, 6).sum(axis=1)
+    return out
+
+
+def extrapolate(level_S):
+    """Group sums of W_inf - 1 and of |W_N - W_inf| per (point, group) from
+    level sums: the quadratic in 1/N through W_N, W_N/2, W_N/4 evaluated at
+    1/N = 0 (the weights sum to one, so W - 1 sums combine the same way).
+    Returns [n_points][G][2] (scalar, spinor) of extrapolated W - 1 sums."""
+    a, b, c = EXTRAPOLATION
+    return a * level_S[:, :, 0:2] + b * level_S[:, :, 2:4] + c * level_S[:, :, 4:6]

@@ -125,3 +125,64 @@ def test_flux_tube_field_matches_eq_bwln():
     got = ost.eB_profile(Profile(PROFILE_FLUX_TUBE, F=F, lam=lam), rho)
     want = np.array([Bf(max(x, 1e-12)) for x in rho])
     assert np.allclose(got, want, rtol=1e-12)
+
+
+def test_extrapolation_weights_are_the_quadratic_in_one_over_N():
+    # Lagrange interpolation in x = 1/N through N, N/2, N/4, evaluated at x = 0
+    N = 512.0
+    xs = np.array([1 / N, 2 / N, 4 / N])
+    for coeffs in ([1.0, 0.0, 0.0], [0.3, -2.0, 5.0], [1.0, 7.0, -40.0]):
+        f = np.polyval(coeffs[::-1], xs)        # f(x) = c0 + c1 x + c2 x^2
+        got = np.dot(ost.EXTRAPOLATION, f)
+        assert got == pytest.approx(coeffs[0], rel=1e-12, abs=1e-12)
+    assert sum(ost.EXTRAPOLATION) == pytest.approx(1.0)
+
+
+def test_half_loop_level_matches_exact_constant_field_average():
+    import oracle
+    from paper_1407_7486_gb300.inputs import PROFILE_CONST_B
+    # the circle sub-loop (every other point) is an N/2-point loop, so in a
+    # constant field <W_N/2> is the exact finite-N average at N/2 points
+    N, n_loops, G, b = 64, 12800, 32, 1.5
+    y = oracle.gen_loops(61, n_loops, N)
+    L = ost.level_sums(oracle, y, Profile(PROFILE_CONST_B, B=b), [0.0], [1.0], G)
+    m, e = ost.mean_sem(L, n_loops // G, 2)
+    k = np.arange(1, N // 2)
+    exact = float(np.prod((1.0 + (b / ((N // 2) * np.tan(np.pi * k / (N // 2)))) ** 2) ** -0.5))
+    assert abs(1.0 + m[0] - exact) < 5 * e[0]
+
+
+def _regular_polygon(n, R):
+    k = np.arange(n)
+    return np.stack([R * np.cos(2 * np.pi * k / n), R * np.sin(2 * np.pi * k / n)])[None]
+
+
+def test_levels_of_a_regular_polygon_in_a_constant_field():
+    import oracle
+    from paper_1407_7486_gb300.inputs import PROFILE_CONST_B
+    # the sub-loops of a regular 16-gon are a regular 8-gon (even points) and
+    # two regular 4-gons (1 mod 4, 3 mod 4); in a constant field each phase
+    # is B times the enclosed area (n/2) R^2 sin(2 pi/n), each spin is B T
+    R, B, T = 0.6, 1.7, 1.0
+    y = _regular_polygon(16, R)
+    area = lambda n: 0.5 * n * R * R * np.sin(2 * np.pi / n)
+    L = ost.level_sums(oracle, y, Profile(PROFILE_CONST_B, B=B), [0.0], [T], 1)[0, 0]
+    phases = [B * (area(8) / 2 + area(4) / 4 + area(4) / 4), B * area(8), B * area(4)]
+    for lv, ph in enumerate(phases):
+        assert L[2 * lv] == pytest.approx(np.cos(ph) - 1.0, rel=1e-12, abs=1e-14)
+        assert L[2 * lv + 1] == pytest.approx(np.cos(ph) * np.cosh(B * T) - 1.0, rel=1e-12)
+
+
+def test_levels_of_a_wide_flux_tube_approach_the_constant_field():
+    import oracle
+    from paper_1407_7486_gb300.inputs import PROFILE_CONST_B
+    # near the axis of a tube much wider than the loop the field is uniform,
+    # e B = F / (pi lambda^2); the sub-loop spins then sum T/N' per segment to
+    # B T on every sub-loop (a wrong proper time per segment scales them by
+    # N'/N), and the phases approach B times the areas
+    lam, Beff, T = 1.0e3, 0.7, 1.3
+    F = Beff * np.pi * lam * lam
+    y = oracle.gen_loops(3, 4, 64)
+    tube = ost.level_sums(oracle, y, Profile(0, F=F, lam=lam), [0.0], [T], 4)
+    const = ost.level_sums(oracle, y, Profile(PROFILE_CONST_B, B=Beff), [0.0], [T], 4)
+    np.testing.assert_allclose(tube, const, rtol=1e-5, atol=1e-9)
