@@ -22,6 +22,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -65,10 +66,11 @@ def _kernel_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _ncu_traffic(workload: str):
-    """DRAM bytes per Wilson launch from the committed ncu summary, or None when
-    the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", f"wilson_kernel_{workload}.md")
+def _ncu_traffic(summary: str):
+    """DRAM bytes per Wilson launch from the committed ncu summary
+    profiles/<summary>.md, or None when the kernel source changed since the
+    capture."""
+    path = os.path.join(ROOT, "profiles", f"{summary}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -87,7 +89,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # WLN_CLOCKS_DIR keeps the raw samples somewhere the caller chooses.
+        d = os.environ.get("WLN_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -157,9 +161,10 @@ def _max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", cov: bool = True):
+def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", cov: bool = True,
+             loop0: int = 0):
     """One pass of the path; returns (outputs, h2d_bytes, d2h_bytes)."""
-    ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
+    ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
     S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec, where=where)
     lpg = wl.n_loops // wl.n_groups
     outs = {"S": S}
@@ -196,8 +201,8 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     threads = oracle.max_threads()
     q = 1 if len(wl.profiles) > 1 else 0
     prof = wl.profiles[q]
-    rho = wl.rho[q][::8]
-    T = wl.T[q][::8]
+    rho = wl.rho[q][::4]
+    T = wl.T[q][::4]
     lpg = wl.n_loops // wl.n_groups
     # calibrate on one group at every sampled point (enough (point, group) pairs for all threads)
     y = oracle.gen_loops(wl.seed, lpg, wl.ppl).astype(np.float32).astype(np.float64)
@@ -222,7 +227,7 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
                      "ferm_max_rel_to_max(1,|<W>-1|)": float(rel.max())}
     ens.free()
     return {"value": lp / dt, "unit": "loop-point evals/s", "cores": threads, "kind": "oracle",
-            "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every 8th), "
+            "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every 4th), "
                       f"{n_groups * lpg} loops ({n_groups} groups) x {wl.ppl} ppl; {dt:.1f} s",
             "gpu_error_vs_oracle_on_sample": err}
 
@@ -275,6 +280,8 @@ def main():
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--rate-scales", default="sat",
                     help="comma list: 'sat' (2000 req/s) and/or fractions of measured capacity")
+    ap.add_argument("--levels", action="store_true",
+                    help="time the discretisation-level pass (N, N/2, N/4) and extrapolation")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -290,6 +297,8 @@ def main():
         return run_serve(args)
     if args.workload == "batched":
         return run_batched(args, wl)
+    if args.levels:
+        return run_levels(args, wl)
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -301,12 +310,14 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
     ctx = wln.Context(dev, stream)
-    seed = wl.seed + rank       # weak scaling: every rank its own ensemble
+    # weak scaling: rank r holds loops [r N_l, (r+1) N_l) of one ensemble (the
+    # Philox counter is the global loop index), so N ranks evaluate N N_l loops
+    seed, loop0 = wl.seed, rank * wl.n_loops
 
     # warm-up (compiles nothing; fills caches, grows scratch)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            run_step(ctx, wl, seed, args.prec)
+            run_step(ctx, wl, seed, args.prec, loop0=loop0)
     stream.synchronize()
 
     # device-resident timed region
@@ -319,7 +330,7 @@ def main():
     with ClockSampler(dev) as clk, torch.cuda.stream(stream):
         e0.record(stream)
         for i in range(args.steps):
-            ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl)
+            ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
             wk[i][0].record(stream)
             S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
             wk[i][1].record(stream)
@@ -350,7 +361,7 @@ def main():
     h2d = d2h = 0
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
-            _, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True)
+            _, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True, loop0=loop0)
     stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _max_over_ranks(e2e_s, ws)
@@ -367,7 +378,7 @@ def main():
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
     seg = wl.segment_evals
     achieved = N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12
-    traffic = _ncu_traffic(args.workload)
+    traffic = _ncu_traffic(f"wilson_kernel_{args.workload}")
     line = {
         "metric": METRIC, "value": value, "unit": "loop-point evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -471,6 +482,111 @@ def run_batched(args, wl: I.Workload):
     line["autotune_candidates"] = tuned.get("candidates")
     line["finite_gamma"] = bool(np.isfinite(g).all())
     b.free(); ens.free(); ctx.close()
+    print(json.dumps(line))
+
+
+def run_levels(args, wl: I.Workload):
+    """Discretisation levels (Sec. "Estimating the Discretization
+    Uncertainties"): per step, draw the ensemble, walk the three interleaved
+    sub-loops of every loop at every point (one pass, N segments per loop and
+    point), and extrapolate every point to infinitely many points per loop
+    with its group error and discretisation uncertainty."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    import oracle
+    from oracle import stats as ost
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    lpg = wl.n_loops // wl.n_groups
+
+    def step(where="device"):
+        ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+        L = ctx.wilson_levels(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec,
+                              where=where)
+        X = ctx.extrapolate(L, wl.n_groups, lpg, where=where)
+        ens.free()
+        return L, X
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        n0 = ctx.launch_count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for i in range(args.steps):
+                ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+                wk[i][0].record(stream)
+                L = ctx.wilson_levels(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+                wk[i][1].record(stream)
+                X = ctx.extrapolate(L, wl.n_groups, lpg)
+                ens.free()
+            e1.record(stream)
+            stream.synchronize()
+        launches = ctx.launch_count - n0
+        ms = e0.elapsed_time(e1) / args.steps
+        kern_ms = statistics.mean(a.elapsed_time(b) for a, b in wk)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 2))
+        for _ in range(e2e_steps):
+            Lh, Xh = step(where="host")
+        stream.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(r.nbytes + t.nbytes for r, t in zip(wl.rho, wl.T)) + Lh.nbytes
+    d2h = Lh.nbytes + Xh.nbytes
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    seg = wl.segment_evals            # circle N/2 + square N/4 + triangle N/4 = N per loop and point
+    achieved = N_ALG_FP32 * seg / (kern_ms / 1e3) / 1e12
+    line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation)",
+                        wl.loop_points / (ms / 1e3), "loop-point evals/s", args.steps,
+                        args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
+                        {"workload": wl.name, "n_loops": wl.n_loops, "ppl": wl.ppl,
+                         "n_points": wl.n_points, "n_groups": wl.n_groups,
+                         "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                        "unit": "T FP32 op/s", "frac": achieved / peak_ops,
+                        "traffic": _ncu_traffic(f"wilson_levels_{args.workload}"),
+                        "kernel": "wilson_kernel<F32Comp,4,8,levels>", "kernel_ms": kern_ms,
+                        "segment_evals_per_s": seg / (kern_ms / 1e3),
+                        "n_alg_fp32_per_segment": N_ALG_FP32,
+                        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                      f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
+    line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clk.summary()
+    # the extrapolation on the workload: spread of delta against the group error
+    Xa = Xh.reshape(-1, 2, 6)
+    line["discretisation"] = {
+        "median_delta_over_sem_spinor": float(np.median(Xa[:, 1, 5] / np.maximum(Xa[:, 1, 4], 1e-300))),
+        "median_delta_over_sem_scalar": float(np.median(Xa[:, 0, 5] / np.maximum(Xa[:, 0, 4], 1e-300)))}
+    if not args.no_cpu_baseline:
+        q = 1 if len(wl.profiles) > 1 else 0
+        prof, rho, T = wl.profiles[q], wl.rho[q][::4], wl.T[q][::4]
+        y = oracle.gen_loops(wl.seed, wl.n_loops, wl.ppl).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        ref = ost.level_sums(oracle, y, prof, rho, T, wl.n_groups, threads=oracle.max_threads())
+        dt = time.perf_counter() - t0
+        ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+        G = ctx.wilson_levels(ens, [prof], [rho], [T], wl.n_groups, prec=args.prec, where="host")
+        ens.free()
+        line["cpu_baseline"] = {
+            "value": wl.n_loops * len(rho) * len(T) / dt, "unit": "loop-point evals/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"F={prof.F}, {len(rho)} rho x {len(T)} T (every 4th), all {wl.n_loops} "
+                      f"loops x {wl.ppl} ppl, levels; {dt:.1f} s",
+            "gpu_error_vs_oracle_on_sample": {
+                "scal_max_abs": float(np.abs(G - ref)[:, :, 0::2].max() / lpg),
+                "ferm_max_rel_to_max(1,|<W>-1|)": float(
+                    (np.abs(G - ref)[:, :, 1::2] / np.maximum(np.abs(ref[:, :, 1::2]), lpg)).max())}}
+    ctx.close()
     print(json.dumps(line))
 
 

@@ -85,6 +85,18 @@ enum {
   WLN_C_FERM_SQ = 4   /* sum of (W_ferm - 1)^2 */
 };
 
+/* Components of a discretisation-level group sum (WLN_KL per point and
+ * group; see wln_wilson_levels): W - 1 at N, N/2 and N/4 points per loop. */
+#define WLN_KL 6
+enum {
+  WLN_L_SCAL_N = 0,   /* sum of (W_scal - 1) at level N */
+  WLN_L_FERM_N = 1,   /* sum of (W_ferm - 1) at level N */
+  WLN_L_SCAL_N2 = 2,  /* level N/2 */
+  WLN_L_FERM_N2 = 3,
+  WLN_L_SCAL_N4 = 4,  /* level N/4 */
+  WLN_L_FERM_N4 = 5
+};
+
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
@@ -235,6 +247,28 @@ wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* ens,
                                   const double* T, const int32_t* T_off,
                                   int32_t n_groups, wln_prec prec, double* group_sums);
 
+/*
+ * Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
+ * every loop of N points is split into three interleaved closed sub-loops,
+ *   circle:   points 0, 2, 4, ...          (N/2 points)
+ *   square:   points 1, 5, 9, ... (1 mod 4) (N/4 points)
+ *   triangle: points 3, 7, 11, ... (3 mod 4) (N/4 points)
+ * each walked like a loop in wln_wilson_avg (straight segments, exact
+ * integrals, proper time T/N' per segment for N' points; the same centre of
+ * mass, no re-centring).  With o, s, t the phases of the three sub-loops,
+ *   W_N/4 = e^{i (t + s)/2},  W_N/2 = e^{i o},  W_N = e^{i o/2} e^{i s/4} e^{i t/4},
+ * and the spin integrals combine with the same weights (W_ferm = cos(phase)
+ * cosh(spin) at each level).  group_sums: double[n_points][n_groups][WLN_KL]
+ * (see WLN_L_*), host or device.  Arguments and rules as wln_wilson_avg, and
+ * the ensemble's ppl must be a multiple of 4 and at least 8.  The pass costs
+ * about what wln_wilson_avg does (N segments per loop and point).
+ */
+wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens,
+                             const wln_profile* profiles, int32_t n_profiles,
+                             const double* rho_cm, const int32_t* rho_off,
+                             const double* T, const int32_t* T_off,
+                             int32_t n_groups, wln_prec prec, double* group_sums);
+
 /* -------------------------------------------------------------- statistics */
 
 /*
@@ -264,6 +298,23 @@ wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_point
 wln_status wln_loop_sem(wln_ctx* ctx, const double* group_sums, int32_t n_points,
                         int32_t n_groups, int32_t n_loops, int32_t comp_sum,
                         int32_t comp_sq, double* out);
+
+/*
+ * Extrapolation to infinitely many points per loop and the discretisation
+ * uncertainty (Sec. "Estimating the Discretization Uncertainties"), from the
+ * level sums of wln_wilson_levels.  For x in (scalar, spinor) and each point:
+ *   m_L = mean over all loops of W - 1 at level L in (N, N/2, N/4);
+ *   W_inf - 1 = 8/3 m_N - 2 m_N/2 + 1/3 m_N/4 (the parabola in 1/N through
+ *   the three levels, taken at 1/N = 0);
+ *   sem_inf = the group standard error of that combination (it is linear, so
+ *   each group's extrapolation is the combination of its means);
+ *   delta = |m_N - (W_inf - 1)|, the paper's discretisation uncertainty.
+ * out: double[n_points][2][6] = (m_N, m_N/2, m_N/4, W_inf - 1, sem_inf,
+ * delta) for the scalar, then the spinor loop.  level_sums and out host or
+ * device.
+ */
+wln_status wln_extrapolate(wln_ctx* ctx, const double* level_sums, int32_t n_points,
+                           int32_t n_groups, int32_t loops_per_group, double* out);
 
 /*
  * Effective-action density per group and its group mean and standard error

@@ -512,25 +512,35 @@ wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t
   return WLN_OK;
 }
 
-wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
-                          int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
-                          const double* T, const int32_t* T_off, int32_t n_groups,
-                          wln_prec prec, double* group_sums) {
+}  // extern "C"
+
+namespace wln {
+namespace {
+
+// Group sums of one Wilson pass: the plain sums (WLN_K components) or the
+// discretisation levels (WLN_KL components).
+wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                       int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                       const double* T, const int32_t* T_off, int32_t n_groups,
+                       wln_prec prec, double* group_sums, bool levels) {
   if (!ctx || !ens || !group_sums) return fail(ctx, WLN_EINVAL, "null argument");
   if (prec != WLN_PREC_FP64 && prec != WLN_PREC_FP32_COMP && prec != WLN_PREC_FP32_NAIVE)
     return fail(ctx, WLN_EINVAL, "unknown precision");
   if (ens->device != ctx->device) return fail(ctx, WLN_EINVAL, "ensemble lives on another device");
   if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
     return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
+  if (levels && (ens->e.ppl % 4 != 0 || ens->e.ppl < 8))
+    return fail(ctx, WLN_EINVAL, "discretisation levels need ppl a multiple of 4 and >= 8");
   wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
   if (st != WLN_OK) return st;
   DeviceGuard guard(ctx->device);
+  const int K = levels ? WLN_KL : WLN_K;
 
   Batch bt;
-  const int P = plan_points_per_lane(ctx, prec);
+  const int P = plan_points_per_lane(ctx, prec, levels);
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl, P, bt);
   if (bt.n_points > (int64_t(1) << 31) - 1) return fail(ctx, WLN_EINVAL, "too many points");
-  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec);
+  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, levels);
 
   // Device layout of this call: work list | profiles | radii | partials | (host output)
   Carve cv;
@@ -538,9 +548,9 @@ wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profi
   const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
   const size_t o_rho = cv.take<double>(bt.rho.size());
   const size_t upload = cv.off;
-  const size_t n_partial = static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * WLN_K;
+  const size_t n_partial = static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
   const size_t o_part = cv.take<double>(n_partial);
-  Out out = plan_out(cv, group_sums, static_cast<size_t>(bt.n_points) * n_groups * WLN_K);
+  Out out = plan_out(cv, group_sums, static_cast<size_t>(bt.n_points) * n_groups * K);
   if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) return st;
   if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
   bind_out(out, ctx->scratch.ptr);
@@ -569,6 +579,58 @@ wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profi
     if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy group sums");
     return check_flag(ctx);
   }
+  return WLN_OK;
+}
+
+}  // namespace
+}  // namespace wln
+
+extern "C" {
+
+wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                          int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                          const double* T, const int32_t* T_off, int32_t n_groups,
+                          wln_prec prec, double* group_sums) {
+  return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
+                     group_sums, false);
+}
+
+wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                             int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                             const double* T, const int32_t* T_off, int32_t n_groups,
+                             wln_prec prec, double* group_sums) {
+  return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
+                     group_sums, true);
+}
+
+wln_status wln_extrapolate(wln_ctx* ctx, const double* level_sums, int32_t n_points,
+                           int32_t n_groups, int32_t loops_per_group, double* out) {
+  if (!ctx || !level_sums || !out) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_points < 1 || n_groups < 2 || loops_per_group < 1)
+    return fail(ctx, WLN_EINVAL, "bad extrapolation sizes");
+  DeviceGuard guard(ctx->device);
+  const size_t nS = static_cast<size_t>(n_points) * n_groups * WLN_KL;
+  const bool s_dev = is_device_ptr(level_sums);
+  Carve cv;
+  const size_t o_S = s_dev ? 0 : cv.take<double>(nS);
+  Out oo = plan_out(cv, out, static_cast<size_t>(n_points) * 12);
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(oo, ctx->scratch.ptr);
+  const double* S = level_sums;
+  cudaError_t err = cudaSuccess;
+  if (!s_dev) {
+    double* dS = at<double>(ctx->scratch.ptr, o_S);
+    err = cudaMemcpyAsync(dS, level_sums, nS * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    S = dS;
+  }
+  if (err == cudaSuccess)
+    err = launch_extrapolate(ctx->stream, S, n_points, n_groups, loops_per_group,
+                             static_cast<double*>(oo.dev));
+  ++ctx->launches;
+  if (err == cudaSuccess) err = copy_back(oo, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "extrapolation");
+  if (oo.host || !s_dev) return check_flag(ctx);
   return WLN_OK;
 }
 

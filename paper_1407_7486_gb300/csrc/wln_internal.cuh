@@ -71,6 +71,7 @@ struct WilsonPlan {
   int n_chains;       // ceil(n_blocks / chain)
   int64_t n_items;    // n_chains * n_tile_groups
   int grid;           // persistent CTAs
+  bool levels;        // discretisation-level pass (WLN_KL components)
 };
 
 struct Scratch {
@@ -141,8 +142,10 @@ cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
 
 // Wilson loops (wln_wilson.cu).
-WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec);
-int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec);
+// levels: the discretisation-level pass (K = WLN_KL components per point).
+WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
+                     bool levels = false);
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, bool levels = false);
 cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
@@ -156,6 +159,8 @@ cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const
 cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
                              int32_t lpg, int32_t comp, double* mean, double* sem,
                              double* jk_var, double* dev_scratch, double* cov, int64_t* launches);
+cudaError_t launch_extrapolate(cudaStream_t s, const double* level_sums, int32_t n_points,
+                               int32_t G, int32_t lpg, double* out);
 cudaError_t launch_loop_sem(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
                             int32_t n_loops, int32_t comp_sum, int32_t comp_sq, double* out);
 

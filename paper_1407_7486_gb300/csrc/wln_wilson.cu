@@ -26,6 +26,15 @@
 // chain in L2.  W terms are reduced over lanes (and blocks) in FP64 in a
 // fixed order into per-(chain, group) partials; a second kernel sums the
 // partials of each group in chain order.
+//
+// Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
+// the same pass can instead walk the three interleaved sub-loops of every
+// loop -- circle (even points, N/2 of them), square (points 1 mod 4) and
+// triangle (points 3 mod 4), N/4 each -- as closed polygons with proper time
+// T/N' per segment, and combine their phases and spins into W at the levels
+// N, N/2 and N/4.  A staged row (points 2i, 2i+1) feeds the circle with its
+// even point and the square (i even) or the triangle (i odd) with its odd
+// point, so the levels cost the same N segments per loop and radius.
 #include <cfloat>
 
 #include "wln_internal.cuh"
@@ -34,6 +43,7 @@ namespace wln {
 namespace {
 
 constexpr int kComps = WLN_K;
+constexpr int kLevelComps = WLN_KL;
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -420,24 +430,58 @@ __device__ __forceinline__ void issue_next(const KParams& k, Pipe& pp, int slot)
   }
 }
 
+// Phase and spin sums of one walk at radius p, as true sums (s - c) in
+// double; the spin scaled by m (the walk's N / N').
+template <class WalkT>
+__device__ __forceinline__ void walk_sums(const WalkT& w, int p, double m, double& ph,
+                                          double& sp) {
+  double ps, pc, ss, sc;
+  w.raw(p, ps, pc, ss, sc);
+  ph = ps - pc;
+  sp = (ss - sc) * m;
+}
+
+// W - 1 (scalar, spinor) of one level from its phase and spin sums.  The
+// float flavours take the sums as a float pair (hi - lo = the double sum).
+template <class A>
+__device__ __forceinline__ void level_terms(double ph, double sp, F2 tp, F2 st, double tp_d,
+                                            double st_d, double* out) {
+  double w[kComps];
+  if constexpr (sizeof(typename A::F) == 8) {
+    wilson_terms<A>(ph, 0.0, sp, 0.0, tp, st, tp_d, st_d, w);
+  } else {
+    const float ph_hi = static_cast<float>(ph), sp_hi = static_cast<float>(sp);
+    wilson_terms<A>(ph_hi, static_cast<float>(static_cast<double>(ph_hi) - ph), sp_hi,
+                    static_cast<float>(static_cast<double>(sp_hi) - sp), tp, st, tp_d, st_d, w);
+  }
+  out[0] = w[0];
+  out[1] = w[1];
+}
+
 // One work item for one warp: its tile against every loop of the chain.
 // Per-lane W terms are added into the warp's shared-memory accumulators
 // acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
 // flush sums each row over the lanes in lane order and writes the partial
-// of (chain, group).
-template <class A, int P, class WalkT>
+// of (chain, group).  LV selects the discretisation levels (K = WLN_KL):
+// walks w[0..2] are the circle, square and triangle sub-loops.
+template <class A, int P, class WalkT, bool LV>
 __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const Tile& tile,
                          const ProfileDev& prof, bool active, volatile int* abort_flag,
                          int lane) {
   using F = typename A::F;
-  constexpr int V = P * kComps;
-  WalkT wk;
-  wk.s = static_cast<F>(sqrt(tile.T));
-  wk.l2 = static_cast<F>(prof.l2);
+  constexpr int K = LV ? kLevelComps : kComps;
+  constexpr int NW = LV ? 3 : 1;
+  constexpr int V = P * K;
+  WalkT w[NW];
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    const int i = p < tile.n_valid ? p : (tile.n_valid > 0 ? tile.n_valid - 1 : 0);
-    wk.rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
+  for (int q = 0; q < NW; ++q) {
+    w[q].s = static_cast<F>(sqrt(tile.T));
+    w[q].l2 = static_cast<F>(prof.l2);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int i = p < tile.n_valid ? p : (tile.n_valid > 0 ? tile.n_valid - 1 : 0);
+      w[q].rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
+    }
   }
   const double st_d = prof.spin_per * tile.T;
   const F2 tp = split(prof.turns_per), st = split(st_d);
@@ -449,13 +493,13 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     __syncwarp();
     if (active) {
       double* dst = k.partial + tile.part_base +
-                    (static_cast<size_t>(c + g) * tile.part_stride + tile.p0) * kComps;
+                    (static_cast<size_t>(c + g) * tile.part_stride + tile.p0) * K;
       for (int j = lane; j < V; j += 32) {
         double sum = 0.0;
         const double* row = acc + j * 33;
 #pragma unroll 8
         for (int l = 0; l < 32; ++l) sum += row[l];
-        if (j / kComps < tile.n_valid) dst[j] = sum;
+        if (j / K < tile.n_valid) dst[j] = sum;
       }
     }
     __syncwarp();
@@ -467,7 +511,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   for (int b = b0; b < b1; ++b) {
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
-    float fx = 0.f, fy = 0.f;  // the loop's first point, for the closing segment
+    // first point of each walk, for the closing segments
+    float fx[NW], fy[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) { fx[q] = 0.f; fy[q] = 0.f; }
     for (int ch = 0; ch < pp.chunks_per_block; ++ch) {
       const int slot = static_cast<int>(pp.kc % pp.stages);
       const uint32_t parity = static_cast<uint32_t>((pp.kc / pp.stages) & 1);
@@ -478,19 +525,45 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       }
       const float4* rowp = pp.ring + static_cast<size_t>(slot) * pp.chunk_rows * 32 + lane;
       if (active) {
-        int r = 0;
-        if (ch == 0) {
-          const float4 v = rowp[0];
-          fx = v.x; fy = v.y;
-          wk.start(v.x, v.y);
-          wk.step(v.z, v.w);
-          r = 1;
-        }
-        for (; r < pp.chunk_rows; ++r) {
-          const float4 v = rowp[r * 32];
-          wk.step(v.x, v.y);
-          wk.step(v.z, v.w);
-          if ((r & 3) == 3) wk.fold();   // every 8 segments
+        if constexpr (!LV) {
+          int r = 0;
+          if (ch == 0) {
+            const float4 v = rowp[0];
+            fx[0] = v.x; fy[0] = v.y;
+            w[0].start(v.x, v.y);
+            w[0].step(v.z, v.w);
+            r = 1;
+          }
+          for (; r < pp.chunk_rows; ++r) {
+            const float4 v = rowp[r * 32];
+            w[0].step(v.x, v.y);
+            w[0].step(v.z, v.w);
+            if ((r & 3) == 3) w[0].fold();   // every 8 segments
+          }
+        } else {
+          // Rows come in pairs (chunk_rows is even): row r even holds points
+          // 2r (circle) and 2r + 1 = 1 mod 4 (square), row r + 1 holds
+          // 2r + 2 (circle) and 2r + 3 = 3 mod 4 (triangle).
+          int r = 0;
+          if (ch == 0) {
+            const float4 a = rowp[0], v = rowp[32];
+            fx[0] = a.x; fy[0] = a.y; fx[1] = a.z; fy[1] = a.w; fx[2] = v.z; fy[2] = v.w;
+            w[0].start(a.x, a.y);
+            w[1].start(a.z, a.w);
+            w[0].step(v.x, v.y);
+            w[2].start(v.z, v.w);
+            r = 2;
+          }
+          for (; r < pp.chunk_rows; r += 2) {
+            const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+            w[0].step(a.x, a.y);
+            w[1].step(a.z, a.w);
+            w[0].step(v.x, v.y);
+            w[2].step(v.z, v.w);
+            if ((r & 7) == 6) {   // every 8 circle segments
+              w[0].fold(); w[1].fold(); w[2].fold();
+            }
+          }
         }
       }
       __syncwarp();
@@ -508,8 +581,11 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       if (*abort_flag) return false;
     }
     if (!active) continue;
-    wk.step(fx, fy);  // closing segment r_{N-1} -> r_0
-    wk.fold();
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      w[q].step(fx[q], fy[q]);  // closing segment back to the walk's first point
+      w[q].fold();
+    }
     const int g_lane = valid ? loop / k.lpg : -1;
     const int g_lo = (b * 32) / k.lpg;
     const int g_hi = min(b * 32 + 31, k.n_loops - 1) / k.lpg;
@@ -518,12 +594,37 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       const bool mine = g_lane == g;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        double ps, pc, ss, sc, w[kComps];
-        wk.raw(p, ps, pc, ss, sc);
-        wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, w);
+        if constexpr (!LV) {
+          double ps, pc, ss, sc, t[K];
+          w[0].raw(p, ps, pc, ss, sc);
+          wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, t);
 #pragma unroll
-        for (int q = 0; q < kComps; ++q)
-          if (mine) acc[(p * kComps + q) * 33 + lane] += w[q];
+          for (int q = 0; q < K; ++q)
+            if (mine) acc[(p * K + q) * 33 + lane] += t[q];
+        } else {
+          // Spin per segment is T/N' on a sub-loop of N' points: the circle's
+          // sums count twice, the square's and triangle's four times, of the
+          // full loop's T/N (a constant field's spin is B T on every loop).
+          const bool tube = prof.kind != WLN_PROFILE_CONST_B;
+          double po, so, pq, sq, pt, stt;
+          walk_sums(w[0], p, tube ? 2.0 : 1.0, po, so);
+          walk_sums(w[1], p, tube ? 4.0 : 1.0, pq, sq);
+          walk_sums(w[2], p, tube ? 4.0 : 1.0, pt, stt);
+          // W_N = e^{i (circ/2 + sq/4 + tri/4)}, W_N/2 = e^{i circ},
+          // W_N/4 = e^{i (sq + tri)/2}; the spins combine the same way.  One
+          // copy of the W arithmetic serves the three levels (registers).
+#pragma unroll 1
+          for (int L = 0; L < 3; ++L) {
+            const double ph = L == 0 ? 0.5 * po + 0.25 * (pq + pt) : (L == 1 ? po : 0.5 * (pq + pt));
+            const double sp = L == 0 ? 0.5 * so + 0.25 * (sq + stt) : (L == 1 ? so : 0.5 * (sq + stt));
+            double t[2];
+            level_terms<A>(ph, sp, tp, st, prof.turns_per, st_d, t);
+            if (mine) {
+              acc[(p * K + 2 * L) * 33 + lane] += t[0];
+              acc[(p * K + 2 * L + 1) * 33 + lane] += t[1];
+            }
+          }
+        }
       }
     }
   }
@@ -531,8 +632,12 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   return true;
 }
 
-template <class A, int P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(const KParams k) {
+// The plain pass keeps 16 warps per SM (at most 128 registers a thread); the
+// level pass holds three walks per radius and runs 8 warps per SM with up to
+// 255 registers, which measured faster than spilling at 16.
+template <class A, int P, int WARPS, bool LV>
+__global__ void __launch_bounds__(WARPS * 32, (LV ? 256 : 512) / (WARPS * 32)) wilson_kernel(const KParams k) {
+  constexpr int K = LV ? kLevelComps : kComps;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
 
@@ -545,10 +650,10 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(
   pp.stages = k.stages;
   pp.ring = reinterpret_cast<float4*>(smem);
   const size_t ring_bytes = static_cast<size_t>(k.stages) * pp.chunk_rows * 512;
-  double* acc = reinterpret_cast<double*>(smem + ring_bytes) + warp * (P * kComps * 33);
-  pp.full = reinterpret_cast<uint64_t*>(smem + ring_bytes + WARPS * P * kComps * 33 * sizeof(double));
+  double* acc = reinterpret_cast<double*>(smem + ring_bytes) + warp * (P * K * 33);
+  pp.full = reinterpret_cast<uint64_t*>(smem + ring_bytes + WARPS * P * K * 33 * sizeof(double));
   pp.empty = pp.full + k.stages;
-  for (int j = 0; j < P * kComps; ++j) acc[j * 33 + lane] = 0.0;
+  for (int j = 0; j < P * K; ++j) acc[j * 33 + lane] = 0.0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < k.stages; ++s) {
@@ -576,9 +681,9 @@ __global__ void __launch_bounds__(WARPS * 32, 512 / (WARPS * 32)) wilson_kernel(
     const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
     const ProfileDev prof = k.profs[tile.profile];
     if (prof.kind == WLN_PROFILE_CONST_B)
-      ok = run_item<A, P, WalkB<A, P>>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+      ok = run_item<A, P, WalkB<A, P>, LV>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
     else
-      ok = run_item<A, P, Walk<A, P>>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+      ok = run_item<A, P, Walk<A, P>, LV>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -603,23 +708,24 @@ __global__ void selftest_wait_kernel(int* flag, uint64_t limit_ns) {
 
 // Sum the partials of each group over its chains, in chain order.
 __global__ void reduce_partials_kernel(const double* partial, int64_t n_points, int32_t G,
-                                       int32_t lpg, int32_t chain_loops, double* out) {
+                                       int32_t lpg, int32_t chain_loops, int32_t K,
+                                       double* out) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n_points * G * kComps) return;
-  const int q = static_cast<int>(i % kComps);
-  const int g = static_cast<int>((i / kComps) % G);
-  const int64_t p = i / (static_cast<int64_t>(kComps) * G);
+  if (i >= n_points * G * K) return;
+  const int q = static_cast<int>(i % K);
+  const int g = static_cast<int>((i / K) % G);
+  const int64_t p = i / (static_cast<int64_t>(K) * G);
   const int c_lo = static_cast<int>((static_cast<int64_t>(g) * lpg) / chain_loops);
   const int c_hi = static_cast<int>((static_cast<int64_t>(g + 1) * lpg - 1) / chain_loops);
   double s = 0.0;
   for (int c = c_lo; c <= c_hi; ++c)
-    s += partial[(static_cast<size_t>(c + g) * n_points + p) * kComps + q];
+    s += partial[(static_cast<size_t>(c + g) * n_points + p) * K + q];
   out[i] = s;
 }
 
-template <class A, int P, int WARPS>
+template <class A, int P, int WARPS, bool LV>
 cudaError_t launch_t(cudaStream_t s, const KParams& kp, int grid, size_t smem) {
-  auto kern = wilson_kernel<A, P, WARPS>;
+  auto kern = wilson_kernel<A, P, WARPS, LV>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -627,10 +733,10 @@ cudaError_t launch_t(cudaStream_t s, const KParams& kp, int grid, size_t smem) {
   return cudaGetLastError();
 }
 
-template <class A, int P, int WARPS>
+template <class A, int P, int WARPS, bool LV>
 int occupancy(size_t smem) {
   int n = 0;
-  auto kern = wilson_kernel<A, P, WARPS>;
+  auto kern = wilson_kernel<A, P, WARPS, LV>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 1;
@@ -641,30 +747,37 @@ int occupancy(size_t smem) {
 
 size_t smem_bytes(const WilsonPlan& p, int ppl) {
   const int chunk_rows = p.rows < ppl / 2 ? p.rows : ppl / 2;
+  const int K = p.levels ? kLevelComps : kComps;
   return static_cast<size_t>(p.stages) * chunk_rows * 512 +
-         static_cast<size_t>(p.warps) * p.P * kComps * 33 * sizeof(double) +
+         static_cast<size_t>(p.warps) * p.P * K * 33 * sizeof(double) +
          2 * p.stages * sizeof(uint64_t);
 }
 
 }  // namespace
 
 // Tuning applies to the float flavours; the FP64 comparison path keeps its
-// own shape (2 radii per lane, 4 warps).
-int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec) {
+// own shape (2 radii per lane, 4 warps).  The discretisation levels run three
+// walks per radius (4 radii per lane, FP64 1) and ignore the tuning of the
+// plain pass.
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, bool levels) {
+  if (levels) return prec == WLN_PREC_FP64 ? 1 : 4;
   if (prec == WLN_PREC_FP64) return 2;
   return ctx->tune_P ? ctx->tune_P : 4;
 }
 
-WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec) {
+WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
+                     bool levels) {
   WilsonPlan p{};
-  p.P = plan_points_per_lane(ctx, prec);
+  p.P = plan_points_per_lane(ctx, prec, levels);
+  p.levels = levels;
   const bool f64 = prec == WLN_PREC_FP64;
-  p.warps = f64 ? 4 : (ctx->tune_warps ? ctx->tune_warps : 8);
-  p.rows = (!f64 && ctx->tune_rows) ? ctx->tune_rows : 32;
-  p.stages = (!f64 && ctx->tune_stages) ? ctx->tune_stages : 3;
+  const bool fixed = f64 || levels;   // shapes that ignore the tuning
+  p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : 8);
+  p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
+  p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
   p.n_tiles = n_tiles;
   p.n_tile_groups = (n_tiles + p.warps - 1) / p.warps;
-  if (ctx->tune_chain && !f64) {
+  if (ctx->tune_chain && !fixed) {
     p.chain = ctx->tune_chain;
   } else {
     // Enough items to keep every SM busy with a small tail, few partials.
@@ -695,13 +808,22 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensem
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-#define WLN_CASE(A, P_, W_)                                                          \
-  if (plan.P == P_ && plan.warps == W_) {                                            \
-    const int occ = occupancy<A, P_, W_>(smem);                                      \
+#define WLN_CASE_L(A, P_, W_, LV_)                                                   \
+  if (plan.P == P_ && plan.warps == W_ && plan.levels == LV_) {                      \
+    const int occ = occupancy<A, P_, W_, LV_>(smem);                                 \
     const int64_t g = static_cast<int64_t>(sms) * occ;                               \
     const int grid = static_cast<int>(g < plan.n_items ? g : plan.n_items);          \
     ++*launches;                                                                     \
-    return launch_t<A, P_, W_>(s, kp, grid, smem);                                   \
+    return launch_t<A, P_, W_, LV_>(s, kp, grid, smem);                              \
+  }
+#define WLN_CASE(A, P_, W_) WLN_CASE_L(A, P_, W_, false)
+  if (plan.levels) {
+    switch (prec) {
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, true) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, true) break;
+      case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, true) break;
+    }
+    return cudaErrorInvalidConfiguration;
   }
   switch (prec) {
     case WLN_PREC_FP32_COMP:
@@ -718,6 +840,7 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensem
       break;
   }
 #undef WLN_CASE
+#undef WLN_CASE_L
   return cudaErrorInvalidConfiguration;
 }
 
@@ -730,10 +853,11 @@ cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const
                                    const double* partial, int64_t n_points, int32_t n_groups,
                                    int32_t loops_per_group, double* group_sums) {
   (void)e;
-  const int64_t n = n_points * n_groups * kComps;
+  const int K = plan.levels ? kLevelComps : kComps;
+  const int64_t n = n_points * n_groups * K;
   if (n == 0) return cudaSuccess;
   reduce_partials_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
-      partial, n_points, n_groups, loops_per_group, plan.chain * 32, group_sums);
+      partial, n_points, n_groups, loops_per_group, plan.chain * 32, K, group_sums);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwln.so")
 
 WLN_K = 5
+WLN_KL = 6
 C_SCAL, C_FERM, C_SIN, C_SCAL_SQ, C_FERM_SQ = range(5)
 PREC = {"fp64": 0, "fp32": 1, "fp32_comp": 1, "fp32_naive": 2}
 STATUS = {0: "WLN_OK", 1: "WLN_EINVAL", 2: "WLN_ENOMEM", 3: "WLN_ECUDA",
@@ -47,6 +48,9 @@ SIGNATURES = {
     "wln_wilson_avg": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
     "wln_wilson_avg_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
                                ctypes.c_int),
+    "wln_wilson_levels": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
+                          ctypes.c_int),
+    "wln_extrapolate": ([_P, _P, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
@@ -286,6 +290,34 @@ class Context:
         self._check(load().wln_wilson_avg_noalloc(self.handle, ens.handle, profs, len(profiles),
                                                   _ptr(rho_f), _ptr(rho_off), _ptr(T_f),
                                                   _ptr(T_off), n_groups, PREC[prec], _ptr(out)))
+        return out
+
+    def wilson_levels(self, ens: Ensemble, profiles: Sequence[Profile], rho: Sequence,
+                      T: Sequence, n_groups: int, prec: str = "fp32", out=None,
+                      where: str = "device"):
+        """Discretisation-level group sums [n_points][n_groups][6]: W - 1
+        (scalar, spinor) at N, N/2 and N/4 points per loop, from the
+        interleaved sub-loops of every loop."""
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
+        if out is None:
+            out = self._empty((n_points, n_groups, WLN_KL), np.float64, where)
+        profs = _profiles(profiles)
+        self._check(load().wln_wilson_levels(self.handle, ens.handle, profs, len(profiles),
+                                             _ptr(rho_f), _ptr(rho_off), _ptr(T_f), _ptr(T_off),
+                                             n_groups, PREC[prec], _ptr(out)))
+        return out
+
+    def extrapolate(self, level_sums, n_groups: int, loops_per_group: int,
+                    where: str = "device"):
+        """[n_points][2][6]: for the scalar then the spinor loop, the level
+        means (N, N/2, N/4), the extrapolation W_inf - 1, its group standard
+        error, and the discretisation uncertainty |m_N - (W_inf - 1)|."""
+        n_points = level_sums.shape[0]
+        out = self._empty((n_points, 2, 6), np.float64, where)
+        self._check(load().wln_extrapolate(self.handle, _ptr(level_sums), n_points, n_groups,
+                                           loops_per_group, _ptr(out)))
         return out
 
     # --------------------------------------------------------- statistics

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
 
-Tolerances ("Parity bar"):
+Tolerances:
   * Philox words: bit-exact.
   * Loops: the double copy within 1e-13 absolute (coordinates are O(1));
     float copies identical except where the double value sits on a float
@@ -50,7 +50,7 @@ def _ensemble_from_oracle(ctx, seed, n_loops, ppl):
 # (2^-21) of the sum of their terms' magnitudes, P = sum_k |phase_k| and s,
 # and W an error of about 2^-21 P (scalar) and cosh(s) 2^-21 (s + P)
 # (spinor).  Where that exceeds the 1e-6 bar (phases or spins of tens of
-# radians) it is the bar (reading R15).  The FP64 path uses 2^-50.
+# radians) it is the bar.  The FP64 path uses 2^-50.
 F32_REL = 2.0 ** -21
 F64_REL = 2.0 ** -50
 
