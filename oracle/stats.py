@@ -9,6 +9,7 @@ c = 0: sum (W_scal - 1), 1: sum (W_ferm - 1), 2: sum sin(phase),
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -198,3 +199,139 @@ def extrapolate(level_S):
     Returns [n_points][G][2] (scalar, spinor) of extrapolated W - 1 sums."""
     a, b, c = EXTRAPOLATION
     return a * level_S[:, :, 0:2] + b * level_S[:, :, 2:4] + c * level_S[:, :, 4:6]
+
+
+# --------------------------------------------------------------------------
+# Full effective action (Sec. "Renormalization": small-T split; Sec.
+# "Computing an Effective Action": integrals over [0, inf) mapped to a finite
+# interval by x = 1/(1 + T/T_max); Sec. "Verification and Validation": LCF).
+# --------------------------------------------------------------------------
+GRID_LINEAR, GRID_LOG, GRID_MAPPED = 0, 1, 2
+
+
+def mapped_nodes(n: int, scale: float, start: float) -> np.ndarray:
+    """n ascending nodes of [start, inf) under x = 1/(1 + v/scale): x runs over
+    x_k = x0 k/n, k = n .. 1 (x0 = 1/(1 + start/scale)), v = scale (1/x - 1).
+    The node x = 0 (v = inf) is not stored: the integrand vanishes there."""
+    x0 = 1.0 / (1.0 + start / scale)
+    x = x0 * (n - np.arange(n)) / n
+    v = scale * (1.0 / x - 1.0)
+    v[0] = start
+    return v
+
+
+def mapped_weights(n: int, scale: float, start: float) -> np.ndarray:
+    """Weights w such that sum_j w_j g(v_j) approximates int_start^inf g(v) dv
+    on mapped_nodes: Simpson in x over the n + 1 nodes x_0 = 0 .. x_n = x0
+    (g = 0 at x = 0), times dv/dx = scale / x^2."""
+    x0 = 1.0 / (1.0 + start / scale)
+    h = x0 / n
+    ws = simpson_weights(n + 1, h)                # over x_0 .. x_n
+    k = n - np.arange(n)                          # node j sits at x_k
+    x = x0 * k / n
+    return ws[k] * scale / (x * x)
+
+
+def _bernoulli_even(n_max: int):
+    """B_0, B_2, .., B_{2 n_max} as exact fractions (Akiyama-Tanigawa)."""
+    from fractions import Fraction
+    m_top = 2 * n_max
+    a = [Fraction(0)] * (m_top + 1)
+    B = []
+    for m in range(m_top + 1):
+        a[m] = Fraction(1, m + 1)
+        for j in range(m, 0, -1):
+            a[j - 1] = j * (a[j - 1] - a[j])
+        B.append(a[0])                            # B_m (with B_1 = +1/2)
+    return [B[2 * k] for k in range(n_max + 1)]
+
+
+@functools.lru_cache(maxsize=None)
+def _series_coeffs(spinor: bool, n_terms: int = 12):
+    """Coefficients c_k of x^{2k}, k = 2.., of x coth x - 1 - x^2/3 (spinor) or
+    x / sinh x - 1 + x^2/6 (scalar), from x coth x = sum 2^{2k} B_2k x^{2k}/(2k)!
+    and x / sinh x = sum -(2^{2k} - 2) B_2k x^{2k}/(2k)!."""
+    B = _bernoulli_even(n_terms + 2)
+    out = []
+    for k in range(2, n_terms + 2):
+        f = math.factorial(2 * k)
+        c = (2 ** (2 * k)) * B[k] / f if spinor else -(2 ** (2 * k) - 2) * B[k] / f
+        out.append(float(c))
+    return tuple(out)
+
+
+def lcf_bracket(x, spinor: bool = True):
+    """The constant-field bracket of the LCF integrand (Eq. LCFferm and its
+    scalar counterpart): x coth x - 1 - x^2/3, or x / sinh x - 1 + x^2/6, with
+    x = eB T.  Below |x| = 0.5 from the exact Taylor series (the closed form
+    cancels to ~x^4 there)."""
+    x = np.abs(np.asarray(x, np.float64))
+    c = _series_coeffs(spinor)
+    small = x < 0.5
+    xs = np.where(small, x, 0.0)
+    ser = np.zeros_like(x)
+    for k, ck in reversed(list(enumerate(c, start=2))):
+        ser = ser * xs * xs + ck
+    ser = ser * xs ** 4
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        xl = np.where(small, 1.0, x)
+        direct = (xl / np.tanh(xl) - 1.0 - xl * xl / 3.0) if spinor else (
+            xl / np.sinh(xl) - 1.0 + xl * xl / 6.0)
+    return np.where(small, ser, direct)
+
+
+def small_T_integral(eB, a: float, spinor: bool = True):
+    """int_0^a of the small-T expansion of the integrand, Eq. fermI (spinor)
+    or Eq. scalI (scalar), m = 1, term by term."""
+    b4 = np.asarray(eB, np.float64) ** 4
+    b6 = np.asarray(eB, np.float64) ** 6
+    if spinor:
+        c = (-b4 / 45.0, b4 / 45.0, 2.0 * b6 / 945.0 - b4 / 90.0, (7.0 * b4 - 4.0 * b6) / 1890.0)
+    else:
+        c = (7.0 * b4 / 360.0, -7.0 * b4 / 360.0, (147.0 * b4 - 31.0 * b6) / 15120.0,
+             (31.0 * b6 - 49.0 * b4) / 15120.0)
+    # the term c_i T^(i+1) integrates to c_i a^(i+2) / (i+2)
+    return sum(ci * a ** (i + 2) / (i + 2) for i, ci in enumerate(c))
+
+
+def axis_weights(kind: int, v: np.ndarray, scale: float = 0.0) -> np.ndarray:
+    """Quadrature weights of one axis (without the rho factor of rho drho):
+    LINEAR: Simpson on evenly spaced v; LOG: Simpson in ln v (dv = v du);
+    MAPPED: mapped_weights with start v[0]."""
+    v = np.asarray(v, np.float64)
+    n = len(v)
+    if kind == GRID_LINEAR:
+        return simpson_weights(n, (v[-1] - v[0]) / (n - 1) if n > 1 else 0.0)
+    if kind == GRID_LOG:
+        return simpson_weights(n, math.log(v[-1] / v[0]) / (n - 1) if n > 1 else 0.0) * v
+    return mapped_weights(n, scale, v[0])
+
+
+def full_effective_action(S, loops_per_group: int, profile, rho, T, rho_kind: int,
+                          T_kind: int, rho_scale: float = 0.0, T_scale: float = 0.0,
+                          small_T: bool = True, spinor: bool = True):
+    """Per group g, the T integral at every radius,
+      D_g(rho) = int_0^a I_series dT + sum_j w_j e^{-T_j}/T_j^3 (<W>_g - 1 - c (eB T_j)^2)
+    (a = T_0 when small_T, Eq. fermI/scalI; c = 1/3 spinor, -1/6 scalar), and
+    the action Gamma_g = (1/4 pi) sum_i w_i rho_i D_g(rho_i) (Eq. cylEA).  The
+    same with the constant-field value of the bracket at eB(rho) T in place
+    of <W> - 1 - c (eB T)^2 gives the LCF approximation (Eq. LCFferm).
+    Returns dict: D [n_rho][G], gamma [G], D_lcf [n_rho], gamma_lcf, and the
+    integrand I [n_T][n_rho][G], I_lcf [n_T][n_rho]."""
+    rho = np.asarray(rho, np.float64)
+    T = np.asarray(T, np.float64)
+    comp = 1 if spinor else 0
+    m = group_means(S, loops_per_group, comp).reshape(len(T), len(rho), -1)
+    eB = eB_profile(profile, rho)
+    x = eB[None, :] * T[:, None]
+    ct = x * x / 3.0 if spinor else -x * x / 6.0
+    pref = (np.exp(-T) / T ** 3)[:, None]
+    I = pref[:, :, None] * (m - ct[:, :, None])
+    I_lcf = pref * lcf_bracket(x, spinor)
+    wT = axis_weights(T_kind, T, T_scale)
+    wr = axis_weights(rho_kind, rho, rho_scale) * rho
+    small = small_T_integral(eB, T[0], spinor) if small_T else np.zeros_like(rho)
+    D = np.einsum("j,jig->ig", wT, I) + small[:, None]
+    D_lcf = wT @ I_lcf + small
+    return {"D": D, "gamma": wr @ D / (4.0 * math.pi), "D_lcf": D_lcf,
+            "gamma_lcf": float(wr @ D_lcf / (4.0 * math.pi)), "I": I, "I_lcf": I_lcf}

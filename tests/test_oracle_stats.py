@@ -186,3 +186,95 @@ def test_levels_of_a_wide_flux_tube_approach_the_constant_field():
     tube = ost.level_sums(oracle, y, Profile(0, F=F, lam=lam), [0.0], [T], 4)
     const = ost.level_sums(oracle, y, Profile(PROFILE_CONST_B, B=Beff), [0.0], [T], 4)
     np.testing.assert_allclose(tube, const, rtol=1e-5, atol=1e-9)
+
+
+def test_small_T_series_integral_matches_sympy_expansion():
+    sp = pytest.importorskip("sympy")
+    T, b, a = sp.symbols("T b a", positive=True)
+    for spinor in (True, False):
+        br = b * T / sp.tanh(b * T) - 1 - (b * T) ** 2 / 3 if spinor else \
+            b * T / sp.sinh(b * T) - 1 + (b * T) ** 2 / 6
+        ser = sp.series(sp.exp(-T) / T ** 3 * br, T, 0, 5).removeO()
+        integral = sp.integrate(ser, (T, 0, a))
+        for bv, av in ((0.7, 0.05), (3.0, 0.01), (0.2, 0.3)):
+            want = float(integral.subs({b: bv, a: av}))
+            got = float(ost.small_T_integral(bv, av, spinor))
+            assert got == pytest.approx(want, rel=1e-12, abs=1e-300)
+
+
+def test_lcf_bracket_matches_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for x in (1e-6, 1e-3, 0.1, 0.4999, 0.5001, 1.0, 7.0, 40.0, 400.0):
+        f = float(x * mp.coth(x) - 1 - mp.mpf(x) ** 2 / 3)
+        s = float(x / mp.sinh(x) - 1 + mp.mpf(x) ** 2 / 6)
+        assert float(ost.lcf_bracket(x, True)) == pytest.approx(f, rel=1e-12)
+        assert float(ost.lcf_bracket(x, False)) == pytest.approx(s, rel=1e-12, abs=1e-300)
+
+
+def test_mapped_quadrature_on_known_integrals():
+    # int_a^inf e^{-v} dv = e^{-a};  int_a^inf v^2 e^{-v} dv = (a^2 + 2a + 2) e^{-a}:
+    # Simpson in x converges at least like h^4 (the mapped integrand is smooth
+    # at x = 0, where every derivative vanishes)
+    cases = ((lambda v: np.exp(-v), lambda a: np.exp(-a)),
+             (lambda v: v * v * np.exp(-v), lambda a: (a * a + 2 * a + 2) * np.exp(-a)))
+    for scale, a in ((1.0, 0.01), (3.0, 0.2), (0.5, 0.0)):
+        for f, F in cases:
+            err = []
+            for n in (64, 128, 256):
+                v = ost.mapped_nodes(n, scale, a)
+                w = ost.mapped_weights(n, scale, a)
+                assert np.all(np.diff(v) > 0) and v[0] == a
+                err.append(abs(w @ f(v) / F(a) - 1.0))
+            assert err[2] < 1e-9
+            assert err[1] <= max(err[0] / 16.0, 1e-11) and err[2] <= max(err[1] / 16.0, 1e-11)
+    # an even node count (odd interval count) takes the 3/8 panel
+    v, w = ost.mapped_nodes(129, 1.0, 0.1), ost.mapped_weights(129, 1.0, 0.1)
+    assert w @ np.exp(-v) == pytest.approx(np.exp(-0.1), rel=1e-8)
+
+
+def test_full_lcf_action_matches_adaptive_quadrature():
+    sc = pytest.importorskip("scipy.integrate")
+    # flux tube, LCF: (1/4 pi) int_0^inf rho drho int_0^inf dT e^{-T}/T^3 bracket(eB(rho) T)
+    prof = Profile(0, F=2 * np.pi * 10.0, lam=1.0)
+    for spinor in (True, False):
+        a = 0.01
+        T = ost.mapped_nodes(96, 1.0, a)
+        rho = ost.mapped_nodes(96, 1.5, 0.0)
+        S = np.zeros((len(T) * len(rho), 2, 5))
+        r = ost.full_effective_action(S, 10, prof, rho, T, ost.GRID_MAPPED, ost.GRID_MAPPED,
+                                      rho_scale=1.5, T_scale=1.0, spinor=spinor)
+
+        def inner(rr):
+            eB = float(ost.eB_profile(prof, np.array([rr]))[0])
+            f = lambda t: np.exp(-t) / t ** 3 * float(ost.lcf_bracket(eB * t, spinor))
+            return sc.quad(f, 0, 1, epsabs=0, epsrel=1e-11, limit=200)[0] + \
+                sc.quad(f, 1, np.inf, epsabs=0, epsrel=1e-11, limit=200)[0]
+
+        # T integral at a few radii (small-T series + mapped Simpson vs adaptive)
+        for i in (0, 20, 60):
+            assert r["D_lcf"][i] == pytest.approx(inner(rho[i]), rel=2e-5)
+        want = sc.quad(lambda rr: rr * inner(rr), 0, np.inf, epsabs=0, epsrel=1e-8,
+                       limit=200)[0] / (4 * np.pi)
+        assert r["gamma_lcf"] == pytest.approx(want, rel=1e-4)
+
+
+def test_full_action_of_constant_field_averages_equals_lcf():
+    # with the continuum constant-field averages as <W>, every group reproduces
+    # the LCF result exactly (same quadrature): W_ferm - 1 = x coth x - 1 and
+    # W_scal - 1 = x / sinh x - 1 at x = eB(rho) T
+    prof = Profile(0, F=20.0, lam=0.7)
+    T = ost.mapped_nodes(24, 1.0, 0.02)
+    rho = np.linspace(0.0, 3.0, 17)
+    eB = ost.eB_profile(prof, rho)
+    x = eB[None, :] * T[:, None]
+    G, lpg = 4, 8
+    S = np.zeros((len(T) * len(rho), G, 5))
+    S[:, :, 1] = ((ost.lcf_bracket(x, True) + x * x / 3.0).reshape(-1) * lpg)[:, None]
+    S[:, :, 0] = ((ost.lcf_bracket(x, False) - x * x / 6.0).reshape(-1) * lpg)[:, None]
+    for spinor in (True, False):
+        r = ost.full_effective_action(S, lpg, prof, rho, T, ost.GRID_LINEAR, ost.GRID_MAPPED,
+                                      T_scale=1.0, spinor=spinor)
+        np.testing.assert_allclose(r["D"], np.repeat(r["D_lcf"][:, None], G, 1), rtol=1e-9,
+                                   atol=1e-12)
+        np.testing.assert_allclose(r["gamma"], r["gamma_lcf"], rtol=1e-9)
