@@ -48,8 +48,44 @@ N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 
 
 def _workload(name: str) -> I.Workload:
+    if name == "paper_mapped":
+        return _paper_mapped()
     return {"paper": I.paper, "small": I.small, "paper_slice": I.paper_slice,
             "batched": I.batched}[name]()
+
+
+def _paper_mapped() -> I.Workload:
+    """The paper ensemble and flux tubes with the paper's own quadrature: T and
+    rho_cm on [0, inf) mapped by x = 1/(1 + v/scale) (64 times from a = 1e-3
+    with T_max = 1, 128 radii with scale lambda = 1), the small-T part added
+    analytically below a.  Grid nodes come from the library (wln_mapped_grid)."""
+    from paper_1407_7486_gb300 import build, wln
+    build.build()
+    wl = I.paper()
+    T = wln.mapped_grid(64, 1.0, 1e-3)
+    rho = wln.mapped_grid(128, 1.0, 0.0)
+    wl.name = ("paper_mapped: 10240 loops x 2048 ppl, flux tubes F=[1.0, 10.0, 50.0] lam=1, "
+               "64 T mapped (T_max=1) from 1e-3 x 128 rho mapped (scale 1) from 0, "
+               "small-T part below 1e-3, G=32")
+    wl.rho = [rho.copy() for _ in wl.profiles]
+    wl.T = [T.copy() for _ in wl.profiles]
+    wl.meta["quad"] = (wln.GRID_MAPPED, wln.GRID_MAPPED, 1.0, 1.0, True)
+    return wl
+
+
+def _action(ctx, wl: I.Workload, S, lpg: int, where: str = "device"):
+    """The effective action of the step: the paper's full form (small-T part,
+    mapped grids, LCF comparison) when the workload carries its quadrature,
+    else Simpson on the linear/geometric grids."""
+    if wl.meta.get("quad"):
+        from paper_1407_7486_gb300 import wln
+        quad = [wln.Quad(*wl.meta["quad"]) for _ in wl.profiles]
+        r = ctx.effective_action_full(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, quad=quad,
+                                      spinor=True, where=where)
+        return r["gamma_groups"], r["gamma"], r
+    gg, ms = ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True,
+                                  where=where)
+    return gg, ms, None
 
 
 def _peaks():
@@ -183,11 +219,12 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
             d2h += sum(v.nbytes for v in js.values() if v is not None)
             h2d += Sq.nbytes * 2
         off += n
-    gg, ms = ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True,
-                                  where=where)
+    gg, ms, full = _action(ctx, wl, S, lpg, where=where)
     outs["gamma"] = (gg, ms)
     if where == "host":
         d2h += gg.nbytes + ms.nbytes
+        if full is not None:
+            d2h += full["density"].nbytes + full["integrand"].nbytes
         h2d += S.nbytes
     ens.free()
     return outs, h2d, d2h
@@ -274,7 +311,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wln", choices=["wln", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "paper_slice", "batched"])
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "small", "paper_slice", "batched", "paper_mapped"])
     ap.add_argument("--serve", action="store_true",
                     help="replay the seed-7 Poisson request stream against the serving ensemble")
     ap.add_argument("--requests", type=int, default=24)
@@ -341,7 +379,7 @@ def main():
                 ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 1, jk_var=True, cov=True)
                 ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 0, jk_var=False, cov=False)
                 off += n
-            ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True)
+            _action(ctx, wl, S, lpg)
             ens.free()
         e1.record(stream)
         stream.synchronize()
@@ -361,7 +399,8 @@ def main():
     h2d = d2h = 0
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
-            _, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True, loop0=loop0)
+            outs, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True,
+                                      loop0=loop0)
     stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _max_over_ranks(e2e_s, ws)
@@ -402,6 +441,13 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if wl.meta.get("quad"):
+        # the step's physics: spinor effective action per flux tube, mean +- group
+        # SEM, against the LCF approximation on the same quadrature
+        g = outs["gamma"][1]
+        line["effective_action"] = [
+            {"F": p.F, "lam": p.lam, "gamma": float(g[q, 0]), "sem": float(g[q, 1]),
+             "lcf": float(g[q, 2])} for q, p in enumerate(wl.profiles)]
     # FP64 GPU path on one profile and a sparse subset of points (it is ~10^2 slower)
     if args.prec == "fp32":
         q = 1 if len(wl.profiles) > 1 else 0

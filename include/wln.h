@@ -339,6 +339,76 @@ wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles,
                                 int32_t n_groups, int32_t loops_per_group, int32_t spinor,
                                 double* gamma_groups, double* gamma_mean_sem);
 
+/*
+ * Quadrature grids of the full effective action.  Sec. "Computing an
+ * Effective Action" maps integrals over [0, inf) to a finite interval with
+ * x = 1/(1 + v/scale) and applies Simpson's rule in x.  Per profile:
+ *   rho_kind  WLN_GRID_LINEAR: evenly spaced radii, Simpson over [rho_0, rho_last];
+ *             WLN_GRID_MAPPED: radii from wln_mapped_grid(n_rho, rho_scale, rho_0),
+ *             integral over [rho_0, inf).
+ *   T_kind    WLN_GRID_LOG: geometric times, Simpson in u = ln T over [T_0, T_last];
+ *             WLN_GRID_MAPPED: times from wln_mapped_grid(n_T, T_scale, T_0),
+ *             integral over [T_0, inf).
+ *   small_T   != 0: add the exact integral over [0, T_0] of the small-T
+ *             expansion of the integrand (Eq. fermI, or Eq. scalI for the
+ *             scalar loop; m = 1, eB at rho), the split of Sec. "Renormalization"
+ *             with a = T_0.
+ * A mapped axis of n nodes v_i = scale (1/x_i - 1), x_i = x0 (n - i)/n,
+ * x0 = 1/(1 + v_0/scale), takes Simpson weights over the n + 1 points
+ * x_0 = 0 .. x_n = x0 (the integrand is 0 at x = 0, v = inf) times
+ * dv/dx = scale/x^2.  An even point count ends with a 3/8 panel.
+ */
+enum { WLN_GRID_LINEAR = 0, WLN_GRID_LOG = 1, WLN_GRID_MAPPED = 2 };
+typedef struct {
+  int32_t rho_kind;   /* WLN_GRID_LINEAR or WLN_GRID_MAPPED */
+  int32_t T_kind;     /* WLN_GRID_LOG or WLN_GRID_MAPPED */
+  double rho_scale;   /* mapped radii: scale (> 0) */
+  double T_scale;     /* mapped times: T_max (> 0) */
+  int32_t small_T;    /* add the small-T part over [0, T_0] */
+  int32_t reserved;   /* set to 0 */
+} wln_quad;
+
+/*
+ * Nodes of a mapped grid, ascending: out[i] = scale (1/x_i - 1) with
+ * x_i = x0 (n - i)/n, x0 = 1/(1 + start/scale), i = 0 .. n-1 (out[0] = start).
+ * Host only; no context.  Rules: n >= 1, scale > 0, start >= 0, out host.
+ */
+wln_status wln_mapped_grid(int32_t n, double scale, double start, double* out);
+
+/*
+ * The full effective action with error bars and the LCF comparison
+ * (Eq. cylEA; Sec. "Renormalization"; Sec. "Computing an Effective Action";
+ * Eq. LCFferm and Sec. "Verification and Validation").  For profile q with
+ * radii rho_i and times T_j (the grids its group sums were computed on) and
+ * quadrature weights w_j (T axis) and w_i (rho axis) from quad[q]:
+ *   I_g(rho_i, T_j) = e^{-T}/T^3 (m_g - c (eB T)^2),  m_g = group mean of W - 1,
+ *   D_g(rho_i) = [int_0^{T_0} of the small-T expansion] + sum_j w_j I_g(rho_i, T_j),
+ *   Gamma_g = (1/4 pi) sum_i w_i rho_i D_g(rho_i),
+ * c = 1/3 for the spinor loop (spinor != 0, WLN_C_FERM), -1/6 for the scalar
+ * loop (WLN_C_SCAL); eB = eB(rho_i) of the profile.  The LCF approximation
+ * replaces m_g - c (eB T)^2 by the constant-field bracket x coth x - 1 - x^2/3
+ * (scalar: x / sinh x - 1 + x^2/6), x = eB(rho_i) T_j, with the same
+ * quadrature and small-T part.
+ * Outputs (host or device; any of gamma_groups, density, integrand may be NULL):
+ *   gamma_groups double[n_profiles][n_groups]  Gamma_g
+ *   gamma        double[n_profiles][3]          mean over groups, its standard error, LCF
+ *   density      double[n_rho_total][3]         D(rho): mean, standard error, LCF
+ *                                               (indexed like rho_cm)
+ *   integrand    double[n_points][3]            I(rho, T): mean, standard error, LCF
+ *                                               (points ordered as in wln_wilson_avg)
+ * quad: host array of n_profiles (NULL: every profile LINEAR radii, LOG times,
+ * no small-T part, as wln_effective_action).  Grids must match their kind
+ * (relative tolerance 1e-9), else WLN_EINVAL.
+ */
+wln_status wln_effective_action_full(wln_ctx* ctx, const wln_profile* profiles,
+                                     int32_t n_profiles, const double* rho_cm,
+                                     const int32_t* rho_off, const double* T,
+                                     const int32_t* T_off, const wln_quad* quad,
+                                     const double* group_sums, int32_t n_groups,
+                                     int32_t loops_per_group, int32_t spinor,
+                                     double* gamma_groups, double* gamma, double* density,
+                                     double* integrand);
+
 /* ------------------------------------------------------- runtime: tuning */
 
 /*

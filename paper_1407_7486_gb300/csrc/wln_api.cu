@@ -1,5 +1,6 @@
 // C ABI of libwln: argument checks, device buffers and launch sequencing.
 // The arithmetic lives in wln_gen.cu, wln_wilson.cu and wln_stats.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -210,9 +211,37 @@ wln_status check_batch(wln_ctx* ctx, const wln_profile* profiles, int32_t n_prof
   return WLN_OK;
 }
 
+namespace {
+
+// Mapped-grid node i of n: scale (1/x_i - 1), x_i = x0 (n - i)/n.
+double mapped_node(int i, int n, double scale, double start, double* x0_out) {
+  const double x0 = 1.0 / (1.0 + start / scale);
+  if (x0_out) *x0_out = x0;
+  if (i == 0) return start;
+  const double x = x0 * static_cast<double>(n - i) / n;
+  return scale * (1.0 / x - 1.0);
+}
+
+bool check_mapped(const double* v, int n, double scale, const char* what, std::string* why) {
+  if (!(scale > 0.0 && std::isfinite(scale))) {
+    if (why) *why = std::string(what) + ": mapped grid needs a finite scale > 0";
+    return false;
+  }
+  for (int i = 1; i < n; ++i) {
+    const double want = mapped_node(i, n, scale, v[0], nullptr);
+    if (std::fabs(v[i] - want) > 1e-9 * std::fabs(want)) {
+      if (why) *why = std::string(what) + " do not follow the mapped grid (wln_mapped_grid)";
+      return false;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
 bool build_quad(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
                 const int32_t* rho_off, const double* T, const int32_t* T_off,
-                std::vector<QuadProfile>& qp, std::string* why) {
+                std::vector<QuadProfile>& qp, std::string* why, const wln_quad* quad) {
   qp.assign(n_profiles, QuadProfile{});
   int64_t base = 0;
   for (int q = 0; q < n_profiles; ++q) {
@@ -223,18 +252,40 @@ bool build_quad(const wln_profile* profiles, int32_t n_profiles, const double* r
     x.kind = profiles[q].kind;
     x.n_rho = nr; x.n_T = nt; x.rho_base = rho_off[q]; x.T_base = T_off[q];
     x.p0 = base;
-    x.h_rho = nr > 1 ? (r[nr - 1] - r[0]) / (nr - 1) : 0.0;
-    x.h_u = nt > 1 ? std::log(t[nt - 1] / t[0]) / (nt - 1) : 0.0;
-    for (int i = 1; i < nr; ++i)
-      if (std::fabs((r[i] - r[i - 1]) - x.h_rho) > 1e-9 * (std::fabs(x.h_rho) + std::fabs(r[i]))) {
-        if (why) *why = "rho_cm must be evenly spaced";
+    if (quad) {
+      x.rho_kind = quad[q].rho_kind;
+      x.T_kind = quad[q].T_kind;
+      x.rho_scale = quad[q].rho_scale;
+      x.T_scale = quad[q].T_scale;
+      x.small_T = quad[q].small_T != 0;
+      if ((x.rho_kind != WLN_GRID_LINEAR && x.rho_kind != WLN_GRID_MAPPED) ||
+          (x.T_kind != WLN_GRID_LOG && x.T_kind != WLN_GRID_MAPPED)) {
+        if (why) *why = "unknown grid kind (radii: LINEAR or MAPPED; times: LOG or MAPPED)";
         return false;
       }
-    for (int i = 1; i < nt; ++i)
-      if (std::fabs(std::log(t[i] / t[i - 1]) - x.h_u) > 1e-9 * (std::fabs(x.h_u) + 1.0)) {
-        if (why) *why = "T must be geometrically spaced";
-        return false;
-      }
+    }
+    if (x.rho_kind == WLN_GRID_LINEAR) {
+      x.h_rho = nr > 1 ? (r[nr - 1] - r[0]) / (nr - 1) : 0.0;
+      for (int i = 1; i < nr; ++i)
+        if (std::fabs((r[i] - r[i - 1]) - x.h_rho) > 1e-9 * (std::fabs(x.h_rho) + std::fabs(r[i]))) {
+          if (why) *why = "rho_cm must be evenly spaced";
+          return false;
+        }
+    } else {
+      if (!check_mapped(r, nr, x.rho_scale, "rho_cm", why)) return false;
+      mapped_node(0, nr, x.rho_scale, r[0], &x.rho_x0);
+    }
+    if (x.T_kind == WLN_GRID_LOG) {
+      x.h_u = nt > 1 ? std::log(t[nt - 1] / t[0]) / (nt - 1) : 0.0;
+      for (int i = 1; i < nt; ++i)
+        if (std::fabs(std::log(t[i] / t[i - 1]) - x.h_u) > 1e-9 * (std::fabs(x.h_u) + 1.0)) {
+          if (why) *why = "T must be geometrically spaced";
+          return false;
+        }
+    } else {
+      if (!check_mapped(t, nt, x.T_scale, "T", why)) return false;
+      mapped_node(0, nt, x.T_scale, t[0], &x.T_x0);
+    }
     if (x.kind == WLN_PROFILE_FLUX_TUBE) {
       x.l2 = profiles[q].lambda * profiles[q].lambda;
       x.eB_scale = profiles[q].F * x.l2 / 3.14159265358979323846;   // 2 calF lambda^2
@@ -764,6 +815,88 @@ wln_status wln_effective_action(wln_ctx* ctx, const wln_profile* profiles, int32
   if (err == cudaSuccess) err = copy_back(om, ctx->stream);
   if (err != cudaSuccess) return cuda_fail(ctx, err, "effective action");
   if (og.host || om.host || !s_dev) return check_flag(ctx);
+  return WLN_OK;
+}
+
+wln_status wln_mapped_grid(int32_t n, double scale, double start, double* out) {
+  if (n < 1 || !out || !(scale > 0.0 && std::isfinite(scale)) || !(start >= 0.0 && std::isfinite(start)))
+    return WLN_EINVAL;
+  for (int i = 0; i < n; ++i) out[i] = mapped_node(i, n, scale, start, nullptr);
+  return WLN_OK;
+}
+
+wln_status wln_effective_action_full(wln_ctx* ctx, const wln_profile* profiles, int32_t n_profiles,
+                                     const double* rho_cm, const int32_t* rho_off, const double* T,
+                                     const int32_t* T_off, const wln_quad* quad,
+                                     const double* group_sums, int32_t n_groups,
+                                     int32_t loops_per_group, int32_t spinor, double* gamma_groups,
+                                     double* gamma, double* density, double* integrand) {
+  if (!ctx || !group_sums || !gamma) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_groups < 2 || loops_per_group < 1) return fail(ctx, WLN_EINVAL, "bad group sizes");
+  wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
+  if (st != WLN_OK) return st;
+  std::vector<QuadProfile> qp;
+  std::string why;
+  if (!build_quad(profiles, n_profiles, rho_cm, rho_off, T, T_off, qp, &why, quad))
+    return fail(ctx, WLN_EINVAL, why);
+  const int64_t n_points = qp.back().p0 + static_cast<int64_t>(qp.back().n_rho) * qp.back().n_T;
+  const int32_t n_rho_total = rho_off[n_profiles];
+  int32_t max_rho = 0;
+  std::vector<int32_t> point_profile(static_cast<size_t>(n_points));
+  for (int q = 0; q < n_profiles; ++q) {
+    max_rho = std::max(max_rho, qp[q].n_rho);
+    for (int64_t p = 0; p < static_cast<int64_t>(qp[q].n_rho) * qp[q].n_T; ++p)
+      point_profile[static_cast<size_t>(qp[q].p0 + p)] = q;
+  }
+  DeviceGuard guard(ctx->device);
+  const size_t nS = static_cast<size_t>(n_points) * n_groups * WLN_K;
+  const bool s_dev = is_device_ptr(group_sums);
+  Carve cv;
+  const size_t o_qp = cv.take<QuadProfile>(qp.size());
+  const size_t o_r = cv.take<double>(n_rho_total);
+  const size_t o_t = cv.take<double>(T_off[n_profiles]);
+  const size_t o_pp = cv.take<int32_t>(point_profile.size());
+  const size_t upload = cv.off;
+  const size_t o_S = s_dev ? 0 : cv.take<double>(nS);
+  const size_t o_dg = cv.take<double>(static_cast<size_t>(n_rho_total) * n_groups);
+  const size_t o_gg = cv.take<double>(static_cast<size_t>(n_profiles) * n_groups);
+  const size_t o_den = cv.take<double>(static_cast<size_t>(n_rho_total) * 3);
+  Out og = plan_out(cv, gamma_groups, static_cast<size_t>(n_profiles) * n_groups);
+  Out om = plan_out(cv, gamma, static_cast<size_t>(n_profiles) * 3);
+  Out od = plan_out(cv, density, static_cast<size_t>(n_rho_total) * 3);
+  Out oi = plan_out(cv, integrand, static_cast<size_t>(n_points) * 3);
+  if ((st = ensure_scratch(ctx, cv.off + 256)) != WLN_OK) return st;
+  if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
+  for (Out* o : {&og, &om, &od, &oi}) bind_out(*o, ctx->scratch.ptr);
+  char* h = static_cast<char*>(ctx->pinned);
+  std::memcpy(h + o_qp, qp.data(), qp.size() * sizeof(QuadProfile));
+  std::memcpy(h + o_r, rho_cm, n_rho_total * sizeof(double));
+  std::memcpy(h + o_t, T, T_off[n_profiles] * sizeof(double));
+  std::memcpy(h + o_pp, point_profile.data(), point_profile.size() * sizeof(int32_t));
+  char* d = static_cast<char*>(ctx->scratch.ptr);
+  cudaError_t err = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
+  const double* S = group_sums;
+  if (err == cudaSuccess && !s_dev) {
+    err = cudaMemcpyAsync(d + o_S, group_sums, nS * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->stream);
+    S = at<double>(d, o_S);
+  }
+  int64_t launches = 0;
+  if (err == cudaSuccess)
+    err = launch_effective_action_full(
+        ctx->stream, at<QuadProfile>(d, o_qp), n_profiles, max_rho, n_rho_total, n_points,
+        at<int32_t>(d, o_pp), at<double>(d, o_r), at<double>(d, o_t), S, n_groups,
+        loops_per_group, spinor, at<double>(d, o_dg),
+        gamma_groups ? static_cast<double*>(og.dev) : at<double>(d, o_gg),
+        static_cast<double*>(om.dev),
+        density ? static_cast<double*>(od.dev) : at<double>(d, o_den),
+        static_cast<double*>(oi.dev), &launches);
+  ctx->launches += launches;
+  for (const Out* o : {&og, &om, &od, &oi})
+    if (err == cudaSuccess) err = copy_back(*o, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "full effective action");
+  if (og.host || om.host || od.host || oi.host || !s_dev) return check_flag(ctx);
   return WLN_OK;
 }
 

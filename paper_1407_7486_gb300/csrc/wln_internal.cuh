@@ -175,12 +175,29 @@ struct QuadProfile {
   double h_u;        // spacing of ln T
   double eB_scale;   // flux tube: 2 calF lambda^2 = F lambda^2 / pi; constant: B
   double l2;
+  // axis kinds (WLN_GRID_*) and mapped-grid parameters
+  int32_t rho_kind = WLN_GRID_LINEAR, T_kind = WLN_GRID_LOG;
+  int32_t small_T = 0, pad2 = 0;
+  double rho_scale = 0.0, T_scale = 0.0;
+  double rho_x0 = 1.0, T_x0 = 1.0;   // x at the first node of a mapped axis
 };
 // Quadrature tables of a batch of profiles; false (with a reason) when a
 // profile's radii are not evenly spaced or its times not geometric (wln_api.cu).
+// quad: per-profile grid kinds (nullptr: linear radii, geometric times).
 bool build_quad(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
                 const int32_t* rho_off, const double* T, const int32_t* T_off,
-                std::vector<QuadProfile>& qp, std::string* why);
+                std::vector<QuadProfile>& qp, std::string* why,
+                const wln_quad* quad = nullptr);
+// Full effective action (wln_effective_action_full): d_groups is scratch of
+// n_rho_total * G doubles; rho_profile maps a flattened radius to its profile.
+cudaError_t launch_effective_action_full(cudaStream_t s, const QuadProfile* qp,
+                                         int32_t n_profiles, int32_t max_rho,
+                                         int32_t n_rho_total, int64_t n_points,
+                                         const int32_t* point_profile, const double* rho,
+                                         const double* T, const double* S, int32_t G,
+                                         int32_t lpg, int32_t spinor, double* d_groups,
+                                         double* gamma_groups, double* gamma, double* density,
+                                         double* integrand, int64_t* launches);
 cudaError_t launch_effective_action(cudaStream_t s, const QuadProfile* qp, int32_t n_profiles,
                                     const double* rho, const double* T, const double* S,
                                     int32_t G, int32_t lpg, int32_t spinor, double* gamma_groups,

@@ -191,6 +191,185 @@ __global__ void __launch_bounds__(256) effective_action_kernel(
   if (threadIdx.x == 0) gamma_groups[q * G + g] = red[0] / (4.0 * 3.14159265358979323846);
 }
 
+// ------------------------------------------------ full effective action
+// Small-argument series of the constant-field brackets (coefficients of
+// x^4, x^6, ..., x^26; gen_lcf_series.py, exact Bernoulli numbers):
+//   x coth x - 1 - x^2/3 (spinor),  x / sinh x - 1 + x^2/6 (scalar).
+__constant__ double kLcfSpin[12] = {
+    -0.022222222222222223, 0.0021164021164021165, -0.00021164021164021165,
+    2.1377799155576935e-05, -2.1644042808063972e-06, 2.1925947851873778e-07,
+    -2.2214608789979678e-08, 2.2507846516808994e-09, -2.2805151204592183e-10,
+    2.3106432599002624e-11, -2.3411706819824882e-12, 2.3721017400233653e-13};
+__constant__ double kLcfScal[12] = {
+    0.019444444444444445, -0.00205026455026455, 0.0002099867724867725,
+    -2.1336045641601196e-05, 2.1633474427786596e-06, -2.192327134456764e-07,
+    2.2213930853920414e-08, -2.2507674795567867e-09, 2.280510770721821e-10,
+    -2.3106421580996967e-11, 2.3411704028931947e-12, -2.3721016693292245e-13};
+
+// The LCF bracket at x = eB T (Eq. LCFferm and its scalar counterpart): the
+// series below |x| = 1/2, where the closed form cancels to ~x^4.
+__device__ double lcf_bracket(double x, bool spinor) {
+  x = fabs(x);
+  if (x < 0.5) {
+    const double* c = spinor ? kLcfSpin : kLcfScal;
+    const double x2 = x * x;
+    double p = c[11];
+    for (int k = 10; k >= 0; --k) p = fma(p, x2, c[k]);
+    return p * x2 * x2;
+  }
+  return spinor ? x / tanh(x) - 1.0 - x * x / 3.0 : x / sinh(x) - 1.0 + x * x / 6.0;
+}
+
+// int_0^a of the small-T expansion of the integrand, term by term (Eq. fermI
+// for the spinor loop, Eq. scalI for the scalar loop, m = 1).
+__device__ double small_T_part(double eB, double a, bool spinor) {
+  const double b2 = eB * eB, b4 = b2 * b2, b6 = b4 * b2;
+  double c0, c1, c2, c3;   // coefficients of T, T^2, T^3, T^4
+  if (spinor) {
+    c0 = -b4 / 45.0; c1 = b4 / 45.0; c2 = 2.0 * b6 / 945.0 - b4 / 90.0;
+    c3 = (7.0 * b4 - 4.0 * b6) / 1890.0;
+  } else {
+    c0 = 7.0 * b4 / 360.0; c1 = -7.0 * b4 / 360.0; c2 = (147.0 * b4 - 31.0 * b6) / 15120.0;
+    c3 = (31.0 * b6 - 49.0 * b4) / 15120.0;
+  }
+  const double a2 = a * a;
+  return a2 * (c0 / 2.0 + a * (c1 / 3.0 + a * (c2 / 4.0 + a * (c3 / 5.0))));
+}
+
+__device__ double profile_eB(const QuadProfile& pr, double r) {
+  if (pr.kind == WLN_PROFILE_CONST_B) return pr.eB_scale;
+  const double q2 = pr.l2 + r * r;
+  return pr.eB_scale / (q2 * q2);
+}
+
+// Weight of node i of a mapped axis of n nodes: Simpson in x over the n + 1
+// points 0, x0/n, .., x0 (node i sits at x = x0 (n - i)/n), times scale/x^2.
+__device__ double mapped_weight(int i, int n, double x0, double scale) {
+  const int k = n - i;
+  const double x = x0 * k / n;
+  return simpson_weight(k, n + 1, x0 / n) * scale / (x * x);
+}
+
+__device__ double T_weight(const QuadProfile& pr, int j, double t) {
+  return pr.T_kind == WLN_GRID_MAPPED ? mapped_weight(j, pr.n_T, pr.T_x0, pr.T_scale)
+                                      : simpson_weight(j, pr.n_T, pr.h_u) * t;
+}
+
+__device__ double rho_weight(const QuadProfile& pr, int i) {
+  return pr.rho_kind == WLN_GRID_MAPPED ? mapped_weight(i, pr.n_rho, pr.rho_x0, pr.rho_scale)
+                                        : simpson_weight(i, pr.n_rho, pr.h_rho);
+}
+
+// One thread per (radius of profile q, group g) and one more "group" g = G
+// for the LCF: D(rho_i) = small-T part + sum_j w_j I(rho_i, T_j), in T order.
+__global__ void density_kernel(const QuadProfile* qp, const double* rho, const double* T,
+                               const double* S, int32_t G, int32_t lpg, int32_t spinor,
+                               double* d_groups, double* density) {
+  const int q = blockIdx.y;
+  const QuadProfile pr = qp[q];
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<int64_t>(pr.n_rho) * (G + 1)) return;
+  const int i = static_cast<int>(idx / (G + 1)), g = static_cast<int>(idx % (G + 1));
+  const bool sp = spinor != 0;
+  const int comp = sp ? WLN_C_FERM : WLN_C_SCAL;
+  const double c_ct = sp ? 1.0 / 3.0 : -1.0 / 6.0;
+  const double r = rho[pr.rho_base + i];
+  const double eB = profile_eB(pr, r);
+  double acc = pr.small_T ? small_T_part(eB, T[pr.T_base], sp) : 0.0;
+  for (int j = 0; j < pr.n_T; ++j) {
+    const double t = T[pr.T_base + j];
+    const double et = eB * t;
+    const double pref = exp(-t) / (t * t * t);
+    double b;
+    if (g < G) {
+      const int64_t p = pr.p0 + static_cast<int64_t>(j) * pr.n_rho + i;
+      b = S[(p * G + g) * kComps + comp] / lpg - c_ct * et * et;
+    } else {
+      b = lcf_bracket(et, sp);
+    }
+    acc += T_weight(pr, j, t) * pref * b;
+  }
+  const int64_t ri = pr.rho_base + i;
+  if (g < G) d_groups[ri * G + g] = acc;
+  else density[ri * 3 + 2] = acc;
+}
+
+// One CTA per (group, profile); group index G is the LCF.  Gamma = (1/4 pi)
+// sum_i w_i rho_i D(rho_i), each thread over a fixed stride of radii, then a
+// fixed tree.
+__global__ void __launch_bounds__(256) action_kernel(const QuadProfile* qp, const double* rho,
+                                                     int32_t G, const double* d_groups,
+                                                     const double* density,
+                                                     double* gamma_groups, double* gamma) {
+  const int q = blockIdx.y, g = blockIdx.x;
+  const QuadProfile pr = qp[q];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < pr.n_rho; i += blockDim.x) {
+    const int64_t ri = pr.rho_base + i;
+    const double D = g < G ? d_groups[ri * G + g] : density[ri * 3 + 2];
+    acc += rho_weight(pr, i) * rho[ri] * D;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = red[0] / (4.0 * 3.14159265358979323846);
+    if (g < G) gamma_groups[q * G + g] = v;
+    else gamma[q * 3 + 2] = v;
+  }
+}
+
+// Mean over groups and its standard error of rows x[r][G], into out[r * stride + 0, 1].
+__global__ void mean_sem_rows_kernel(const double* x, int32_t n_rows, int32_t G, double* out,
+                                     int32_t stride) {
+  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (r >= n_rows) return;
+  const double* v = x + r * G;
+  double m = 0.0;
+  for (int g = 0; g < G; ++g) m += v[g];
+  m /= G;
+  double ss = 0.0;
+  for (int g = 0; g < G; ++g) ss += (v[g] - m) * (v[g] - m);
+  out[r * stride] = m;
+  out[r * stride + 1] = sqrt(ss / (static_cast<double>(G) * (G - 1)));
+}
+
+// The integrand at every point: mean and standard error over groups of
+// I_g = e^{-T}/T^3 (m_g - c (eB T)^2), and the LCF integrand.
+__global__ void integrand_kernel(const QuadProfile* qp, const int32_t* point_profile,
+                                 const double* rho, const double* T, const double* S,
+                                 int64_t n_points, int32_t G, int32_t lpg, int32_t spinor,
+                                 double* out) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n_points) return;
+  const QuadProfile pr = qp[point_profile[p]];
+  const int64_t local = p - pr.p0;
+  const int j = static_cast<int>(local / pr.n_rho), i = static_cast<int>(local % pr.n_rho);
+  const bool sp = spinor != 0;
+  const int comp = sp ? WLN_C_FERM : WLN_C_SCAL;
+  const double c_ct = sp ? 1.0 / 3.0 : -1.0 / 6.0;
+  const double t = T[pr.T_base + j];
+  const double et = profile_eB(pr, rho[pr.rho_base + i]) * t;
+  const double pref = exp(-t) / (t * t * t);
+  const double ct = c_ct * et * et;
+  const double* s = S + p * G * kComps + comp;
+  double m = 0.0;
+  for (int g = 0; g < G; ++g) m += pref * (s[g * kComps] / lpg - ct);
+  m /= G;
+  double ss = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double d = pref * (s[g * kComps] / lpg - ct) - m;
+    ss += d * d;
+  }
+  out[p * 3] = m;
+  out[p * 3 + 1] = sqrt(ss / (static_cast<double>(G) * (G - 1)));
+  out[p * 3 + 2] = pref * lcf_bracket(et, sp);
+}
+
 __global__ void group_mean_sem_kernel(const double* x, int32_t n_rows, int32_t G, double* out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_rows) return;
@@ -233,6 +412,42 @@ cudaError_t launch_loop_sem(cudaStream_t s, const double* S, int32_t n_points, i
   loop_sem_kernel<<<static_cast<unsigned>((n_points + 255) / 256), 256, 0, s>>>(
       S, n_points, G, n_loops, comp_sum, comp_sq, out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_effective_action_full(cudaStream_t s, const QuadProfile* qp,
+                                         int32_t n_profiles, int32_t max_rho,
+                                         int32_t n_rho_total, int64_t n_points,
+                                         const int32_t* point_profile, const double* rho,
+                                         const double* T, const double* S, int32_t G,
+                                         int32_t lpg, int32_t spinor, double* d_groups,
+                                         double* gamma_groups, double* gamma, double* density,
+                                         double* integrand, int64_t* launches) {
+  // density (n_rho_total x 3, never null) carries the LCF T integral in column 2.
+  const int64_t n_thr = static_cast<int64_t>(max_rho) * (G + 1);
+  density_kernel<<<dim3(static_cast<unsigned>((n_thr + 127) / 128), n_profiles), 128, 0, s>>>(
+      qp, rho, T, S, G, lpg, spinor, d_groups, density);
+  ++*launches;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  action_kernel<<<dim3(G + 1, n_profiles), 256, 0, s>>>(qp, rho, G, d_groups, density,
+                                                        gamma_groups, gamma);
+  ++*launches;
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  mean_sem_rows_kernel<<<static_cast<unsigned>((n_profiles + 127) / 128), 128, 0, s>>>(
+      gamma_groups, n_profiles, G, gamma, 3);
+  ++*launches;
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  mean_sem_rows_kernel<<<static_cast<unsigned>((n_rho_total + 127) / 128), 128, 0, s>>>(
+      d_groups, n_rho_total, G, density, 3);
+  ++*launches;
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (integrand) {
+    integrand_kernel<<<static_cast<unsigned>((n_points + 127) / 128), 128, 0, s>>>(
+        qp, point_profile, rho, T, S, n_points, G, lpg, spinor, integrand);
+    ++*launches;
+    err = cudaGetLastError();
+  }
+  return err;
 }
 
 cudaError_t launch_effective_action(cudaStream_t s, const QuadProfile* qp, int32_t n_profiles,

@@ -51,6 +51,9 @@ SIGNATURES = {
     "wln_wilson_levels": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
                           ctypes.c_int),
     "wln_extrapolate": ([_P, _P, _I32, _I32, _I32, _P], ctypes.c_int),
+    "wln_mapped_grid": ([_I32, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
+    "wln_effective_action_full": ([_P, _P, _I32, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
+                                   _P, _P, _P], ctypes.c_int),
     "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
@@ -84,6 +87,33 @@ class WlnError(RuntimeError):
 class _CProfile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("F", ctypes.c_double),
                 ("lam", ctypes.c_double), ("B", ctypes.c_double)]
+
+
+class _CQuad(ctypes.Structure):
+    _fields_ = [("rho_kind", ctypes.c_int32), ("T_kind", ctypes.c_int32),
+                ("rho_scale", ctypes.c_double), ("T_scale", ctypes.c_double),
+                ("small_T", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+GRID_LINEAR, GRID_LOG, GRID_MAPPED = 0, 1, 2
+
+
+class Quad:
+    """Quadrature grids of one profile for effective_action_full (wln_quad)."""
+
+    def __init__(self, rho_kind: int = GRID_LINEAR, T_kind: int = GRID_LOG,
+                 rho_scale: float = 0.0, T_scale: float = 0.0, small_T: bool = False):
+        self.rho_kind, self.T_kind = rho_kind, T_kind
+        self.rho_scale, self.T_scale, self.small_T = rho_scale, T_scale, small_T
+
+
+def mapped_grid(n: int, scale: float, start: float = 0.0) -> np.ndarray:
+    """Ascending nodes of [start, inf) under x = 1/(1 + v/scale) (wln_mapped_grid)."""
+    out = np.empty(n, np.float64)
+    st = load().wln_mapped_grid(n, float(scale), float(start), _ptr(out))
+    if st != 0:
+        raise WlnError(st, "wln_mapped_grid: needs n >= 1, scale > 0, start >= 0")
+    return out
 
 
 _lib = None
@@ -354,6 +384,34 @@ class Context:
                                                 _ptr(group_sums), n_groups, loops_per_group,
                                                 int(spinor), _ptr(gg), _ptr(ms)))
         return gg, ms
+
+    def effective_action_full(self, profiles: Sequence[Profile], rho: Sequence, T: Sequence,
+                              group_sums, n_groups: int, loops_per_group: int,
+                              quad: Optional[Sequence[Quad]] = None, spinor: bool = True,
+                              where: str = "device"):
+        """Full effective action: {"gamma_groups": [n_profiles][G], "gamma":
+        [n_profiles][3] (mean, SEM, LCF), "density": [n_rho_total][3] (T
+        integral at each radius: mean, SEM, LCF), "integrand": [n_points][3]}."""
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
+        out = {"gamma_groups": self._empty((len(profiles), n_groups), np.float64, where),
+               "gamma": self._empty((len(profiles), 3), np.float64, where),
+               "density": self._empty((len(rho_f), 3), np.float64, where),
+               "integrand": self._empty((n_points, 3), np.float64, where)}
+        cq = None
+        if quad is not None:
+            cq = (_CQuad * len(profiles))()
+            for i, q in enumerate(quad):
+                cq[i] = _CQuad(int(q.rho_kind), int(q.T_kind), float(q.rho_scale),
+                               float(q.T_scale), int(bool(q.small_T)), 0)
+        profs = _profiles(profiles)
+        self._check(load().wln_effective_action_full(
+            self.handle, profs, len(profiles), _ptr(rho_f), _ptr(rho_off), _ptr(T_f),
+            _ptr(T_off), cq, _ptr(group_sums), n_groups, loops_per_group, int(spinor),
+            _ptr(out["gamma_groups"]), _ptr(out["gamma"]), _ptr(out["density"]),
+            _ptr(out["integrand"])))
+        return out
 
 
 class Batch:

@@ -3,6 +3,7 @@ every function that include/wln.h declares (no compute calls here)."""
 import ctypes
 import os
 
+import numpy as np
 import pytest
 
 from paper_1407_7486_gb300 import build, wln
@@ -44,3 +45,13 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.wln_synchronize(None) == 1
     assert lib.wln_last_error(None) == b"no context"
     assert lib.wln_ensemble_info(None, None, None, None) == 1
+
+
+def test_mapped_grid_helper_matches_oracle_nodes():
+    # host-only helper of the C ABI (no GPU work): nodes of x = 1/(1 + v/scale)
+    from oracle import stats as ost
+    for n, scale, start in ((64, 1.0, 0.01), (33, 2.5, 0.0), (1, 1.0, 0.3), (7, 0.2, 5.0)):
+        np.testing.assert_allclose(wln.mapped_grid(n, scale, start),
+                                   ost.mapped_nodes(n, scale, start), rtol=1e-15, atol=0)
+    with pytest.raises(wln.WlnError):
+        wln.mapped_grid(4, -1.0, 0.0)
