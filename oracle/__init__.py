@@ -51,6 +51,11 @@ def _load():
     u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
     u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
     f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    lib.wln_oracle_loop_values.argtypes = [f64p, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.POINTER(_Profile), f64p, ctypes.c_int32, f64p,
+                                           ctypes.c_int32, f64p, ctypes.c_int32]
+    lib.wln_oracle_shuffle.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, i32p]
     lib.wln_oracle_philox4x32.argtypes = [u32p, u32p, ctypes.c_int, u32p]
     lib.wln_oracle_philox4x64.argtypes = [u64p, u64p, ctypes.c_int, u64p]
     lib.wln_oracle_philox_stream.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
@@ -188,6 +193,26 @@ def group_sums(y: np.ndarray, profile, rho, T, n_groups: int, threads: int = 0) 
     _load().wln_oracle_group_sums(y, n_loops, ppl, ctypes.byref(_prof(profile)), rho, len(rho),
                                   T, len(T), n_groups, out, threads or max_threads())
     return out
+
+
+def loop_values(y: np.ndarray, profile, rho, T, threads: int = 0) -> np.ndarray:
+    """W - 1 of every loop at every point [n_T * n_rho][n_loops][2] (scalar,
+    spinor; rho fastest)."""
+    y = np.ascontiguousarray(y, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    T = np.ascontiguousarray(T, np.float64)
+    n_loops, _, ppl = y.shape
+    out = np.zeros((len(T) * len(rho), n_loops, 2), np.float64)
+    _load().wln_oracle_loop_values(y, n_loops, ppl, ctypes.byref(_prof(profile)), rho, len(rho),
+                                   T, len(T), out, threads or max_threads())
+    return out
+
+
+def shuffle(seed: int, point: int, n: int) -> np.ndarray:
+    """The loop permutation of the random grouping of evaluation `point`."""
+    a = np.zeros(n, np.int32)
+    _load().wln_oracle_shuffle(seed, point, n, a)
+    return a
 
 
 from . import stats  # noqa: E402,F401  (numpy statistics and quadrature)

@@ -335,3 +335,38 @@ def full_effective_action(S, loops_per_group: int, profile, rho, T, rho_kind: in
     D_lcf = wT @ I_lcf + small
     return {"D": D, "gamma": wr @ D / (4.0 * math.pi), "D_lcf": D_lcf,
             "gamma_lcf": float(wr @ D_lcf / (4.0 * math.pi)), "I": I, "I_lcf": I_lcf}
+
+
+# --------------------------------------------------------------------------
+# Correlations between evaluations and randomised grouping (Sec.
+# "Correlations between Wilson Loops", Eq. corrcoef; Sec. "Grouping
+# Worldlines": new random groups for every evaluation of the integrand).
+# --------------------------------------------------------------------------
+def group_sums_perm(W: np.ndarray, n_groups: int, perm=None) -> np.ndarray:
+    """Group sums S[p][g][c] of per-loop values W[p][l][c]: group g of point p
+    holds loops perm[p][g n/G .. (g+1) n/G - 1] (perm None: loops in order,
+    the contiguous groups), summed in that order."""
+    n_pts, n_loops, n_c = W.shape
+    lpg = n_loops // n_groups
+    S = np.zeros((n_pts, n_groups, n_c))
+    for p in range(n_pts):
+        order = np.arange(n_loops) if perm is None else perm[p]
+        for g in range(n_groups):
+            acc = np.zeros(n_c)
+            for k in range(g * lpg, (g + 1) * lpg):
+                acc += W[p, order[k]]
+            S[p, g] = acc
+    return S
+
+
+def corrcoef_ref(X: np.ndarray, ref: int) -> np.ndarray:
+    """Eq. corrcoef between row ref and every row of X[p][n] over the n
+    samples (loops, or group means):
+      r_p = sum_n (X_pn - <X_p>)(X_rn - <X_r>) / sqrt(sum_n (X_pn - <X_p>)^2 sum_n (X_rn - <X_r>)^2).
+    A row without spread gives NaN."""
+    X = np.asarray(X, np.float64)
+    d = X - X.mean(axis=1, keepdims=True)
+    num = d @ d[ref]
+    den = np.sqrt((d * d).sum(axis=1) * (d[ref] * d[ref]).sum())
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return num / den

@@ -397,3 +397,51 @@ int32_t wln_oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Per-loop values and randomised groups (Sec. "Correlations between Wilson  */
+/* Loops" and Sec. "Grouping Worldlines": assign the worldlines to groups    */
+/* at random, anew for every evaluation of the integrand).                  */
+/* ------------------------------------------------------------------------ */
+
+/* W - 1 of every loop at every point: out[p][l][0] scalar, [1] spinor,
+ * points p = iT * n_rho + i_rho. */
+void wln_oracle_loop_values(const double* y, int64_t n_loops, int32_t N,
+                            const oracle_profile* prof, const double* rho, int32_t n_rho,
+                            const double* T, int32_t n_T, double* out, int32_t threads) {
+  const int64_t n_pts = (int64_t)n_rho * n_T;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(threads > 0 ? threads : 1)
+  for (int64_t pl = 0; pl < n_pts * n_loops; ++pl) {
+    int64_t p = pl / n_loops, l = pl % n_loops;
+    double ph, sp, w[5];
+    wln_oracle_loop_phase_spin(y + (size_t)l * 2 * N, N, prof, rho[p % n_rho], T[p / n_rho],
+                               &ph, &sp);
+    wln_oracle_wilson_terms(ph, sp, w);
+    out[(size_t)pl * 2] = w[0];
+    out[(size_t)pl * 2 + 1] = w[1];
+  }
+}
+
+/* The random grouping of evaluation `point`: a uniformly random permutation
+ * a[0..n-1] of the loops by the Fisher-Yates shuffle (Durstenfeld's form):
+ * for t = 0 .. n-2, i = n-1-t, draw j uniform in [0, i] and swap a[i], a[j].
+ * Draw t takes 32-bit word t mod 4 of Philox-4x32-10 with counter
+ * (t / 4, point, 2, 0) and key (seed_lo, seed_hi), and j = (u (i+1)) >> 32
+ * (the multiply-shift map, bias below (i+1)/2^32).  Group g then holds
+ * loops a[g n/G .. (g+1) n/G - 1]. */
+void wln_oracle_shuffle(uint64_t seed, int64_t point, int32_t n, int32_t* a) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t u[4] = {0, 0, 0, 0};
+  for (int32_t k = 0; k < n; ++k) a[k] = k;
+  for (int32_t t = 0; t < n - 1; ++t) {
+    if (t % 4 == 0) {
+      uint32_t ctr[4] = {(uint32_t)(t / 4), (uint32_t)point, 2u, 0u};
+      wln_oracle_philox4x32(ctr, key, 10, u);
+    }
+    int32_t i = n - 1 - t;
+    int32_t j = (int32_t)(((uint64_t)u[t % 4] * (uint64_t)(i + 1)) >> 32);
+    int32_t s = a[i];
+    a[i] = a[j];
+    a[j] = s;
+  }
+}

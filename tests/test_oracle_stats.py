@@ -278,3 +278,82 @@ def test_full_action_of_constant_field_averages_equals_lcf():
         np.testing.assert_allclose(r["D"], np.repeat(r["D_lcf"][:, None], G, 1), rtol=1e-9,
                                    atol=1e-12)
         np.testing.assert_allclose(r["gamma"], r["gamma_lcf"], rtol=1e-9)
+
+
+def test_shuffle_is_a_uniform_permutation():
+    import oracle
+    from itertools import permutations
+    for n in (1, 2, 7, 100, 1000):
+        a = oracle.shuffle(11, 3, n)
+        assert sorted(a.tolist()) == list(range(n))
+    # all 24 orders of 4 loops, equally often over 24000 evaluations (chi-square)
+    idx = {p: i for i, p in enumerate(permutations(range(4)))}
+    counts = np.zeros(24)
+    for point in range(24000):
+        counts[idx[tuple(oracle.shuffle(5, point, 4).tolist())]] += 1
+    chi2 = ((counts - 1000.0) ** 2 / 1000.0).sum()
+    assert chi2 < 60.0          # 23 degrees of freedom: P(chi2 > 60) ~ 4e-5
+    # every loop lands in every position equally often (n = 10)
+    pos = np.zeros((10, 10))
+    for point in range(20000):
+        a = oracle.shuffle(9, point, 10)
+        pos[a, np.arange(10)] += 1
+    assert np.abs(pos / 2000.0 - 1.0).max() < 0.12
+    # different evaluations, different orders; the same evaluation, the same order
+    assert not np.array_equal(oracle.shuffle(1, 0, 50), oracle.shuffle(1, 1, 50))
+    assert np.array_equal(oracle.shuffle(1, 7, 50), oracle.shuffle(1, 7, 50))
+
+
+def test_grouping_by_permutation():
+    rng = np.random.default_rng(3)
+    W = rng.normal(size=(3, 12, 2))
+    # identity order = the contiguous groups of the paper's default grouping
+    S = ost.group_sums_perm(W, 4)
+    np.testing.assert_allclose(S, W.reshape(3, 4, 3, 2).sum(axis=2), rtol=1e-15)
+    perm = np.stack([rng.permutation(12) for _ in range(3)])
+    Sp = ost.group_sums_perm(W, 4, perm)
+    np.testing.assert_allclose(Sp.sum(axis=1), W.sum(axis=1), rtol=1e-13)   # totals kept
+    for p in range(3):
+        for g in range(4):
+            np.testing.assert_allclose(Sp[p, g], W[p, perm[p, 3 * g:3 * g + 3]].sum(axis=0),
+                                       rtol=1e-15)
+
+
+def test_corrcoef_definition():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(6, 500))
+    X[1] = 3.0 * X[0] + 2.0          # exact linear relation: +1
+    X[2] = -0.5 * X[0]               # exact inverse relation: -1
+    r = ost.corrcoef_ref(X, 0)
+    assert r[0] == pytest.approx(1.0, abs=1e-14)
+    assert r[1] == pytest.approx(1.0, abs=1e-14) and r[2] == pytest.approx(-1.0, abs=1e-14)
+    assert np.all(np.abs(r[3:]) < 5.0 / np.sqrt(500))     # independent rows: ~0
+    np.testing.assert_allclose(r, np.corrcoef(X)[0], rtol=1e-12, atol=1e-15)
+    assert np.isnan(ost.corrcoef_ref(np.vstack([X[:1], np.ones((1, 500))]), 0)[1])
+
+
+def test_shuffled_groups_remove_point_to_point_correlation():
+    # Fig. corr: W at two evaluations built on the same loops is correlated loop by
+    # loop, and so are the means of fixed groups; new random groups for every
+    # evaluation remove the correlation between the group means
+    import oracle
+    rng = np.random.default_rng(6)
+    n_loops, G = 6400, 64
+    z = rng.normal(size=n_loops)
+    W = np.stack([z + 0.3 * rng.normal(size=n_loops) for _ in range(8)])[:, :, None]
+    lpg = n_loops // G
+    loops = ost.corrcoef_ref(W[:, :, 0], 0)
+    fixed = ost.corrcoef_ref(ost.group_sums_perm(W, G)[:, :, 0] / lpg, 0)
+    perm = np.stack([oracle.shuffle(21, p, n_loops) for p in range(8)])
+    shuffled = ost.corrcoef_ref(ost.group_sums_perm(W, G, perm)[:, :, 0] / lpg, 0)
+    assert np.all(loops[1:] > 0.85) and np.all(fixed[1:] > 0.8)
+    assert np.all(np.abs(shuffled[1:]) < 4.0 / np.sqrt(G))
+
+
+def test_loop_values_sum_to_group_sums():
+    import oracle
+    y = oracle.gen_loops(8, 24, 64)
+    prof, rho, T = Profile(0, F=10.0, lam=1.0), np.array([0.0, 0.7]), np.array([0.1, 2.0])
+    W = oracle.loop_values(y, prof, rho, T)
+    S = oracle.group_sums(y, prof, rho, T, 3)
+    np.testing.assert_allclose(ost.group_sums_perm(W, 3), S[:, :, :2], rtol=1e-13, atol=1e-15)
