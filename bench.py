@@ -318,6 +318,8 @@ def main():
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--rate-scales", default="sat",
                     help="comma list: 'sat' (2000 req/s) and/or fractions of measured capacity")
+    ap.add_argument("--correlation", action="store_true",
+                    help="time per-loop values, randomised groups and Eq. corrcoef")
     ap.add_argument("--levels", action="store_true",
                     help="time the discretisation-level pass (N, N/2, N/4) and extrapolation")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
@@ -337,6 +339,8 @@ def main():
         return run_batched(args, wl)
     if args.levels:
         return run_levels(args, wl)
+    if args.correlation:
+        return run_correlation(args, wl)
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -632,6 +636,104 @@ def run_levels(args, wl: I.Workload):
                 "scal_max_abs": float(np.abs(G - ref)[:, :, 0::2].max() / lpg),
                 "ferm_max_rel_to_max(1,|<W>-1|)": float(
                     (np.abs(G - ref)[:, :, 1::2] / np.maximum(np.abs(ref[:, :, 1::2]), lpg)).max())}}
+    ctx.close()
+    print(json.dumps(line))
+
+
+def run_correlation(args, wl: I.Workload):
+    """Correlations between evaluations and randomised grouping (Sec.
+    "Correlations between Wilson Loops", Sec. "Grouping Worldlines"): per
+    step, draw the ensemble, write every loop's W - 1 at every point (the
+    Wilson kernel in its per-loop mode), regroup the loops at random anew for
+    every point, and take Eq. corrcoef of every point with a reference point
+    over loops, fixed groups and shuffled groups.  The step's Wilson pass is
+    timed on its own for the roofline."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    q = 1 if len(wl.profiles) > 1 else 0
+    prof, rho, T = [wl.profiles[q]], [wl.rho[q]], [wl.T[q]]       # one tube: 4 GB of values
+    n_points = len(rho[0]) * len(T[0])
+    ref = (len(T[0]) // 2) * len(rho[0])                           # mid T, rho = 0
+    W = torch.empty((n_points, wl.n_loops, 2), dtype=torch.float64, device="cuda:0")
+
+    def step(timer=None):
+        ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+        if timer:
+            timer[0].record(stream)
+        ctx.wilson_loops(ens, prof, rho, T, prec=args.prec, out=W)
+        if timer:
+            timer[1].record(stream)
+        S, _ = ctx.group_sums_loops(W, wl.n_groups)
+        Ss, _ = ctx.group_sums_loops(W, wl.n_groups, shuffle=True, seed=wl.seed)
+        r = [ctx.corrcoef(W, ref, comp=1), ctx.corrcoef(S, ref, comp=1),
+             ctx.corrcoef(Ss, ref, comp=1)]
+        ens.free()
+        return r
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        n0 = ctx.launch_count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            for i in range(args.steps):
+                r = step(wk[i])
+            e1.record(stream)
+            stream.synchronize()
+        launches = ctx.launch_count - n0
+        ms = e0.elapsed_time(e1) / args.steps
+        kern_ms = statistics.mean(a.elapsed_time(b) for a, b in wk)
+        # end to end with host buffers: values stay on the device, the three
+        # correlation curves come back
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 2))
+        for _ in range(e2e_steps):
+            ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+            ctx.wilson_loops(ens, prof, rho, T, prec=args.prec, out=W)
+            S, _ = ctx.group_sums_loops(W, wl.n_groups)
+            Ss, _ = ctx.group_sums_loops(W, wl.n_groups, shuffle=True, seed=wl.seed)
+            rh = [ctx.corrcoef(W, ref, comp=1, where="host"), ctx.corrcoef(S, ref, comp=1, where="host"),
+                  ctx.corrcoef(Ss, ref, comp=1, where="host")]
+            ens.free()
+        stream.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    lp = wl.n_loops * n_points
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    seg = lp * wl.ppl
+    achieved = N_ALG_FP32 * seg / (kern_ms / 1e3) / 1e12
+    line = _common_line("loop-point evals/s (per-loop values + randomised groups + Eq. corrcoef)",
+                        lp / (ms / 1e3), "loop-point evals/s", args.steps, args.warmup, ms,
+                        "f32" if args.prec == "fp32" else "f64",
+                        {"workload": f"{wl.name}; one tube (F={prof[0].F}), per-loop values "
+                                     f"{W.numel() * 8 / 1e9:.1f} GB", "n_loops": wl.n_loops,
+                         "ppl": wl.ppl, "n_points": n_points, "n_groups": wl.n_groups,
+                         "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                        "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": None,
+                        "kernel": "wilson_kernel<F32Comp,4,8,loops>", "kernel_ms": kern_ms,
+                        "segment_evals_per_s": seg / (kern_ms / 1e3),
+                        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                      f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
+    line["e2e"] = {"value": lp / e2e_s, "unit": "loop-point evals/s", "h2d_bytes_per_step":
+                   int(sum(a.nbytes for a in rho + T)), "d2h_bytes_per_step": int(3 * n_points * 8)}
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clk.summary()
+    others = np.arange(n_points) != ref
+    line["corr_with_reference"] = {
+        "reference_point": {"T": float(T[0][ref // len(rho[0])]), "rho": 0.0},
+        "median_abs_loops": float(np.nanmedian(np.abs(rh[0][others]))),
+        "median_abs_groups": float(np.nanmedian(np.abs(rh[1][others]))),
+        "median_abs_shuffled_groups": float(np.nanmedian(np.abs(rh[2][others])))}
     ctx.close()
     print(json.dumps(line))
 

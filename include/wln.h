@@ -269,6 +269,20 @@ wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens,
                              const double* T, const int32_t* T_off,
                              int32_t n_groups, wln_prec prec, double* group_sums);
 
+/*
+ * Every loop's W - 1 at every point: the per-worldline values behind the
+ * correlation coefficients of Eq. corrcoef (Sec. "Correlations between
+ * Wilson Loops") and behind any regrouping (wln_group_sums_loops).
+ * Arguments and rules as wln_wilson_avg, without groups.
+ * loop_values: double[n_points][n_loops][2] = (W_scal - 1, W_ferm - 1),
+ * host or device (16 bytes per loop and point).
+ */
+wln_status wln_wilson_loops(wln_ctx* ctx, const wln_ensemble* ens,
+                            const wln_profile* profiles, int32_t n_profiles,
+                            const double* rho_cm, const int32_t* rho_off,
+                            const double* T, const int32_t* T_off, wln_prec prec,
+                            double* loop_values);
+
 /* -------------------------------------------------------------- statistics */
 
 /*
@@ -287,6 +301,43 @@ wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens,
 wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
                          int32_t n_groups, int32_t loops_per_group, int32_t comp,
                          double* mean, double* sem, double* jk_var, double* cov);
+
+/*
+ * Group sums from per-loop values (wln_wilson_loops), with the paper's
+ * randomised grouping as an option (Sec. "Grouping Worldlines": assign the
+ * worldlines to groups at random, anew for every evaluation of the
+ * integrand, so that the group means of different evaluations decorrelate).
+ *   shuffle == 0: group g holds loops g n/G .. (g+1) n/G - 1 (the grouping
+ *                 of wln_wilson_avg);
+ *   shuffle != 0: the loops of point p are put in the order a[0..n-1] of a
+ *                 Fisher-Yates shuffle: a = identity; for t = 0 .. n-2,
+ *                 i = n-1-t, j = (u (i+1)) >> 32, swap a[i], a[j], where u is
+ *                 word t mod 4 of Philox-4x32-10 at counter (t/4, p, 2, 0) with
+ *                 key (seed & 0xffffffff, seed >> 32); group g holds loops
+ *                 a[g n/G .. (g+1) n/G - 1].
+ * Each group is summed in that order.  group_sums: double[n_points][n_groups]
+ * [WLN_K]; WLN_C_SIN is NaN (the imaginary part is not in the per-loop
+ * values); the squares are sums of squared per-loop values.  perm:
+ * int32[n_points][n_loops], the order used (only with shuffle), or NULL.
+ * loop_values, group_sums and perm are host or device.  Rules: n_groups >= 2
+ * divides n_loops; n_points <= 2^32.
+ */
+wln_status wln_group_sums_loops(wln_ctx* ctx, const double* loop_values, int64_t n_points,
+                                int32_t n_loops, int32_t n_groups, int32_t shuffle,
+                                uint64_t seed, double* group_sums, int32_t* perm);
+
+/*
+ * Correlation coefficients of Eq. corrcoef between the evaluation in row ref
+ * and every row of x, over the row's samples:
+ *   r = sum (x - <x>)(y - <y>) / sqrt(sum (x - <x>)^2 sum (y - <y>)^2),
+ * element n of row r at x[(r n_samples + n) stride + comp]: per-loop values
+ * (n_samples = n_loops, stride 2, comp 0 scalar / 1 spinor) or group sums
+ * (n_samples = n_groups, stride WLN_K, comp WLN_C_*), giving the three
+ * curves of the paper's Fig. corr (loops, groups, shuffled groups).
+ * out: double[n_rows]; NaN for a row without spread.  Host or device.
+ */
+wln_status wln_corrcoef(wln_ctx* ctx, const double* x, int32_t n_rows, int32_t n_samples,
+                        int32_t stride, int32_t comp, int32_t ref, double* out);
 
 /*
  * Standard error in the mean over individual loops (Sec. "The Worldline

@@ -573,25 +573,27 @@ namespace {
 wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
                        int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
                        const double* T, const int32_t* T_off, int32_t n_groups,
-                       wln_prec prec, double* group_sums, bool levels) {
+                       wln_prec prec, double* group_sums, int mode) {
   if (!ctx || !ens || !group_sums) return fail(ctx, WLN_EINVAL, "null argument");
   if (prec != WLN_PREC_FP64 && prec != WLN_PREC_FP32_COMP && prec != WLN_PREC_FP32_NAIVE)
     return fail(ctx, WLN_EINVAL, "unknown precision");
   if (ens->device != ctx->device) return fail(ctx, WLN_EINVAL, "ensemble lives on another device");
-  if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
+  const bool per_loop = mode == kModeLoops;
+  if (per_loop) n_groups = 1;
+  else if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
     return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
-  if (levels && (ens->e.ppl % 4 != 0 || ens->e.ppl < 8))
+  if (mode == kModeLevels && (ens->e.ppl % 4 != 0 || ens->e.ppl < 8))
     return fail(ctx, WLN_EINVAL, "discretisation levels need ppl a multiple of 4 and >= 8");
   wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
   if (st != WLN_OK) return st;
   DeviceGuard guard(ctx->device);
-  const int K = levels ? WLN_KL : WLN_K;
+  const int K = mode == kModeLevels ? WLN_KL : WLN_K;
 
   Batch bt;
-  const int P = plan_points_per_lane(ctx, prec, levels);
+  const int P = plan_points_per_lane(ctx, prec, mode);
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl, P, bt);
   if (bt.n_points > (int64_t(1) << 31) - 1) return fail(ctx, WLN_EINVAL, "too many points");
-  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, levels);
+  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, mode);
 
   // Device layout of this call: work list | profiles | radii | partials | (host output)
   Carve cv;
@@ -599,9 +601,12 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
   const size_t o_rho = cv.take<double>(bt.rho.size());
   const size_t upload = cv.off;
-  const size_t n_partial = static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
+  const size_t n_partial =
+      per_loop ? 0 : static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
   const size_t o_part = cv.take<double>(n_partial);
-  Out out = plan_out(cv, group_sums, static_cast<size_t>(bt.n_points) * n_groups * K);
+  const size_t n_out = per_loop ? static_cast<size_t>(bt.n_points) * ens->e.n_loops * 2
+                                : static_cast<size_t>(bt.n_points) * n_groups * K;
+  Out out = plan_out(cv, group_sums, n_out);
   if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) return st;
   if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
   bind_out(out, ctx->scratch.ptr);
@@ -615,19 +620,27 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
   if (err != cudaSuccess) return cuda_fail(ctx, err, "upload work list");
 
-  const int32_t lpg = ens->e.n_loops / n_groups;
   int64_t launches = 0;
-  err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles), at<ProfileDev>(d, o_profs),
-                      at<double>(d, o_rho), n_groups, lpg, prec, at<double>(d, o_part),
-                      bt.n_points, ctx->d_flag, &launches);
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
-  err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
-                               n_groups, lpg, static_cast<double*>(out.dev));
-  ++launches;
-  ctx->launches += launches;
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "group reduction");
+  if (per_loop) {
+    err = launch_wilson_loops(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
+                              at<ProfileDev>(d, o_profs), at<double>(d, o_rho), prec,
+                              static_cast<double*>(out.dev), ctx->d_flag, &launches);
+    ctx->launches += launches;
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+  } else {
+    const int32_t lpg = ens->e.n_loops / n_groups;
+    err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
+                        at<ProfileDev>(d, o_profs), at<double>(d, o_rho), n_groups, lpg, prec,
+                        at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+    err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
+                                 n_groups, lpg, static_cast<double*>(out.dev));
+    ++launches;
+    ctx->launches += launches;
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "group reduction");
+  }
   if (out.host) {
-    if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy group sums");
+    if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy results");
     return check_flag(ctx);
   }
   return WLN_OK;
@@ -643,7 +656,7 @@ wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens, const wln_profi
                           const double* T, const int32_t* T_off, int32_t n_groups,
                           wln_prec prec, double* group_sums) {
   return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
-                     group_sums, false);
+                     group_sums, kModeSums);
 }
 
 wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
@@ -651,7 +664,89 @@ wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens, const wln_pr
                              const double* T, const int32_t* T_off, int32_t n_groups,
                              wln_prec prec, double* group_sums) {
   return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
-                     group_sums, true);
+                     group_sums, kModeLevels);
+}
+
+wln_status wln_wilson_loops(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,
+                            int32_t n_profiles, const double* rho_cm, const int32_t* rho_off,
+                            const double* T, const int32_t* T_off, wln_prec prec,
+                            double* loop_values) {
+  return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, 0, prec,
+                     loop_values, kModeLoops);
+}
+
+wln_status wln_group_sums_loops(wln_ctx* ctx, const double* loop_values, int64_t n_points,
+                                int32_t n_loops, int32_t n_groups, int32_t shuffle, uint64_t seed,
+                                double* group_sums, int32_t* perm) {
+  if (!ctx || !loop_values || !group_sums) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_points < 1 || n_loops < 1 || n_groups < 2 || n_loops % n_groups != 0)
+    return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
+  if (n_points > (int64_t(1) << 32)) return fail(ctx, WLN_EINVAL, "too many points");
+  DeviceGuard guard(ctx->device);
+  const size_t nW = static_cast<size_t>(n_points) * n_loops * 2;
+  const bool w_dev = is_device_ptr(loop_values);
+  Carve cv;
+  const size_t o_W = w_dev ? 0 : cv.take<double>(nW);
+  const bool need_perm = shuffle != 0;
+  const size_t o_perm = need_perm && !perm ? cv.take<int32_t>(static_cast<size_t>(n_points) * n_loops) : 0;
+  Out os = plan_out(cv, group_sums, static_cast<size_t>(n_points) * n_groups * WLN_K);
+  Out op = plan_out(cv, need_perm ? perm : static_cast<int32_t*>(nullptr),
+                    static_cast<size_t>(n_points) * n_loops);
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(os, ctx->scratch.ptr);
+  bind_out(op, ctx->scratch.ptr);
+  const double* W = loop_values;
+  cudaError_t err = cudaSuccess;
+  if (!w_dev) {
+    double* dW = at<double>(ctx->scratch.ptr, o_W);
+    err = cudaMemcpyAsync(dW, loop_values, nW * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    W = dW;
+  }
+  int32_t* dperm = nullptr;
+  if (need_perm) dperm = perm ? static_cast<int32_t*>(op.dev) : at<int32_t>(ctx->scratch.ptr, o_perm);
+  int64_t launches = 0;
+  if (err == cudaSuccess)
+    err = launch_group_sums_loops(ctx->stream, W, n_points, n_loops, n_groups, need_perm, seed,
+                                  dperm, static_cast<double*>(os.dev), &launches);
+  ctx->launches += launches;
+  if (err == cudaSuccess) err = copy_back(os, ctx->stream);
+  if (err == cudaSuccess && need_perm) err = copy_back(op, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "group sums of loop values");
+  if (os.host || op.host || !w_dev) return check_flag(ctx);
+  return WLN_OK;
+}
+
+wln_status wln_corrcoef(wln_ctx* ctx, const double* x, int32_t n_rows, int32_t n_samples,
+                        int32_t stride, int32_t comp, int32_t ref, double* out) {
+  if (!ctx || !x || !out) return fail(ctx, WLN_EINVAL, "null argument");
+  if (n_rows < 1 || n_samples < 2 || stride < 1 || comp < 0 || comp >= stride || ref < 0 ||
+      ref >= n_rows)
+    return fail(ctx, WLN_EINVAL, "bad correlation sizes");
+  DeviceGuard guard(ctx->device);
+  const size_t nX = static_cast<size_t>(n_rows) * n_samples * stride;
+  const bool x_dev = is_device_ptr(x);
+  Carve cv;
+  const size_t o_X = x_dev ? 0 : cv.take<double>(nX);
+  Out oo = plan_out(cv, out, static_cast<size_t>(n_rows));
+  wln_status st = ensure_scratch(ctx, cv.off + 256);
+  if (st != WLN_OK) return st;
+  bind_out(oo, ctx->scratch.ptr);
+  const double* X = x;
+  cudaError_t err = cudaSuccess;
+  if (!x_dev) {
+    double* dX = at<double>(ctx->scratch.ptr, o_X);
+    err = cudaMemcpyAsync(dX, x, nX * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    X = dX;
+  }
+  if (err == cudaSuccess)
+    err = launch_corrcoef(ctx->stream, X, n_rows, n_samples, stride, comp, ref,
+                          static_cast<double*>(oo.dev));
+  ++ctx->launches;
+  if (err == cudaSuccess) err = copy_back(oo, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "correlation coefficients");
+  if (oo.host || !x_dev) return check_flag(ctx);
+  return WLN_OK;
 }
 
 wln_status wln_extrapolate(wln_ctx* ctx, const double* level_sums, int32_t n_points,

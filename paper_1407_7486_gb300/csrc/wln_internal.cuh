@@ -19,6 +19,30 @@ namespace wln {
 // conflict-free 16-byte load per lane.
 constexpr int kLanes = 32;
 
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies with the round keys bumped by the Weyl
+// constants.  Streams in use: counter (j, loop, 0, 0) increments of
+// wln_gen_loops; (m/2, loop, 1, 0) Gaussians of wln_gen_dloops; (t/4, point,
+// 2, 0) the Fisher-Yates draws of the randomised groups.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
 // Device error flag values (bounded waits that ran out).
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
@@ -59,6 +83,10 @@ struct Tile {
   int32_t pad;
 };
 
+// What a Wilson launch produces: group sums (WLN_K per point and group), the
+// discretisation levels (WLN_KL), or every loop's W - 1 (scalar, spinor).
+constexpr int kModeSums = 0, kModeLevels = 1, kModeLoops = 2;
+
 // Geometry of one Wilson launch.
 struct WilsonPlan {
   int P;              // points (radii) per lane
@@ -71,7 +99,7 @@ struct WilsonPlan {
   int n_chains;       // ceil(n_blocks / chain)
   int64_t n_items;    // n_chains * n_tile_groups
   int grid;           // persistent CTAs
-  bool levels;        // discretisation-level pass (WLN_KL components)
+  int mode;           // kModeSums, kModeLevels or kModeLoops
 };
 
 struct Scratch {
@@ -142,14 +170,25 @@ cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
 
 // Wilson loops (wln_wilson.cu).
-// levels: the discretisation-level pass (K = WLN_KL components per point).
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
-                     bool levels = false);
-int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, bool levels = false);
+                     int mode = kModeSums);
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode = kModeSums);
 cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                           double* partial, int64_t n_points, int* d_flag, int64_t* launches);
+// Per-loop values: out[p][loop][2] = (W_scal - 1, W_ferm - 1), p the point.
+cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                                const Tile* tiles, const ProfileDev* profs, const double* rho,
+                                wln_prec prec, double* out, int* d_flag, int64_t* launches);
+// Group sums [n_points][G][WLN_K] of per-loop values [n_points][n_loops][2],
+// contiguous groups or (shuffle) a Fisher-Yates permutation per point;
+// perm: [n_points][n_loops] scratch (and output) for the shuffled order.
+cudaError_t launch_group_sums_loops(cudaStream_t s, const double* W, int64_t n_points,
+                                    int32_t n_loops, int32_t G, bool shuffle, uint64_t seed,
+                                    int32_t* perm, double* S, int64_t* launches);
+cudaError_t launch_corrcoef(cudaStream_t s, const double* X, int32_t n_rows, int32_t n_samples,
+                            int32_t stride, int32_t comp, int32_t ref, double* out);
 cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns);
 cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                                    const double* partial, int64_t n_points, int32_t n_groups,

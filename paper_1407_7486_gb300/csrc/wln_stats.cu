@@ -2,6 +2,8 @@
 // precision (paper Sec. "Grouping Worldlines"; Eq. cylEA; Sec. "Computing an
 // Effective Action").  Every sum runs in a fixed order, so results do not
 // depend on scheduling.
+#include <math_constants.h>
+
 #include "wln_internal.cuh"
 
 namespace wln {
@@ -370,6 +372,86 @@ __global__ void integrand_kernel(const QuadProfile* qp, const int32_t* point_pro
   out[p * 3 + 2] = pref * lcf_bracket(et, sp);
 }
 
+// ------------------------------------- randomised groups and correlations
+// Fisher-Yates shuffle of the loops of every evaluation (one thread per
+// point): for t = 0 .. n-2, i = n-1-t, j = (u (i + 1)) >> 32 with u word
+// t mod 4 of Philox-4x32-10 at counter (t/4, point, 2, 0), swap a[i], a[j].
+__global__ void shuffle_kernel(int64_t n_points, int32_t n, uint32_t k0, uint32_t k1,
+                               int32_t* perm) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n_points) return;
+  int32_t* a = perm + p * n;
+  for (int32_t k = 0; k < n; ++k) a[k] = k;
+  uint4 u = make_uint4(0u, 0u, 0u, 0u);
+  for (int32_t t = 0; t < n - 1; ++t) {
+    if ((t & 3) == 0)
+      u = philox4x32_10(make_uint4(static_cast<uint32_t>(t >> 2), static_cast<uint32_t>(p), 2u, 0u),
+                        k0, k1);
+    const uint32_t w = (t & 3) == 0 ? u.x : (t & 3) == 1 ? u.y : (t & 3) == 2 ? u.z : u.w;
+    const int32_t i = n - 1 - t;
+    const int32_t j = static_cast<int32_t>((static_cast<uint64_t>(w) * static_cast<uint64_t>(i + 1)) >> 32);
+    const int32_t x = a[i];
+    a[i] = a[j];
+    a[j] = x;
+  }
+}
+
+// Group sums of per-loop values W[p][l] = (W_scal - 1, W_ferm - 1): group g
+// of point p holds the loops at positions g n/G .. (g+1) n/G - 1 of the
+// point's order (perm, or the generation order), summed in that order.
+// Layout [p][g][WLN_K]; the imaginary part is not kept per loop: NaN.
+__global__ void group_sums_loops_kernel(const double2* W, int64_t n_points, int32_t n, int32_t G,
+                                        const int32_t* perm, double* S) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n_points * G) return;
+  const int64_t p = i / G;
+  const int g = static_cast<int>(i % G);
+  const int lpg = n / G;
+  const double2* w = W + p * n;
+  const int32_t* a = perm ? perm + p * n : nullptr;
+  double s0 = 0.0, s1 = 0.0, q0 = 0.0, q1 = 0.0;
+  for (int k = g * lpg; k < (g + 1) * lpg; ++k) {
+    const double2 v = w[a ? a[k] : k];
+    s0 += v.x; s1 += v.y;
+    q0 += v.x * v.x; q1 += v.y * v.y;
+  }
+  double* o = S + i * kComps;
+  o[WLN_C_SCAL] = s0; o[WLN_C_FERM] = s1; o[WLN_C_SIN] = CUDART_NAN;
+  o[WLN_C_SCAL_SQ] = q0; o[WLN_C_FERM_SQ] = q1;
+}
+
+// Eq. corrcoef between row ref and every row of X over its samples, one warp
+// per row: x(r, n) = X[(r n_samples + n) stride + comp].  Two passes (means,
+// then centred sums) with lanes striding the samples and a fixed butterfly.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void corrcoef_kernel(const double* X, int32_t n_rows, int32_t n_samples,
+                                int32_t stride, int32_t comp, int32_t ref, double* out) {
+  const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const double* x = X + row * static_cast<int64_t>(n_samples) * stride + comp;
+  const double* y = X + static_cast<int64_t>(ref) * n_samples * stride + comp;
+  double sx = 0.0, sy = 0.0;
+  for (int n = lane; n < n_samples; n += 32) {
+    sx += x[static_cast<int64_t>(n) * stride];
+    sy += y[static_cast<int64_t>(n) * stride];
+  }
+  const double mx = warp_sum(sx) / n_samples, my = warp_sum(sy) / n_samples;
+  double sxy = 0.0, sxx = 0.0, syy = 0.0;
+  for (int n = lane; n < n_samples; n += 32) {
+    const double dx = x[static_cast<int64_t>(n) * stride] - mx;
+    const double dy = y[static_cast<int64_t>(n) * stride] - my;
+    sxy += dx * dy; sxx += dx * dx; syy += dy * dy;
+  }
+  sxy = warp_sum(sxy); sxx = warp_sum(sxx); syy = warp_sum(syy);
+  if (lane == 0) out[row] = sxy / sqrt(sxx * syy);
+}
+
 __global__ void group_mean_sem_kernel(const double* x, int32_t n_rows, int32_t G, double* out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_rows) return;
@@ -404,6 +486,31 @@ cudaError_t launch_extrapolate(cudaStream_t s, const double* level_sums, int32_t
   const int64_t n = 2 * static_cast<int64_t>(n_points);
   extrapolate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(level_sums, n_points,
                                                                            G, lpg, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_sums_loops(cudaStream_t s, const double* W, int64_t n_points,
+                                    int32_t n_loops, int32_t G, bool shuffle, uint64_t seed,
+                                    int32_t* perm, double* S, int64_t* launches) {
+  cudaError_t err = cudaSuccess;
+  if (shuffle) {
+    shuffle_kernel<<<static_cast<unsigned>((n_points + 127) / 128), 128, 0, s>>>(
+        n_points, n_loops, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), perm);
+    ++*launches;
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const int64_t n = n_points * G;
+  group_sums_loops_kernel<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(
+      reinterpret_cast<const double2*>(W), n_points, n_loops, G, shuffle ? perm : nullptr, S);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corrcoef(cudaStream_t s, const double* X, int32_t n_rows, int32_t n_samples,
+                            int32_t stride, int32_t comp, int32_t ref, double* out) {
+  const int64_t threads = static_cast<int64_t>(n_rows) * 32;
+  corrcoef_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(
+      X, n_rows, n_samples, stride, comp, ref, out);
   return cudaGetLastError();
 }
 

@@ -206,6 +206,7 @@ struct KParams {
   int32_t n_tile_groups, n_chains;
   int64_t n_items;
   int* flag;
+  double* loops_out;     // per-loop mode: [n_points][n_loops][2]
 };
 
 // Per-lane walk of one loop for the P radii of a tile (flux tube).
@@ -462,13 +463,16 @@ __device__ __forceinline__ void level_terms(double ph, double sp, F2 tp, F2 st, 
 // Per-lane W terms are added into the warp's shared-memory accumulators
 // acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
 // flush sums each row over the lanes in lane order and writes the partial
-// of (chain, group).  LV selects the discretisation levels (K = WLN_KL):
-// walks w[0..2] are the circle, square and triangle sub-loops.
-template <class A, int P, class WalkT, bool LV>
+// of (chain, group).  MODE kModeLevels walks the circle, square and triangle
+// sub-loops (w[0..2], K = WLN_KL); kModeLoops writes every loop's W - 1 to
+// global memory instead of accumulating (lanes store 32 consecutive loops).
+template <class A, int P, class WalkT, int MODE>
 __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const Tile& tile,
                          const ProfileDev& prof, bool active, volatile int* abort_flag,
                          int lane) {
   using F = typename A::F;
+  constexpr bool LV = MODE == kModeLevels;
+  constexpr bool PL = MODE == kModeLoops;
   constexpr int K = LV ? kLevelComps : kComps;
   constexpr int NW = LV ? 3 : 1;
   constexpr int V = P * K;
@@ -490,6 +494,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   int g_cur = (b0 * 32) / k.lpg;
 
   auto flush = [&](int g) {
+    if (PL) return;
     __syncwarp();
     if (active) {
       double* dst = k.partial + tile.part_base +
@@ -586,6 +591,21 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       w[q].step(fx[q], fy[q]);  // closing segment back to the walk's first point
       w[q].fold();
     }
+    if constexpr (PL) {
+      if (valid) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          if (p < tile.n_valid) {
+            double ps, pc, ss, sc, t[kComps];
+            w[0].raw(p, ps, pc, ss, sc);
+            wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, t);
+            reinterpret_cast<double2*>(k.loops_out)[static_cast<int64_t>(tile.p0 + p) * k.n_loops + loop] =
+                make_double2(t[0], t[1]);
+          }
+        }
+      }
+      continue;
+    }
     const int g_lane = valid ? loop / k.lpg : -1;
     const int g_lo = (b * 32) / k.lpg;
     const int g_hi = min(b * 32 + 31, k.n_loops - 1) / k.lpg;
@@ -635,9 +655,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 // The plain pass keeps 16 warps per SM (at most 128 registers a thread); the
 // level pass holds three walks per radius and runs 8 warps per SM with up to
 // 255 registers, which measured faster than spilling at 16.
-template <class A, int P, int WARPS, bool LV>
-__global__ void __launch_bounds__(WARPS * 32, (LV ? 256 : 512) / (WARPS * 32)) wilson_kernel(const KParams k) {
-  constexpr int K = LV ? kLevelComps : kComps;
+template <class A, int P, int WARPS, int MODE>
+__global__ void __launch_bounds__(WARPS * 32, (MODE == kModeLevels ? 256 : 512) / (WARPS * 32)) wilson_kernel(const KParams k) {
+  constexpr int K = MODE == kModeLevels ? kLevelComps : kComps;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
 
@@ -681,9 +701,9 @@ __global__ void __launch_bounds__(WARPS * 32, (LV ? 256 : 512) / (WARPS * 32)) w
     const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
     const ProfileDev prof = k.profs[tile.profile];
     if (prof.kind == WLN_PROFILE_CONST_B)
-      ok = run_item<A, P, WalkB<A, P>, LV>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+      ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
     else
-      ok = run_item<A, P, Walk<A, P>, LV>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+      ok = run_item<A, P, Walk<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -723,9 +743,9 @@ __global__ void reduce_partials_kernel(const double* partial, int64_t n_points, 
   out[i] = s;
 }
 
-template <class A, int P, int WARPS, bool LV>
+template <class A, int P, int WARPS, int MODE>
 cudaError_t launch_t(cudaStream_t s, const KParams& kp, int grid, size_t smem) {
-  auto kern = wilson_kernel<A, P, WARPS, LV>;
+  auto kern = wilson_kernel<A, P, WARPS, MODE>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -733,10 +753,10 @@ cudaError_t launch_t(cudaStream_t s, const KParams& kp, int grid, size_t smem) {
   return cudaGetLastError();
 }
 
-template <class A, int P, int WARPS, bool LV>
+template <class A, int P, int WARPS, int MODE>
 int occupancy(size_t smem) {
   int n = 0;
-  auto kern = wilson_kernel<A, P, WARPS, LV>;
+  auto kern = wilson_kernel<A, P, WARPS, MODE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 1;
@@ -747,7 +767,7 @@ int occupancy(size_t smem) {
 
 size_t smem_bytes(const WilsonPlan& p, int ppl) {
   const int chunk_rows = p.rows < ppl / 2 ? p.rows : ppl / 2;
-  const int K = p.levels ? kLevelComps : kComps;
+  const int K = p.mode == kModeLevels ? kLevelComps : kComps;
   return static_cast<size_t>(p.stages) * chunk_rows * 512 +
          static_cast<size_t>(p.warps) * p.P * K * 33 * sizeof(double) +
          2 * p.stages * sizeof(uint64_t);
@@ -759,19 +779,20 @@ size_t smem_bytes(const WilsonPlan& p, int ppl) {
 // own shape (2 radii per lane, 4 warps).  The discretisation levels run three
 // walks per radius (4 radii per lane, FP64 1) and ignore the tuning of the
 // plain pass.
-int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, bool levels) {
-  if (levels) return prec == WLN_PREC_FP64 ? 1 : 4;
+int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode) {
+  if (mode == kModeLevels) return prec == WLN_PREC_FP64 ? 1 : 4;
+  if (mode == kModeLoops) return prec == WLN_PREC_FP64 ? 2 : 4;
   if (prec == WLN_PREC_FP64) return 2;
   return ctx->tune_P ? ctx->tune_P : 4;
 }
 
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
-                     bool levels) {
+                     int mode) {
   WilsonPlan p{};
-  p.P = plan_points_per_lane(ctx, prec, levels);
-  p.levels = levels;
+  p.P = plan_points_per_lane(ctx, prec, mode);
+  p.mode = mode;
   const bool f64 = prec == WLN_PREC_FP64;
-  const bool fixed = f64 || levels;   // shapes that ignore the tuning
+  const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : 8);
   p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
   p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
@@ -792,12 +813,16 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   return p;
 }
 
-cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble& e,
-                          const Tile* tiles, const ProfileDev* profs, const double* rho,
-                          int32_t n_groups, int32_t loops_per_group, wln_prec prec,
-                          double* partial, int64_t n_points, int* d_flag, int64_t* launches) {
+namespace {
+
+cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble& e,
+                       const Tile* tiles, const ProfileDev* profs, const double* rho,
+                       int32_t n_groups, int32_t loops_per_group, wln_prec prec,
+                       double* partial, int64_t n_points, int* d_flag, int64_t* launches,
+                       double* loops_out) {
   WilsonPlan plan = plan_in;
   KParams kp{};
+  kp.loops_out = loops_out;
   kp.blocks = e.blocks; kp.n_blocks = e.n_blocks; kp.ppl = e.ppl; kp.n_loops = e.n_loops;
   kp.tiles = tiles; kp.n_tiles = plan.n_tiles; kp.profs = profs; kp.rho = rho;
   kp.lpg = loops_per_group; kp.G = n_groups; kp.partial = partial; kp.n_points = n_points;
@@ -808,20 +833,28 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensem
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-#define WLN_CASE_L(A, P_, W_, LV_)                                                   \
-  if (plan.P == P_ && plan.warps == W_ && plan.levels == LV_) {                      \
-    const int occ = occupancy<A, P_, W_, LV_>(smem);                                 \
+#define WLN_CASE_L(A, P_, W_, M_)                                                    \
+  if (plan.P == P_ && plan.warps == W_ && plan.mode == M_) {                         \
+    const int occ = occupancy<A, P_, W_, M_>(smem);                                  \
     const int64_t g = static_cast<int64_t>(sms) * occ;                               \
     const int grid = static_cast<int>(g < plan.n_items ? g : plan.n_items);          \
     ++*launches;                                                                     \
-    return launch_t<A, P_, W_, LV_>(s, kp, grid, smem);                              \
+    return launch_t<A, P_, W_, M_>(s, kp, grid, smem);                               \
   }
-#define WLN_CASE(A, P_, W_) WLN_CASE_L(A, P_, W_, false)
-  if (plan.levels) {
+#define WLN_CASE(A, P_, W_) WLN_CASE_L(A, P_, W_, kModeSums)
+  if (plan.mode == kModeLevels) {
     switch (prec) {
-      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, true) break;
-      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, true) break;
-      case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, true) break;
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, kModeLevels) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, kModeLevels) break;
+      case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, kModeLevels) break;
+    }
+    return cudaErrorInvalidConfiguration;
+  }
+  if (plan.mode == kModeLoops) {
+    switch (prec) {
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, kModeLoops) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, kModeLoops) break;
+      case WLN_PREC_FP64: WLN_CASE_L(F64, 2, 4, kModeLoops) break;
     }
     return cudaErrorInvalidConfiguration;
   }
@@ -844,6 +877,24 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan_in, const Ensem
   return cudaErrorInvalidConfiguration;
 }
 
+}  // namespace
+
+cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                          const Tile* tiles, const ProfileDev* profs, const double* rho,
+                          int32_t n_groups, int32_t loops_per_group, wln_prec prec,
+                          double* partial, int64_t n_points, int* d_flag, int64_t* launches) {
+  return launch_any(s, plan, e, tiles, profs, rho, n_groups, loops_per_group, prec, partial,
+                    n_points, d_flag, launches, nullptr);
+}
+
+cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
+                                const Tile* tiles, const ProfileDev* profs, const double* rho,
+                                wln_prec prec, double* out, int* d_flag, int64_t* launches) {
+  // groups play no part; lpg = n_loops keeps the group arithmetic in range
+  return launch_any(s, plan, e, tiles, profs, rho, 1, e.n_loops, prec, nullptr, 0, d_flag,
+                    launches, out);
+}
+
 cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns) {
   selftest_wait_kernel<<<1, 32, 0, s>>>(d_flag, limit_ns);
   return cudaGetLastError();
@@ -853,7 +904,7 @@ cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const
                                    const double* partial, int64_t n_points, int32_t n_groups,
                                    int32_t loops_per_group, double* group_sums) {
   (void)e;
-  const int K = plan.levels ? kLevelComps : kComps;
+  const int K = plan.mode == kModeLevels ? kLevelComps : kComps;
   const int64_t n = n_points * n_groups * K;
   if (n == 0) return cudaSuccess;
   reduce_partials_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(

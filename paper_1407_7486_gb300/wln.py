@@ -54,6 +54,10 @@ SIGNATURES = {
     "wln_mapped_grid": ([_I32, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
     "wln_effective_action_full": ([_P, _P, _I32, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
                                    _P, _P, _P], ctypes.c_int),
+    "wln_wilson_loops": ([_P, _P, _P, _I32, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "wln_group_sums_loops": ([_P, _P, _I64, _I32, _I32, _I32, ctypes.c_uint64, _P, _P],
+                             ctypes.c_int),
+    "wln_corrcoef": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
@@ -348,6 +352,47 @@ class Context:
         out = self._empty((n_points, 2, 6), np.float64, where)
         self._check(load().wln_extrapolate(self.handle, _ptr(level_sums), n_points, n_groups,
                                            loops_per_group, _ptr(out)))
+        return out
+
+    def wilson_loops(self, ens: Ensemble, profiles: Sequence[Profile], rho: Sequence, T: Sequence,
+                     prec: str = "fp32", out=None, where: str = "device"):
+        """Every loop's W - 1 at every point: [n_points][n_loops][2] (scalar, spinor)."""
+        rho_f, rho_off = _csr(rho)
+        T_f, T_off = _csr(T)
+        n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
+        if out is None:
+            out = self._empty((n_points, ens.n_loops, 2), np.float64, where)
+        profs = _profiles(profiles)
+        self._check(load().wln_wilson_loops(self.handle, ens.handle, profs, len(profiles),
+                                            _ptr(rho_f), _ptr(rho_off), _ptr(T_f), _ptr(T_off),
+                                            PREC[prec], _ptr(out)))
+        return out
+
+    def group_sums_loops(self, loop_values, n_groups: int, shuffle: bool = False, seed: int = 0,
+                         with_perm: bool = False, where: str = "device"):
+        """Group sums [n_points][G][5] of per-loop values, contiguous groups or a
+        random grouping per point; returns (sums, order or None)."""
+        n_points, n_loops = int(loop_values.shape[0]), int(loop_values.shape[1])
+        S = self._empty((n_points, n_groups, WLN_K), np.float64, where)
+        perm = None
+        if shuffle and with_perm:
+            if where == "host":
+                perm = np.empty((n_points, n_loops), np.int32)
+            else:
+                import torch
+                perm = torch.empty((n_points, n_loops), dtype=torch.int32,
+                                   device=f"cuda:{self.device}")
+        self._check(load().wln_group_sums_loops(self.handle, _ptr(loop_values), n_points, n_loops,
+                                                n_groups, int(bool(shuffle)), seed, _ptr(S),
+                                                _ptr(perm)))
+        return S, perm
+
+    def corrcoef(self, x, ref: int, comp: int = 0, where: str = "device"):
+        """Eq. corrcoef of every row of x ([rows][samples][stride]) with row ref."""
+        n_rows, n_samples, stride = (int(v) for v in x.shape)
+        out = self._empty((n_rows,), np.float64, where)
+        self._check(load().wln_corrcoef(self.handle, _ptr(x), n_rows, n_samples, stride, comp,
+                                        ref, _ptr(out)))
         return out
 
     # --------------------------------------------------------- statistics
