@@ -38,12 +38,14 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # Algorithmic FP32 operations per (segment, point) of the compensated walk,
 # counted from the formulas in csrc/wln_wilson.cu (an FMA, a min/max or a
-# select each count 1): 19 per radius for the geometry, the closed-form
-# integrals, the products and the two partial sums; 17 for the arctangent
-# (range fold 2, quotient 1, square 1, polynomial 8, octant unfolding 4,
-# plus t*s 1); 11 per segment shared by the lane's P = 4 radii (11/4); and
-# two Kahan folds of 4 operations every 8 segments (1).
-N_ALG_FP32 = 19 + 17 + 11 / 4 + 1
+# select each count 1): 18 per radius for the geometry, the closed-form
+# integrals (theta = atan2(sqrt(D), Q0 + B)), the products and the two partial
+# sums; 17 for the arctangent (range fold 2, quotient 1, square 1, polynomial
+# 8, octant unfolding 4, plus t*s 1); 11 per segment shared by the lane's
+# P = 4 radii (11/4); and two Kahan folds of 4 operations every 8 segments (1).
+# The level pass keeps theta = atan2(C sqrt(D), D + B (B + C)): 19 per radius.
+N_ALG_FP32 = 18 + 17 + 11 / 4 + 1
+N_ALG_FP32_LEVELS = 19 + 17 + 11 / 4 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 
 
@@ -434,7 +436,7 @@ def main():
                    "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                      "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "wilson_kernel<F32Comp,4,8>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
+                     "kernel": "wilson_kernel<F32Comp,4,4>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
                      "kernel_ms": wilson_ms,
                      "segment_evals_per_s": seg / (wilson_ms / 1e3),
                      "n_alg_fp32_per_segment": N_ALG_FP32, "n_alg_mufu_per_segment": N_ALG_MUFU,
@@ -593,7 +595,7 @@ def run_levels(args, wl: I.Workload):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     seg = wl.segment_evals            # circle N/2 + square N/4 + triangle N/4 = N per loop and point
-    achieved = N_ALG_FP32 * seg / (kern_ms / 1e3) / 1e12
+    achieved = N_ALG_FP32_LEVELS * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation)",
                         wl.loop_points / (ms / 1e3), "loop-point evals/s", args.steps,
                         args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
@@ -605,7 +607,7 @@ def run_levels(args, wl: I.Workload):
                         "traffic": _ncu_traffic(f"wilson_levels_{args.workload}"),
                         "kernel": "wilson_kernel<F32Comp,4,8,levels>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
-                        "n_alg_fp32_per_segment": N_ALG_FP32,
+                        "n_alg_fp32_per_segment": N_ALG_FP32_LEVELS,
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",

@@ -1,7 +1,8 @@
 """Autotuner of the Wilson kernel's work decomposition.
 
-The kernel's shape parameters are searched: radii per lane P (points per
-thread: register pressure against reuse of each staged loop segment), the
+The kernel's shape parameters are searched: radii per lane P and warps per
+CTA (register pressure and occupancy against reuse of each staged loop
+segment: (P, warps) in (2, 8), (4, 4), (4, 8), (8, 8)), the
 float4 rows of loop data per staged chunk (loops-per-CTA tile: 32 loops x
 rows), and the number of chunks in flight.  Each candidate is timed with
 CUDA events on a probe: the caller's own profiles, truncated to about
@@ -25,7 +26,8 @@ from .inputs import Profile
 from . import wln
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "wln", "autotune.json")
-CANDIDATES = {"P": (2, 4), "rows": (16, 32, 64), "stages": (2, 3, 4)}
+CANDIDATES = {"shape": ((2, 8), (4, 4), (4, 8), (8, 8)), "rows": (16, 32, 64),
+              "stages": (2, 3, 4)}
 
 
 def _key(ens: "wln.Ensemble", prec: str) -> str:
@@ -68,25 +70,25 @@ def _probe(profiles, rho, T, n_loops, ppl, seg_per_s, seconds):
 def tune(ctx: "wln.Context", ens: "wln.Ensemble", profiles: Sequence[Profile], rho, T,
          n_groups: int, prec: str = "fp32", probe_seconds: float = 0.05, use_cache: bool = True,
          verbose: bool = False) -> dict:
-    """Pick (P, rows, stages) for this ensemble and precision; returns the choice
+    """Pick (P, warps, rows, stages) for this ensemble and precision; returns the choice
     and the probe timings, and leaves it set on ctx."""
     import torch
     if prec == "fp64":
         ctx.set_tuning()
-        return {"P": 2, "rows": 32, "stages": 3, "source": "fixed for fp64"}
+        return {"P": 2, "warps": 4, "rows": 32, "stages": 3, "source": "fixed for fp64"}
     key = _key(ens, prec)
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
-            ctx.set_tuning(hit["P"], 8, hit["rows"], hit["stages"], 0)
+            ctx.set_tuning(hit["P"], hit.get("warps", 8), hit["rows"], hit["stages"], 0)
             return dict(hit, source="cache")
     pr, r, t, n_pts = _probe(profiles, rho, T, ens.n_loops, ens.ppl, 7e11, probe_seconds)
     stream = ctx.stream
     results = []
     t0 = time.perf_counter()
-    for P, rows, stages in itertools.product(CANDIDATES["P"], CANDIDATES["rows"],
-                                             CANDIDATES["stages"]):
-        ctx.set_tuning(P, 8, rows, stages, 0)
+    for (P, warps), rows, stages in itertools.product(CANDIDATES["shape"], CANDIDATES["rows"],
+                                                      CANDIDATES["stages"]):
+        ctx.set_tuning(P, warps, rows, stages, 0)
         b = wln.Batch(ctx, ens, pr, r, t, n_groups, prec=prec)
         b.run(graph=False)                       # warm-up
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -97,13 +99,14 @@ def tune(ctx: "wln.Context", ens: "wln.Ensemble", profiles: Sequence[Profile], r
         z.synchronize()
         ms = a.elapsed_time(z) / 2
         seg = n_pts * ens.n_loops * ens.ppl / (ms / 1e3)
-        results.append({"P": P, "rows": rows, "stages": stages, "ms": ms, "seg_per_s": seg})
+        results.append({"P": P, "warps": warps, "rows": rows, "stages": stages, "ms": ms,
+                        "seg_per_s": seg})
         b.free()
         if verbose:
             print(results[-1])
     best = max(results, key=lambda x: x["seg_per_s"])
-    ctx.set_tuning(best["P"], 8, best["rows"], best["stages"], 0)
-    entry = {"P": best["P"], "rows": best["rows"], "stages": best["stages"],
+    ctx.set_tuning(best["P"], best["warps"], best["rows"], best["stages"], 0)
+    entry = {"P": best["P"], "warps": best["warps"], "rows": best["rows"], "stages": best["stages"],
              "seg_per_s": best["seg_per_s"], "probe_points": n_pts,
              "tuning_seconds": time.perf_counter() - t0, "candidates": results}
     _store(key, entry)

@@ -84,13 +84,15 @@ extern "C" {
 wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, int32_t rows,
                           int32_t stages, int32_t chain_blocks) {
   if (!ctx) return WLN_EINVAL;
-  const bool p_ok = points_per_lane == 0 || points_per_lane == 2 || points_per_lane == 4;
-  const bool w_ok = warps == 0 || warps == 8;
+  // instantiated shapes (radii per lane, warps per CTA): (2, 8), (4, 4), (4, 8), (8, 8)
+  const int P = points_per_lane ? points_per_lane : 4;
+  const bool p_ok = P == 2 || P == 4 || P == 8;
+  const bool w_ok = warps == 0 || warps == 8 || (warps == 4 && P == 4);
   const bool r_ok = rows == 0 || (rows >= 2 && rows <= 256 && (rows & (rows - 1)) == 0);
   const bool s_ok = stages == 0 || (stages >= 2 && stages <= 8);
   if (!p_ok || !w_ok || !r_ok || !s_ok || chain_blocks < 0)
-    return fail(ctx, WLN_EINVAL, "tuning: P in {2,4}, warps 8, rows a power of two <= 256, "
-                                 "stages 2..8, chain >= 0 (0 = automatic)");
+    return fail(ctx, WLN_EINVAL, "tuning: (P, warps) in (2, 8), (4, 4), (4, 8), (8, 8), rows a "
+                                 "power of two <= 256, stages 2..8, chain >= 0 (0 = automatic)");
   ctx->tune_P = points_per_lane;
   ctx->tune_warps = warps;
   ctx->tune_rows = rows;

@@ -7,7 +7,8 @@
 // With d = r_{k+1} - r_k, Q(t) = lambda^2 + |r + t d|^2 = C t^2 + 2 B t + Q0:
 //   C = |d|^2, B = r.d, X = r x d, D = lambda^2 C + X^2 (the discriminant,
 //   by the Lagrange identity |r|^2 |d|^2 - (r.d)^2 = X^2),
-//   int_0^1 dt/Q   = theta / sqrt(D),  theta = atan2(C sqrt(D), D + B (B + C)),
+//   int_0^1 dt/Q   = theta / sqrt(D),  theta = atan2(C sqrt(D), D + B (B + C))
+//                  = atan2(sqrt(D), Q0 + B)  (Q0 C = D + B^2),
 //   int_0^1 dt/Q^2 = [(C + B)/Q1 - B/Q0 + C int dt/Q] / (2 D), where
 //   (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1) since Q1 = Q0 + 2B + C.
 // The flux tube f = rho^2/(lambda^2 + rho^2) has f/rho^2 = 1/Q, so the phase
@@ -209,8 +210,11 @@ struct KParams {
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
 };
 
-// Per-lane walk of one loop for the P radii of a tile (flux tube).
-template <class A, int P>
+// Per-lane walk of one loop for the P radii of a tile (flux tube).  CQ
+// carries Q at the current point so that theta = atan2(sqrt(D), Q0 + B)
+// (one multiply fewer per segment and radius, one register more per radius);
+// without it theta = atan2(C sqrt(D), D + B (B + C)).
+template <class A, int P, bool CQ = true>
 struct Walk {
   using F = typename A::F;
   F s, l2;           // sqrt(T), lambda^2
@@ -219,7 +223,7 @@ struct Walk {
   F ux, uy;          // unit-loop point
   F ry;              // scaled y (shared by the radii)
   F rx[P];           // shifted, scaled x
-  F rq[P];           // 1/Q at the current point
+  F q[P], rq[P];     // Q and 1/Q at the current point
   Acc<F, A::kCompensated> ph[P], sp[P];
 
   __device__ __forceinline__ void start(F x0, F y0) {
@@ -229,7 +233,9 @@ struct Walk {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       rx[p] = fma(s, x0, rho[p]);
-      rq[p] = A::rcp(fma(rx[p], rx[p], e0));
+      const F q0 = fma(rx[p], rx[p], e0);
+      if (CQ) q[p] = q0;
+      rq[p] = A::rcp(q0);
       ph[p].zero();
       sp[p].zero();
     }
@@ -246,13 +252,16 @@ struct Walk {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const F rx1 = fma(s, x1, rho[p]);
-      const F rq1 = A::rcp(fma(rx1, rx1, e1));
+      const F q1 = fma(rx1, rx1, e1);
+      const F rq1 = A::rcp(q1);
       const F B = fma(rx[p], dx, rydy);
       const F X = fma(rx[p], dy, -rydx);
       const F D = fma(X, X, l2C);
       const F rsD = A::rsq(D);
       const F BC = B + C;
-      const F theta = A::at2(C * (D * rsD), fma(B, BC, D));
+      // atan2(C sqrt(D), D + B (B + C)) with the common factor C removed:
+      // Q0 C = D + B^2 (Lagrange), so D + B (B + C) = C (Q0 + B).
+      const F theta = CQ ? A::at2(D * rsD, q[p] + B) : A::at2(C * (D * rsD), fma(B, BC, D));
       const F J1 = theta * rsD;
       ph[p].add(X * J1);
       // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
@@ -260,6 +269,7 @@ struct Walk {
       const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
       sp[p].add(br * (rsD * rsD));
       rx[p] = rx1;
+      if (CQ) q[p] = q1;
       rq[p] = rq1;
     }
     ux = x1; uy = y1; ry = ry1;
@@ -652,11 +662,19 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   return true;
 }
 
-// The plain pass keeps 16 warps per SM (at most 128 registers a thread); the
-// level pass holds three walks per radius and runs 8 warps per SM with up to
-// 255 registers, which measured faster than spilling at 16.
+// Resident CTAs per SM the register budget is sized for (65536 registers a
+// SM): the level pass (three walks per radius) and 8 radii per lane run 8
+// warps per SM with up to 255 registers; 4 radii in CTAs of 4 warps run 12
+// warps with up to 168; the other shapes 16 warps with up to 128.  Measured
+// on the paper workload: 4 radii x 4 warps x 3 CTAs 664 ms, 8 radii x 8 warps
+// x 1 CTA 659 ms, 4 radii x 8 warps x 2 CTAs 682 ms (spilling).
+constexpr int min_ctas(int P, int warps, int mode) {
+  return (mode == kModeLevels || P >= 8) ? 256 / (warps * 32)
+                                         : (P == 4 && warps == 4) ? 3 : 512 / (warps * 32);
+}
+
 template <class A, int P, int WARPS, int MODE>
-__global__ void __launch_bounds__(WARPS * 32, (MODE == kModeLevels ? 256 : 512) / (WARPS * 32)) wilson_kernel(const KParams k) {
+__global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_kernel(const KParams k) {
   constexpr int K = MODE == kModeLevels ? kLevelComps : kComps;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
@@ -702,8 +720,9 @@ __global__ void __launch_bounds__(WARPS * 32, (MODE == kModeLevels ? 256 : 512) 
     const ProfileDev prof = k.profs[tile.profile];
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
-    else
-      ok = run_item<A, P, Walk<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+    else   // the level pass holds three walks per radius: no register to spare for Q
+      ok = run_item<A, P, Walk<A, P, MODE != kModeLevels>, MODE>(k, pp, acc, c, tile, prof, active,
+                                                                  &abort_flag, lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -793,7 +812,8 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   p.mode = mode;
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
-  p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : 8);
+  const int def_warps = (mode == kModeSums && p.P == 4) ? 4 : 8;   // (4, 4): 3 CTAs per SM
+  p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
   p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
   p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
   p.n_tiles = n_tiles;
@@ -860,11 +880,15 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
   }
   switch (prec) {
     case WLN_PREC_FP32_COMP:
+      WLN_CASE(F32Comp, 4, 4)
       WLN_CASE(F32Comp, 4, 8)
+      WLN_CASE(F32Comp, 8, 8)
       WLN_CASE(F32Comp, 2, 8)
       break;
     case WLN_PREC_FP32_NAIVE:
+      WLN_CASE(F32Naive, 4, 4)
       WLN_CASE(F32Naive, 4, 8)
+      WLN_CASE(F32Naive, 8, 8)
       WLN_CASE(F32Naive, 2, 8)
       break;
     case WLN_PREC_FP64:
