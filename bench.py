@@ -530,6 +530,19 @@ def run_batched(args, wl: I.Workload):
                         "kernel_ms": ms, "note": "whole graph pass timed (Wilson > 99%)"}
     line["gpu_launches"] = int(ctx.launch_count - n0)
     line["clocks"] = clk.summary()
+    # end to end through the public API: build the batch from the host grids
+    # (work list upload), one graph pass, results read back to the host
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        b2 = wln.Batch(ctx, ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+        b2.run(graph=True)
+        S2, st2, g2 = b2.results()
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        b2.free()
+    line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
+                   "h2d_bytes_per_step": int(sum(a.nbytes for a in wl.rho + wl.T)),
+                   "d2h_bytes_per_step": int(S2.nbytes + st2.nbytes + g2.nbytes)}
     line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
     line["autotune_candidates"] = tuned.get("candidates")
     line["finite_gamma"] = bool(np.isfinite(g).all())
@@ -766,7 +779,7 @@ def run_serve(args):
             times = list(np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(reqs))))
             label = f"{scale} x capacity = {rate:.3f} req/s"
         sv = wln.Server(ctx, ens, cfg["n_groups"], prec=args.prec, arena_bytes=16 << 30,
-                        tile_groups_per_step=64)
+                        tile_groups_per_step=128)
         t0 = time.perf_counter()
         pending = list(range(len(reqs)))
         ids, done_at = {}, {}
@@ -806,7 +819,7 @@ def run_serve(args):
                         "loop-point evals/s", len(reqs), 0, None, "f32",
                         {"workload": f"serving: {cfg['n_loops']} loops x {cfg['ppl']} ppl, G={cfg['n_groups']}, "
                                      f"first {len(reqs)} requests of the seed-7 Poisson stream",
-                         "arena": "16 GiB", "tile_groups_per_step": 64})
+                         "arena": "16 GiB", "tile_groups_per_step": 128})
     line["serve"] = runs
     line["capacity_req_per_s"] = capacity
     ens.free(); ctx.close()
