@@ -280,11 +280,10 @@ def reference_arm(args, wl: I.Workload):
     threads = oracle.max_threads()
     q = 1 if len(wl.profiles) > 1 else 0
     prof, rho, T = wl.profiles[q], wl.rho[q][::16], wl.T[q][::16]
-    lpg = wl.n_loops // wl.n_groups
-    y = oracle.gen_loops(wl.seed, lpg, wl.ppl)
+    y = oracle.gen_loops(wl.seed, wl.n_loops, wl.ppl, threads=threads)
 
     def step():
-        oracle.group_sums(y, prof, rho, T, 1, threads=threads)
+        oracle.group_sums(y, prof, rho, T, wl.n_groups, threads=threads)
 
     for _ in range(args.warmup):
         step()
@@ -292,10 +291,10 @@ def reference_arm(args, wl: I.Workload):
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / args.steps
-    lp = lpg * len(rho) * len(T)
+    lp = wl.n_loops * len(rho) * len(T)
     v = lp / dt
-    sample = (f"per step: F={prof.F}, {len(rho)} rho x {len(T)} T (every 16th), {lpg} loops "
-              f"(one group) x {wl.ppl} ppl")
+    sample = (f"per step: F={prof.F}, {len(rho)} rho x {len(T)} T (every 16th), all {wl.n_loops} "
+              f"loops ({wl.n_groups} groups) x {wl.ppl} ppl")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "loop-point evals/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
