@@ -821,11 +821,17 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   if (ctx->tune_chain && !fixed) {
     p.chain = ctx->tune_chain;
   } else {
-    // Enough items to keep every SM busy with a small tail, few partials.
+    // Enough items to keep every SM busy with a small tail, few partials;
+    // then short enough chains that the one every CTA is sweeping stays in L2
+    // (all CTAs work on the same chain at a time): measured on the paper
+    // workload, 42 MB chains read the ensemble 2.9x from DRAM, 10 MB chains
+    // 1.2x, in the same time.
     const int64_t target = static_cast<int64_t>(ctx->num_sms) * 32;
+    const int64_t block_bytes = static_cast<int64_t>(e.ppl) * 16 * kLanes / 2;
     int chain = e.n_blocks;
     while (chain > 1 && static_cast<int64_t>((e.n_blocks + chain - 1) / chain) * p.n_tile_groups < target)
       chain = (chain + 1) / 2;
+    while (chain > 1 && chain * block_bytes > (int64_t(16) << 20)) chain = (chain + 1) / 2;
     p.chain = chain;
   }
   p.n_chains = (e.n_blocks + p.chain - 1) / p.chain;
