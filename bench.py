@@ -207,7 +207,7 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
     lpg = wl.n_loops // wl.n_groups
     outs = {"S": S}
     off = 0
-    d2h = S.nbytes if where == "host" else 0
+    d2h = S.nbytes if where != "device" else 0
     h2d = sum(r.nbytes + t.nbytes for r, t in zip(wl.rho, wl.T))
     for q, (r, t) in enumerate(zip(wl.rho, wl.T)):
         n = len(r) * len(t)
@@ -216,14 +216,14 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
         js = ctx.jackknife(Sq, wl.n_groups, lpg, 0, jk_var=False, cov=False, where=where)
         outs[f"ferm{q}"] = jf
         outs[f"scal{q}"] = js
-        if where == "host":
+        if where != "device":
             d2h += sum(v.nbytes for v in jf.values() if v is not None)
             d2h += sum(v.nbytes for v in js.values() if v is not None)
             h2d += Sq.nbytes * 2
         off += n
     gg, ms, full = _action(ctx, wl, S, lpg, where=where)
     outs["gamma"] = (gg, ms)
-    if where == "host":
+    if where != "device":
         d2h += gg.nbytes + ms.nbytes
         if full is not None:
             d2h += full["density"].nbytes + full["integrand"].nbytes
@@ -240,8 +240,9 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     threads = oracle.max_threads()
     q = 1 if len(wl.profiles) > 1 else 0
     prof = wl.profiles[q]
-    rho = wl.rho[q][::4]
-    T = wl.T[q][::4]
+    stride = 1 if wl.n_points <= 1024 else 4        # small configurations run in full
+    rho = wl.rho[q][::stride]
+    T = wl.T[q][::stride]
     lpg = wl.n_loops // wl.n_groups
     # calibrate on one group at every sampled point (enough (point, group) pairs for all threads)
     y = oracle.gen_loops(wl.seed, lpg, wl.ppl).astype(np.float32).astype(np.float64)
@@ -254,6 +255,12 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     ref = oracle.group_sums(y, prof, rho, T, n_groups, threads=threads)
     dt = time.perf_counter() - t0
     lp = n_groups * lpg * len(rho) * len(T)
+    # one thread, one group, at most 32 of the sampled points
+    y1 = y[:lpg]
+    r1, t1 = rho[:8], T[:4]
+    t0 = time.perf_counter()
+    oracle.group_sums(y1, prof, r1, t1, 1, threads=1)
+    single = lpg * len(r1) * len(t1) / (time.perf_counter() - t0)
     # GPU result on the same sample (same loops: the first n_groups groups of the ensemble)
     err = {}
     ens = gpu_ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
@@ -266,8 +273,10 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
                      "ferm_max_rel_to_max(1,|<W>-1|)": float(rel.max())}
     ens.free()
     return {"value": lp / dt, "unit": "loop-point evals/s", "cores": threads, "kind": "oracle",
-            "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every 4th), "
+            "sample": f"F={prof.F} lam={prof.lam}, {len(rho)} rho x {len(T)} T (every {stride}), "
                       f"{n_groups * lpg} loops ({n_groups} groups) x {wl.ppl} ppl; {dt:.1f} s",
+            "single_thread": {"value": single, "unit": "loop-point evals/s",
+                              "sample": f"{lpg} loops x {len(r1) * len(t1)} points, 1 thread"},
             "gpu_error_vs_oracle_on_sample": err}
 
 
@@ -473,6 +482,12 @@ def main():
         ens.free()
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl, ctx)
+    # the paper's own GPU figure, quoted with its hardware (context only: another
+    # machine, another workload, so vs_baseline stays null)
+    line["paper_context"] = {
+        "gpu_rate_loop_point_evals_per_s": 5000 / 0.001315, "hardware": "NVIDIA Tesla C1060",
+        "precision": "fp32", "workload": "5000 loops, one (rho_cm, T) point; ppl not stated",
+        "speedup_vs_serial_cpu": 4.7553 / 0.001315}
     ctx.close()
     print(json.dumps(line))
     if ws > 1:

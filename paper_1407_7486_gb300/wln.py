@@ -249,9 +249,16 @@ class Context:
         return int(load().wln_launch_count(self.handle))
 
     def _empty(self, shape, dtype, where: str):
+        """Output buffer: "host" (numpy), "pinned" (numpy over page-locked
+        host memory, the fast path for device-to-host copies) or "device"
+        (a torch tensor on this context's GPU)."""
         import torch
         if where == "host":
             return np.empty(shape, dtype)
+        if where == "pinned":
+            tdt = {np.float64: torch.float64, np.float32: torch.float32,
+                   np.uint32: torch.int32}[dtype]
+            return torch.empty(shape, dtype=tdt, pin_memory=True).numpy().view(dtype)
         tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint32: torch.int32}[dtype]
         return torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
 
