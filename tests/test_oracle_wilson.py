@@ -203,3 +203,36 @@ def test_repeated_point_still_accumulates_spin():
     r2 = (0.4 + math.sqrt(T) * base[0, 2]) ** 2 + (math.sqrt(T) * base[1, 2]) ** 2
     eB = 2 * calF * lam**2 / (lam**2 + r2) ** 2
     assert sp9 == pytest.approx(sp8 * 8 / 9 + eB * T / 9, rel=1e-12)
+
+
+def test_phase_abs_sum_of_segment_magnitudes():
+    # phase_abs is the sum over segments of |segment phase| (it sizes the
+    # rounding bars of the float path)
+    rng = np.random.default_rng(17)
+    F = 2 * math.pi * 3.0                      # calF = 3
+    # thin tube: each segment's phase is calF times the angle it subtends at the axis
+    prof = Profile(PROFILE_FLUX_TUBE, F=F, lam=1e-9)
+    for _ in range(5):
+        y = oracle.gen_loops(int(rng.integers(1 << 30)), 1, 64)[0]
+        rho, T = 0.3, 0.5
+        r = np.stack([rho + math.sqrt(T) * y[0], math.sqrt(T) * y[1]])
+        if np.min(np.hypot(r[0], r[1])) < 1e-3:
+            continue
+        ang = np.arctan2(r[1], r[0])
+        d = np.diff(np.append(ang, ang[0]))
+        d = (d + math.pi) % (2 * math.pi) - math.pi
+        want = 3.0 * np.abs(d).sum()
+        assert oracle.phase_abs(y[None], prof, rho, T)[0] == pytest.approx(want, rel=1e-7)
+    # |phase| <= phase_abs, equal for a convex polygon around the axis, and
+    # linear in the flux
+    prof = Profile(PROFILE_FLUX_TUBE, F=F, lam=0.7)
+    k = np.arange(12)
+    poly = np.stack([0.8 * np.cos(2 * np.pi * k / 12), 0.5 * np.sin(2 * np.pi * k / 12)])[None]
+    ph, _ = oracle.phase_spin(poly, prof, 0.0, 1.0)
+    assert oracle.phase_abs(poly, prof, 0.0, 1.0)[0] == pytest.approx(abs(ph[0]), rel=1e-13)
+    y = oracle.gen_loops(5, 40, 128)
+    ph, _ = oracle.phase_spin(y, prof, 0.4, 2.0)
+    pa = oracle.phase_abs(y, prof, 0.4, 2.0)
+    assert np.all(pa >= np.abs(ph) * (1 - 1e-13)) and np.any(pa > 1.5 * np.abs(ph))
+    pa2 = oracle.phase_abs(y, Profile(PROFILE_FLUX_TUBE, F=2 * F, lam=0.7), 0.4, 2.0)
+    np.testing.assert_allclose(pa2, 2 * pa, rtol=1e-13)
