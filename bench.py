@@ -280,6 +280,31 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
             "gpu_error_vs_oracle_on_sample": err}
 
 
+def sampled_oracle_error(y32, profiles, rhos, Ts, S, n_groups: int, n_samples: int = 16,
+                         seed: int = 3):
+    """Error of group sums S (points ordered profile, T, rho) against the FP64
+    oracle on seeded (profile, point, group) samples, the oracle working on
+    the same float loops y32 [n_loops][2][ppl]: max |d<W_scal>| and max
+    |d<W_ferm>| / max(1, |<W_ferm> - 1|) over the samples."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    lpg = y32.shape[0] // n_groups
+    offs = np.cumsum([0] + [len(r) * len(t) for r, t in zip(rhos, Ts)])
+    e_s = e_f = 0.0
+    for _ in range(n_samples):
+        q = int(rng.integers(len(profiles)))
+        n = len(rhos[q]) * len(Ts[q])
+        p, g = int(rng.integers(n)), int(rng.integers(n_groups))
+        r, t = rhos[q][p % len(rhos[q])], Ts[q][p // len(rhos[q])]
+        yg = y32[g * lpg:(g + 1) * lpg].astype(np.float64)
+        ref = oracle.group_sums(yg, profiles[q], [r], [t], 1)[0, 0]
+        got = S[offs[q] + p, g]
+        e_s = max(e_s, abs(got[0] - ref[0]) / lpg)
+        e_f = max(e_f, abs(got[1] - ref[1]) / max(abs(ref[1]), lpg))
+    return {"samples": n_samples, "scal_max_abs": float(e_s),
+            "ferm_max_rel_to_max(1,|<W>-1|)": float(e_f)}
+
+
 def reference_arm(args, wl: I.Workload):
     """The oracle as it stands on the host cores, each step a bounded sample."""
     ws, rank, _ = _dist()
@@ -557,6 +582,9 @@ def run_batched(args, wl: I.Workload):
     line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
                    "h2d_bytes_per_step": int(sum(a.nbytes for a in wl.rho + wl.T)),
                    "d2h_bytes_per_step": int(S2.nbytes + st2.nbytes + g2.nbytes)}
+    y32, _ = ctx.loops_copy(ens)
+    line["gpu_error_vs_oracle_sampled"] = sampled_oracle_error(
+        y32, wl.profiles, wl.rho, wl.T, S2, wl.n_groups)
     line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
     line["autotune_candidates"] = tuned.get("candidates")
     line["finite_gamma"] = bool(np.isfinite(g).all())
@@ -836,6 +864,22 @@ def run_serve(args):
                          "arena": "16 GiB", "tile_groups_per_step": 128})
     line["serve"] = runs
     line["capacity_req_per_s"] = capacity
+    # one request through the server, its results against the FP64 oracle
+    sv = wln.Server(ctx, ens, cfg["n_groups"], prec=args.prec, arena_bytes=16 << 30,
+                    tile_groups_per_step=128)
+    r0 = reqs[0]
+    rid = sv.submit(r0.profile, r0.rho, r0.T)
+    for _ in range(100000):
+        sv.step()
+        state, res = sv.poll(rid)
+        if state == sv.DONE:
+            break
+    y32, _ = ctx.loops_copy(ens)
+    line["gpu_error_vs_oracle_sampled"] = dict(
+        sampled_oracle_error(y32, [r0.profile], [r0.rho], [r0.T], res[0], cfg["n_groups"]),
+        request=0)
+    sv.release(rid)
+    sv.free()
     ens.free(); ctx.close()
     print(json.dumps(line))
 
