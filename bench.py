@@ -84,6 +84,8 @@ def _action(ctx, wl: I.Workload, S, lpg: int, where: str = "device"):
         quad = [wln.Quad(*wl.meta["quad"]) for _ in wl.profiles]
         r = ctx.effective_action_full(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, quad=quad,
                                       spinor=True, where=where)
+        r["scalar"] = ctx.effective_action_full(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg,
+                                                quad=quad, spinor=False, where=where)
         return r["gamma_groups"], r["gamma"], r
     gg, ms = ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True,
                                   where=where)
@@ -223,10 +225,12 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
         off += n
     gg, ms, full = _action(ctx, wl, S, lpg, where=where)
     outs["gamma"] = (gg, ms)
+    outs["full"] = full
     if where != "device":
         d2h += gg.nbytes + ms.nbytes
-        if full is not None:
+        if full is not None:       # spinor: gamma_groups and gamma counted above
             d2h += full["density"].nbytes + full["integrand"].nbytes
+            d2h += sum(v.nbytes for v in full["scalar"].values())
         h2d += S.nbytes
     ens.free()
     return outs, h2d, d2h
@@ -484,9 +488,19 @@ def main():
         # the step's physics: spinor effective action per flux tube, mean +- group
         # SEM, against the LCF approximation on the same quadrature
         g = outs["gamma"][1]
-        line["effective_action"] = [
-            {"F": p.F, "lam": p.lam, "gamma": float(g[q, 0]), "sem": float(g[q, 1]),
-             "lcf": float(g[q, 2])} for q, p in enumerate(wl.profiles)]
+        gs = outs["full"]["scalar"]["gamma"]
+        line["effective_action"] = {
+            "note": "lambda = 1 tubes, where the derivative expansion (LCF) is not expected "
+                    "to hold; the e^-T/T^3 factor magnifies the statistical error of <W> at "
+                    "small T (why the paper splits off the small-T part); for F = 50 the "
+                    "spinor's cosh(eB T) outgrows e^-T at large T and the group spread swamps "
+                    "the mean (the paper's fermion problem), while the scalar W = cos(phase) "
+                    "stays bounded",
+            "tubes": [{"F": p.F, "lam": p.lam,
+                       "spinor": {"gamma": float(g[q, 0]), "sem": float(g[q, 1]),
+                                  "lcf": float(g[q, 2])},
+                       "scalar": {"gamma": float(gs[q, 0]), "sem": float(gs[q, 1]),
+                                  "lcf": float(gs[q, 2])}} for q, p in enumerate(wl.profiles)]}
     # FP64 GPU path on one profile and a sparse subset of points (it is ~10^2 slower)
     if args.prec == "fp32":
         q = 1 if len(wl.profiles) > 1 else 0

@@ -135,3 +135,27 @@ def test_full_action_rejects_grids_off_their_kind(ctx):
     with pytest.raises(wln.WlnError):     # linear radii declared as mapped
         ctx.effective_action_full([prof], [rho], [T], S, 4, 4,
                                   quad=[wln.Quad(M, ost.GRID_LOG, 1.0, 0.0)], where="host")
+
+
+@pytest.mark.parametrize("spinor", [True, False])
+def test_wide_tube_agrees_with_lcf_within_statistics(ctx, spinor):
+    # Sec. "Verification and Validation", Fig. vsrhocm: for a tube much wider
+    # than the Compton wavelength (lambda = 10, calF = 10) the worldline action
+    # density agrees with the LCF approximation within the statistics.  Mapped
+    # grids as in Sec. "Computing an Effective Action", small-T part below a = 1.
+    prof = I.Profile(0, F=2 * math.pi * 10.0, lam=10.0)
+    n_loops, G = 10240, 32
+    ens = ctx.gen_loops(1, n_loops, 2048)
+    rho, T = wln.mapped_grid(48, 10.0, 0.0), wln.mapped_grid(64, 2.0, 1.0)
+    S = ctx.wilson_avg(ens, [prof], [rho], [T], G, prec="fp32")
+    r = ctx.effective_action_full([prof], [rho], [T], S, G, n_loops // G,
+                                  quad=[wln.Quad(M, M, 10.0, 2.0, True)], spinor=spinor,
+                                  where="host")
+    D = r["density"]
+    z = (D[:, 0] - D[:, 2]) / D[:, 1]
+    assert np.all(np.isfinite(z)) and np.all(np.abs(z) < 4.0), np.abs(z).max()
+    g = r["gamma"][0]
+    assert abs(g[0] - g[2]) < 4.0 * g[1]
+    # the LCF sign is the physical one: spinor action density negative, scalar positive
+    assert (D[0, 2] < 0) == spinor
+    ens.free()
