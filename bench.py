@@ -791,7 +791,7 @@ def run_correlation(args, wl: I.Workload):
                          "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": None,
-                        "kernel": "wilson_kernel<F32Comp,4,8,loops>", "kernel_ms": kern_ms,
+                        "kernel": "wilson_kernel<F32Comp,4,4,loops>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}

@@ -812,7 +812,7 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   p.mode = mode;
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
-  const int def_warps = (mode == kModeSums && p.P == 4) ? 4 : 8;   // (4, 4): 3 CTAs per SM
+  const int def_warps = (mode != kModeLevels && p.P == 4) ? 4 : 8;   // (4, 4): 3 CTAs per SM
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
   p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
   p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
@@ -878,8 +878,8 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
   }
   if (plan.mode == kModeLoops) {
     switch (prec) {
-      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, kModeLoops) break;
-      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, kModeLoops) break;
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 4, kModeLoops) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 4, kModeLoops) break;
       case WLN_PREC_FP64: WLN_CASE_L(F64, 2, 4, kModeLoops) break;
     }
     return cudaErrorInvalidConfiguration;
