@@ -43,9 +43,9 @@ FP32_LANES_PER_SM = 128
 # sums; 17 for the arctangent (range fold 2, quotient 1, square 1, polynomial
 # 8, octant unfolding 4, plus t*s 1); 11 per segment shared by the lane's
 # P = 4 radii (11/4); and two Kahan folds of 4 operations every 8 segments (1).
-# The level pass keeps theta = atan2(C sqrt(D), D + B (B + C)): 19 per radius.
+# The level pass holds P = 3 radii per lane: the shared part is 11/3.
 N_ALG_FP32 = 18 + 17 + 11 / 4 + 1
-N_ALG_FP32_LEVELS = 19 + 17 + 11 / 4 + 1
+N_ALG_FP32_LEVELS = 18 + 17 + 11 / 3 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 
 
@@ -674,7 +674,7 @@ def run_levels(args, wl: I.Workload):
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
                         "traffic": _ncu_traffic(f"wilson_levels_{args.workload}"),
-                        "kernel": "wilson_kernel<F32Comp,4,8,levels>", "kernel_ms": kern_ms,
+                        "kernel": "wilson_kernel<F32Comp,3,4,levels>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": N_ALG_FP32_LEVELS,
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "

@@ -667,7 +667,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 // warps per SM with up to 255 registers; 4 radii in CTAs of 4 warps run 12
 // warps with up to 168; the other shapes 16 warps with up to 128.  Measured
 // on the paper workload: 4 radii x 4 warps x 3 CTAs 664 ms, 8 radii x 8 warps
-// x 1 CTA 659 ms, 4 radii x 8 warps x 2 CTAs 682 ms (spilling).
+// x 1 CTA 659 ms, 4 radii x 8 warps x 2 CTAs 682 ms (spilling); the level
+// pass 3 radii x 4 warps x 2 CTAs 757 ms, 4 x 8 x 1 774 ms.
 constexpr int min_ctas(int P, int warps, int mode) {
   return (mode == kModeLevels || P >= 8) ? 256 / (warps * 32)
                                          : (P == 4 && warps == 4) ? 3 : 512 / (warps * 32);
@@ -720,9 +721,9 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
     const ProfileDev prof = k.profs[tile.profile];
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
-    else   // the level pass holds three walks per radius: no register to spare for Q
-      ok = run_item<A, P, Walk<A, P, MODE != kModeLevels>, MODE>(k, pp, acc, c, tile, prof, active,
-                                                                  &abort_flag, lane);
+    else   // three walks per radius: Q fits in registers for up to 3 radii per lane
+      ok = run_item<A, P, Walk<A, P, MODE != kModeLevels || P <= 3>, MODE>(k, pp, acc, c, tile, prof,
+                                                                            active, &abort_flag, lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -799,7 +800,7 @@ size_t smem_bytes(const WilsonPlan& p, int ppl) {
 // walks per radius (4 radii per lane, FP64 1) and ignore the tuning of the
 // plain pass.
 int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode) {
-  if (mode == kModeLevels) return prec == WLN_PREC_FP64 ? 1 : 4;
+  if (mode == kModeLevels) return prec == WLN_PREC_FP64 ? 1 : 3;
   if (mode == kModeLoops) return prec == WLN_PREC_FP64 ? 2 : 4;
   if (prec == WLN_PREC_FP64) return 2;
   return ctx->tune_P ? ctx->tune_P : 4;
@@ -812,7 +813,8 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   p.mode = mode;
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
-  const int def_warps = (mode != kModeLevels && p.P == 4) ? 4 : 8;   // (4, 4): 3 CTAs per SM
+  // (4, 4): 3 CTAs per SM; levels (3, 4): 2 CTAs per SM
+  const int def_warps = (mode == kModeLevels || p.P == 4) ? 4 : 8;
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
   p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
   p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
@@ -870,8 +872,8 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
 #define WLN_CASE(A, P_, W_) WLN_CASE_L(A, P_, W_, kModeSums)
   if (plan.mode == kModeLevels) {
     switch (prec) {
-      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 8, kModeLevels) break;
-      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 8, kModeLevels) break;
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 3, 4, kModeLevels) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 3, 4, kModeLevels) break;
       case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, kModeLevels) break;
     }
     return cudaErrorInvalidConfiguration;
