@@ -55,3 +55,24 @@ def test_mapped_grid_helper_matches_oracle_nodes():
                                    ost.mapped_nodes(n, scale, start), rtol=1e-15, atol=0)
     with pytest.raises(wln.WlnError):
         wln.mapped_grid(4, -1.0, 0.0)
+
+
+def _build_c_example(tmp_path):
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    lib = build.build()
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    exe = str(tmp_path / "c_api_example")
+    subprocess.check_call([gcc, "-O2", "-I", os.path.join(root, "include"),
+                           os.path.join(here, "c_api_example.c"), "-L", os.path.dirname(lib),
+                           "-lwln", f"-Wl,-rpath,{os.path.dirname(lib)}", "-o", exe])
+    return exe
+
+
+def test_c_example_compiles_and_links_against_the_library(tmp_path):
+    # the header is plain C and every symbol the example uses resolves in libwln.so
+    assert os.path.exists(_build_c_example(tmp_path))
