@@ -52,6 +52,8 @@ N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 def _workload(name: str) -> I.Workload:
     if name == "paper_mapped":
         return _paper_mapped()
+    if name == "sweep":
+        return I.sweep(4096)
     return {"paper": I.paper, "small": I.small, "paper_slice": I.paper_slice,
             "batched": I.batched}[name]()
 
@@ -351,7 +353,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wln", choices=["wln", "reference"])
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "small", "paper_slice", "batched", "paper_mapped"])
+                    choices=["paper", "small", "paper_slice", "batched", "paper_mapped", "sweep"])
     ap.add_argument("--serve", action="store_true",
                     help="replay the seed-7 Poisson request stream against the serving ensemble")
     ap.add_argument("--requests", type=int, default=24)
@@ -376,6 +378,8 @@ def main():
         return run_serve(args)
     if args.workload == "batched":
         return run_batched(args, wl)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.levels:
         return run_levels(args, wl)
     if args.correlation:
@@ -805,6 +809,73 @@ def run_correlation(args, wl: I.Workload):
         "median_abs_loops": float(np.nanmedian(np.abs(rh[0][others]))),
         "median_abs_groups": float(np.nanmedian(np.abs(rh[1][others]))),
         "median_abs_shuffled_groups": float(np.nanmedian(np.abs(rh[2][others])))}
+    ctx.close()
+    print(json.dumps(line))
+
+
+def run_sweep(args):
+    """Precision and discretisation sweep: 8192 loops at ppl = 256 .. 16384,
+    flux tubes F in {1, 100} x lambda in {0.1, 1} on a 16 x 16 grid and
+    constant fields B in {0.1, 1, 5} at rho = 0.  For every ppl and every
+    precision (FP64, FP32 compensated, FP32 naive) the Wilson pass over all
+    profiles is timed, and its group sums are compared with the FP64 oracle on
+    two groups at a 2 x 2 sub-grid of every profile."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    import oracle
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    rows = []
+    n0 = ctx.launch_count
+    with ClockSampler(0) as clk, torch.cuda.stream(stream):
+        for ppl in (256, 1024, 4096, 16384):
+            wl = I.sweep(ppl)
+            lpg = wl.n_loops // wl.n_groups
+            ens = ctx.gen_loops(wl.seed, wl.n_loops, ppl)
+            y32, _ = ctx.loops_copy(ens)
+            ysub = y32[:2 * lpg].astype(np.float64)
+            subs = []
+            for prof, rho, T in zip(wl.profiles, wl.rho, wl.T):
+                r_s = rho[[0, len(rho) // 2]] if len(rho) > 1 else rho
+                t_s = T[[2, len(T) - 3]]
+                subs.append((prof, r_s, t_s, oracle.group_sums(ysub, prof, r_s, t_s, 2)))
+            for prec in ("fp64", "fp32", "fp32_naive"):
+                reps = 1 if prec == "fp64" else 3
+                ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec)
+                b.record(stream)
+                stream.synchronize()
+                ms = a.elapsed_time(b) / reps
+                e_s = e_f = 0.0
+                for prof, r_s, t_s, ref in subs:
+                    S = ctx.wilson_avg(ens, [prof], [r_s], [t_s], wl.n_groups, prec=prec,
+                                       where="host")[:, :2]
+                    with np.errstate(invalid="ignore", over="ignore"):
+                        fin = np.isfinite(ref[:, :, 1]) & np.isfinite(S[:, :, 1])
+                        e_s = max(e_s, float(np.abs(S[:, :, 0] - ref[:, :, 0]).max() / lpg))
+                        rel = np.abs(S[:, :, 1] - ref[:, :, 1]) / np.maximum(np.abs(ref[:, :, 1]), lpg)
+                        e_f = max(e_f, float(np.where(fin, rel, 0.0).max()))
+                rows.append({"ppl": ppl, "prec": prec, "ms": ms,
+                             "loop_point_evals_per_s": wl.loop_points / (ms / 1e3),
+                             "scal_max_abs_err": e_s, "ferm_max_rel_err": e_f})
+            ens.free()
+    launches = ctx.launch_count - n0
+    main = next(r for r in rows if r["ppl"] == 4096 and r["prec"] == "fp32")
+    line = _common_line("loop-point evals/s (precision sweep; value: FP32 compensated at ppl 4096)",
+                        main["loop_point_evals_per_s"], "loop-point evals/s", 1, 1, main["ms"],
+                        "f32", {"workload": "sweep: 8192 loops, ppl 256..16384, 4 flux tubes "
+                                            "(F in {1, 100} x lambda in {0.1, 1}, 16 T x 16 rho) "
+                                            "+ 3 constant fields at rho = 0 (16 T), G = 32",
+                                "errors": "against the FP64 oracle on 2 groups x 2 x 2 points "
+                                          "of every profile; spinor relative to max(1, |<W>-1|)"})
+    line["sweep"] = rows
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clk.summary()
     ctx.close()
     print(json.dumps(line))
 
