@@ -352,8 +352,9 @@ __device__ __forceinline__ double cosh_m1_f64(double x) {
 //  FP32 compensated: phase and spin arrive as compensated sums times a
 //   double scale, formed as double-float; the fractional turn is exact to
 //   float rounding, so sin/cos are taken on |frac| <= 1/2 with sinpi/cospi.
-//   cosh(spin) - 1 uses expm1f plus the first-order term of the low part;
-//   spins above 80 (cosh beyond float range) go through double.
+//   cosh(spin) - 1 uses expm1f of |spin| (cosh is even) plus the
+//   first-order term of the low part; spins above 80 (cosh beyond float
+//   range) go through double.
 //  FP32 naive: plain float phase in radians, cosf and coshf.
 template <class A>
 __device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp_s, double sp_c,
@@ -376,7 +377,13 @@ __device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp
     const float scal_m1 = -2.0f * h * h;
     float sn, cs;
     sincospif(2.0f * fr, &sn, &cs);
-    const F2 sv = scaled(static_cast<float>(sp_s), static_cast<float>(sp_c), st);
+    F2 sv = scaled(static_cast<float>(sp_s), static_cast<float>(sp_c), st);
+    // cosh is even: evaluate at |spin| (a negative flux or field gives a
+    // negative spin, and expm1 of a large negative argument reaches -1)
+    if (sv.hi < 0.0f) {
+      sv.hi = -sv.hi;
+      sv.lo = -sv.lo;
+    }
     double ferm_m1;
     if (sv.hi < 80.0f) {
       const float em1 = expm1f(sv.hi);

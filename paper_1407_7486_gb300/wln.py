@@ -163,7 +163,8 @@ def _profiles(profiles: Sequence[Profile]):
 
 
 def _csr(grids: Sequence[Sequence[float]]):
-    flat = np.ascontiguousarray(np.concatenate([np.asarray(g, np.float64) for g in grids]))
+    parts = [np.asarray(g, np.float64).reshape(-1) for g in grids]
+    flat = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros(0))
     off = np.zeros(len(grids) + 1, np.int32)
     off[1:] = np.cumsum([len(g) for g in grids])
     return flat, off
