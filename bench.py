@@ -77,7 +77,7 @@ def _paper_mapped() -> I.Workload:
     return wl
 
 
-def _action(ctx, wl: I.Workload, S, lpg: int, where: str = "device"):
+def _action(ctx, wl: I.Workload, S, lpg: int, where: str = "device", out=None):
     """The effective action of the step: the paper's full form (small-T part,
     mapped grids, LCF comparison) when the workload carries its quadrature,
     else Simpson on the linear/geometric grids."""
@@ -90,7 +90,7 @@ def _action(ctx, wl: I.Workload, S, lpg: int, where: str = "device"):
                                                 quad=quad, spinor=False, where=where)
         return r["gamma_groups"], r["gamma"], r
     gg, ms = ctx.effective_action(wl.profiles, wl.rho, wl.T, S, wl.n_groups, lpg, spinor=True,
-                                  where=where)
+                                  where=where, out=out)
     return gg, ms, None
 
 
@@ -203,11 +203,32 @@ def _max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def host_buffers(wl: I.Workload, pinned: bool = True):
+    """Page-locked host buffers for every output of a step, allocated once by
+    the caller and reused (the fast path for device-to-host copies)."""
+    import torch
+
+    def buf(*shape):
+        t = torch.empty(shape, dtype=torch.float64, pin_memory=pinned)
+        return t.numpy()
+
+    G = wl.n_groups
+    b = {"S": buf(wl.n_points, G, 5), "prof": []}
+    for r, t in zip(wl.rho, wl.T):
+        n = len(r) * len(t)
+        b["prof"].append({"ferm": {"mean": buf(n), "sem": buf(n), "jk_var": buf(n), "cov": buf(n, n)},
+                          "scal": {"mean": buf(n), "sem": buf(n)}})
+    b["gamma"] = (buf(len(wl.profiles), G), buf(len(wl.profiles), 2))
+    return b
+
+
 def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", cov: bool = True,
-             loop0: int = 0):
-    """One pass of the path; returns (outputs, h2d_bytes, d2h_bytes)."""
+             loop0: int = 0, bufs=None):
+    """One pass of the path; returns (outputs, h2d_bytes, d2h_bytes).  With
+    `bufs` (host_buffers) every output lands in those caller-owned buffers."""
     ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
-    S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec, where=where)
+    S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec, where=where,
+                       out=bufs["S"] if bufs else None)
     lpg = wl.n_loops // wl.n_groups
     outs = {"S": S}
     off = 0
@@ -216,8 +237,11 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
     for q, (r, t) in enumerate(zip(wl.rho, wl.T)):
         n = len(r) * len(t)
         Sq = S[off:off + n]
-        jf = ctx.jackknife(Sq, wl.n_groups, lpg, 1, jk_var=True, cov=cov, where=where)
-        js = ctx.jackknife(Sq, wl.n_groups, lpg, 0, jk_var=False, cov=False, where=where)
+        pb = bufs["prof"][q] if bufs else {}
+        jf = ctx.jackknife(Sq, wl.n_groups, lpg, 1, jk_var=True, cov=cov, where=where,
+                           out=pb.get("ferm"))
+        js = ctx.jackknife(Sq, wl.n_groups, lpg, 0, jk_var=False, cov=False, where=where,
+                           out=pb.get("scal"))
         outs[f"ferm{q}"] = jf
         outs[f"scal{q}"] = js
         if where != "device":
@@ -225,7 +249,7 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
             d2h += sum(v.nbytes for v in js.values() if v is not None)
             h2d += Sq.nbytes * 2
         off += n
-    gg, ms, full = _action(ctx, wl, S, lpg, where=where)
+    gg, ms, full = _action(ctx, wl, S, lpg, where=where, out=bufs["gamma"] if bufs else None)
     outs["gamma"] = (gg, ms)
     outs["full"] = full
     if where != "device":
@@ -439,7 +463,9 @@ def main():
     loop_points = wl.loop_points
     value = loop_points * ws / (ms / 1e3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: page-locked output
+    # buffers the caller allocates once (outside the timed region) and reuses
+    bufs = host_buffers(wl)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 2))
@@ -447,7 +473,7 @@ def main():
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
             outs, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True,
-                                      loop0=loop0)
+                                      loop0=loop0, bufs=bufs)
     stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _max_over_ranks(e2e_s, ws)

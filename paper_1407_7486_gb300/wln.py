@@ -405,12 +405,21 @@ class Context:
 
     # --------------------------------------------------------- statistics
     def jackknife(self, group_sums, n_groups: int, loops_per_group: int, comp: int,
-                  jk_var: bool = True, cov: bool = False, where: str = "device"):
+                  jk_var: bool = True, cov: bool = False, where: str = "device", out=None):
+        """Group mean, SEM, jackknife variance and covariance; `out` may hold
+        caller-owned buffers under the same keys (reused across calls)."""
         n_points = group_sums.shape[0]
-        mean = self._empty((n_points,), np.float64, where)
-        sem = self._empty((n_points,), np.float64, where)
-        jv = self._empty((n_points,), np.float64, where) if jk_var else None
-        cv = self._empty((n_points, n_points), np.float64, where) if cov else None
+        out = out or {}
+        mean = out.get("mean")
+        mean = self._empty((n_points,), np.float64, where) if mean is None else mean
+        sem = out.get("sem")
+        sem = self._empty((n_points,), np.float64, where) if sem is None else sem
+        jv = out.get("jk_var") if jk_var else None
+        if jk_var and jv is None:
+            jv = self._empty((n_points,), np.float64, where)
+        cv = out.get("cov") if cov else None
+        if cov and cv is None:
+            cv = self._empty((n_points, n_points), np.float64, where)
         self._check(load().wln_jackknife(self.handle, _ptr(group_sums), n_points, n_groups,
                                          loops_per_group, comp, _ptr(mean), _ptr(sem), _ptr(jv),
                                          _ptr(cv)))
@@ -426,11 +435,16 @@ class Context:
 
     def effective_action(self, profiles: Sequence[Profile], rho: Sequence, T: Sequence,
                          group_sums, n_groups: int, loops_per_group: int, spinor: bool = True,
-                         where: str = "device"):
+                         where: str = "device", out=None):
+        """(per-group action [n_profiles][G], (mean, SEM) [n_profiles][2]);
+        `out` may be a caller-owned pair of buffers."""
         rho_f, rho_off = _csr(rho)
         T_f, T_off = _csr(T)
-        gg = self._empty((len(profiles), n_groups), np.float64, where)
-        ms = self._empty((len(profiles), 2), np.float64, where)
+        if out is not None:
+            gg, ms = out
+        else:
+            gg = self._empty((len(profiles), n_groups), np.float64, where)
+            ms = self._empty((len(profiles), 2), np.float64, where)
         profs = _profiles(profiles)
         self._check(load().wln_effective_action(self.handle, profs, len(profiles), _ptr(rho_f),
                                                 _ptr(rho_off), _ptr(T_f), _ptr(T_off),
