@@ -370,3 +370,29 @@ def corrcoef_ref(X: np.ndarray, ref: int) -> np.ndarray:
     den = np.sqrt((d * d).sum(axis=1) * (d[ref] * d[ref]).sum())
     with np.errstate(invalid="ignore", divide="ignore"):
         return num / den
+
+
+def nested_level_sums(oracle_mod, y, profile, rho, T, n_groups, threads=0):
+    """Group sums [n_T * n_rho][G][6] of W - 1 (scalar, spinor) at three
+    nested discretisations of every loop: all N points, the even points
+    (N/2) and the points 0 mod 4 (N/4), each a closed polygon with proper time
+    T/N' per segment.  These are genuine levels of one loop, so the parabola
+    of EXTRAPOLATION applies to them (the paper's own combination of
+    interleaved sub-loops, level_sums, is not a discretisation hierarchy)."""
+    y = np.ascontiguousarray(y, np.float64)
+    subs = [y, np.ascontiguousarray(y[:, :, 0::2]), np.ascontiguousarray(y[:, :, 0::4])]
+    n = y.shape[0]
+    lpg = n // n_groups
+    out = np.zeros((len(T) * len(rho), n_groups, 6))
+    for b, t in enumerate(T):
+        for a, r in enumerate(rho):
+            cols = []
+            for sub in subs:
+                ph, sp = oracle_mod.phase_spin(sub, profile, r, t, threads)
+                h = np.sin(0.5 * ph)
+                scal = -2.0 * h * h
+                sh = np.sinh(0.5 * sp)
+                cols += [scal, np.cos(ph) * 2.0 * sh * sh + scal]
+            w = np.stack(cols, axis=-1)
+            out[b * len(rho) + a] = w.reshape(n_groups, lpg, 6).sum(axis=1)
+    return out

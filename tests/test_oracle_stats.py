@@ -357,3 +357,48 @@ def test_loop_values_sum_to_group_sums():
     W = oracle.loop_values(y, prof, rho, T)
     S = oracle.group_sums(y, prof, rho, T, 3)
     np.testing.assert_allclose(ost.group_sums_perm(W, 3), S[:, :, :2], rtol=1e-13, atol=1e-15)
+
+
+def _exact_const(b, N):
+    k = np.arange(1, N)
+    return float(np.prod((1.0 + (b / (N * np.tan(np.pi * k / N))) ** 2) ** -0.5))
+
+
+def test_nested_levels_are_the_exact_finite_N_averages_and_extrapolate():
+    import oracle
+    from paper_1407_7486_gb300.inputs import PROFILE_CONST_B
+    # constant field: every nested level is a genuine N'-point loop, so its
+    # average is the exact finite-N' product; the bias is ~ b^2 / (2 N') at
+    # O(b^2), so the parabola through N, N/2, N/4 recovers the continuum
+    # b / sinh b far better than the finest level
+    N, n_loops, G, b = 32, 25600, 32, 1.0
+    y = oracle.gen_loops(71, n_loops, N)
+    L = ost.nested_level_sums(oracle, y, Profile(PROFILE_CONST_B, B=b), [0.0], [1.0], G)
+    lpg = n_loops // G
+    for lv, n in enumerate((N, N // 2, N // 4)):
+        m, e = ost.mean_sem(L, lpg, 2 * lv)
+        assert abs(1.0 + m[0] - _exact_const(b, n)) < 5 * e[0], (n, m[0], e[0])
+    E = ost.extrapolate(L)
+    m_inf, e_inf = ost.mean_sem(E, lpg, 0)
+    m_N, _ = ost.mean_sem(L, lpg, 0)
+    cont = b / math.sinh(b) - 1.0
+    assert abs(m_inf[0] - cont) < 5 * e_inf[0]
+    assert abs(m_inf[0] - cont) < 0.2 * abs(m_N[0] - cont)
+    # the exact finite-N values themselves extrapolate to the continuum
+    ex = [_exact_const(b, n) for n in (N, N // 2, N // 4)]
+    assert abs(np.dot(ost.EXTRAPOLATION, ex) - (1.0 + cont)) < 0.02 * abs(ex[0] - (1.0 + cont))
+
+
+def test_paper_levels_are_not_a_discretisation_hierarchy():
+    # the printed combination e^{i(circ/2 + sq/4 + tri/4)} is a point-weighted
+    # mean of sub-loop phases, not the N-point loop: the N-point polygon's
+    # area is not (1/2) A_circ + (1/4)(A_sq + A_tri)
+    import oracle
+    y = oracle.gen_loops(3, 1, 64)[0]
+
+    def area(p):
+        return 0.5 * np.sum(p[0] * np.roll(p[1], -1) - np.roll(p[0], -1) * p[1])
+
+    A = area(y)
+    mix = 0.5 * area(y[:, 0::2]) + 0.25 * (area(y[:, 1::4]) + area(y[:, 3::4]))
+    assert abs(A - mix) > 0.05 * abs(A)
