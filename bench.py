@@ -387,6 +387,8 @@ def main():
                     help="time per-loop values, randomised groups and Eq. corrcoef")
     ap.add_argument("--levels", action="store_true",
                     help="time the discretisation-level pass (N, N/2, N/4) and extrapolation")
+    ap.add_argument("--nested", action="store_true",
+                    help="with --levels: the nested loops (all, even, 0 mod 4 points)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -655,7 +657,7 @@ def run_levels(args, wl: I.Workload):
     def step(where="device"):
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         L = ctx.wilson_levels(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec,
-                              where=where)
+                              where=where, nested=args.nested)
         X = ctx.extrapolate(L, wl.n_groups, lpg, where=where)
         ens.free()
         return L, X
@@ -673,7 +675,8 @@ def run_levels(args, wl: I.Workload):
             for i in range(args.steps):
                 ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
                 wk[i][0].record(stream)
-                L = ctx.wilson_levels(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+                L = ctx.wilson_levels(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec,
+                                      nested=args.nested)
                 wk[i][1].record(stream)
                 X = ctx.extrapolate(L, wl.n_groups, lpg)
                 ens.free()
@@ -693,9 +696,12 @@ def run_levels(args, wl: I.Workload):
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    seg = wl.segment_evals            # circle N/2 + square N/4 + triangle N/4 = N per loop and point
+    # paper's levels: circle N/2 + square N/4 + triangle N/4 = N segments per
+    # loop and point; nested levels: N + N/2 + N/4
+    seg = wl.segment_evals * (1.75 if args.nested else 1.0)
     achieved = N_ALG_FP32_LEVELS * seg / (kern_ms / 1e3) / 1e12
-    line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation)",
+    line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation"
+                        + (", nested loops)" if args.nested else ")"),
                         wl.loop_points / (ms / 1e3), "loop-point evals/s", args.steps,
                         args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
                         {"workload": wl.name, "n_loops": wl.n_loops, "ppl": wl.ppl,
@@ -703,8 +709,9 @@ def run_levels(args, wl: I.Workload):
                          "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
-                        "traffic": _ncu_traffic(f"wilson_levels_{args.workload}"),
-                        "kernel": "wilson_kernel<F32Comp,3,4,levels>", "kernel_ms": kern_ms,
+                        "traffic": None if args.nested else _ncu_traffic(f"wilson_levels_{args.workload}"),
+                        "kernel": "wilson_kernel<F32Comp,3,4,%s>" % ("nested" if args.nested else "levels"),
+                        "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": N_ALG_FP32_LEVELS,
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
@@ -723,10 +730,12 @@ def run_levels(args, wl: I.Workload):
         prof, rho, T = wl.profiles[q], wl.rho[q][::4], wl.T[q][::4]
         y = oracle.gen_loops(wl.seed, wl.n_loops, wl.ppl).astype(np.float32).astype(np.float64)
         t0 = time.perf_counter()
-        ref = ost.level_sums(oracle, y, prof, rho, T, wl.n_groups, threads=oracle.max_threads())
+        lev = ost.nested_level_sums if args.nested else ost.level_sums
+        ref = lev(oracle, y, prof, rho, T, wl.n_groups, threads=oracle.max_threads())
         dt = time.perf_counter() - t0
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
-        G = ctx.wilson_levels(ens, [prof], [rho], [T], wl.n_groups, prec=args.prec, where="host")
+        G = ctx.wilson_levels(ens, [prof], [rho], [T], wl.n_groups, prec=args.prec, where="host",
+                              nested=args.nested)
         ens.free()
         line["cpu_baseline"] = {
             "value": wl.n_loops * len(rho) * len(T) / dt, "unit": "loop-point evals/s",

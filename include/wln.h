@@ -351,6 +351,23 @@ wln_status wln_loop_sem(wln_ctx* ctx, const double* group_sums, int32_t n_points
                         int32_t comp_sq, double* out);
 
 /*
+ * Discretisation levels from nested loops: W - 1 of every loop through all
+ * N points, through the even points (N/2) and through the points 0 mod 4
+ * (N/4), each walked like a loop in wln_wilson_avg (proper time T/N' per
+ * segment; the same centre of mass).  Same layout, arguments and rules as
+ * wln_wilson_levels.  Read as printed, the paper's level N of
+ * wln_wilson_levels is a point-weighted mean of interleaved sub-loop phases
+ * rather than the N-point loop, so it is not a discretisation hierarchy;
+ * these nested levels are, and wln_extrapolate's parabola in 1/N applies to
+ * them.  The pass walks 1.75 N segments per loop and point.
+ */
+wln_status wln_wilson_levels_nested(wln_ctx* ctx, const wln_ensemble* ens,
+                                    const wln_profile* profiles, int32_t n_profiles,
+                                    const double* rho_cm, const int32_t* rho_off,
+                                    const double* T, const int32_t* T_off,
+                                    int32_t n_groups, wln_prec prec, double* group_sums);
+
+/*
  * Extrapolation to infinitely many points per loop and the discretisation
  * uncertainty (Sec. "Estimating the Discretization Uncertainties"), from the
  * level sums of wln_wilson_levels.  For x in (scalar, spinor) and each point:

@@ -582,12 +582,12 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   if (per_loop) n_groups = 1;
   else if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
     return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
-  if (mode == kModeLevels && (ens->e.ppl % 4 != 0 || ens->e.ppl < 8))
+  if (level_mode(mode) && (ens->e.ppl % 4 != 0 || ens->e.ppl < 8))
     return fail(ctx, WLN_EINVAL, "discretisation levels need ppl a multiple of 4 and >= 8");
   wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
   if (st != WLN_OK) return st;
   DeviceGuard guard(ctx->device);
-  const int K = mode == kModeLevels ? WLN_KL : WLN_K;
+  const int K = level_mode(mode) ? WLN_KL : WLN_K;
 
   Batch bt;
   const int P = plan_points_per_lane(ctx, prec, mode);
@@ -665,6 +665,15 @@ wln_status wln_wilson_levels(wln_ctx* ctx, const wln_ensemble* ens, const wln_pr
                              wln_prec prec, double* group_sums) {
   return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
                      group_sums, kModeLevels);
+}
+
+wln_status wln_wilson_levels_nested(wln_ctx* ctx, const wln_ensemble* ens,
+                                    const wln_profile* profiles, int32_t n_profiles,
+                                    const double* rho_cm, const int32_t* rho_off, const double* T,
+                                    const int32_t* T_off, int32_t n_groups, wln_prec prec,
+                                    double* group_sums) {
+  return wilson_pass(ctx, ens, profiles, n_profiles, rho_cm, rho_off, T, T_off, n_groups, prec,
+                     group_sums, kModeNested);
 }
 
 wln_status wln_wilson_loops(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile* profiles,

@@ -85,7 +85,12 @@ struct Tile {
 
 // What a Wilson launch produces: group sums (WLN_K per point and group), the
 // discretisation levels (WLN_KL), or every loop's W - 1 (scalar, spinor).
-constexpr int kModeSums = 0, kModeLevels = 1, kModeLoops = 2;
+// kModeNested: levels from the nested loops (all points, even points, points
+// 0 mod 4), WLN_KL components like kModeLevels.
+constexpr int kModeSums = 0, kModeLevels = 1, kModeLoops = 2, kModeNested = 3;
+__host__ __device__ constexpr bool level_mode(int mode) {
+  return mode == kModeLevels || mode == kModeNested;
+}
 
 // Geometry of one Wilson launch.
 struct WilsonPlan {
@@ -99,7 +104,7 @@ struct WilsonPlan {
   int n_chains;       // ceil(n_blocks / chain)
   int64_t n_items;    // n_chains * n_tile_groups
   int grid;           // persistent CTAs
-  int mode;           // kModeSums, kModeLevels or kModeLoops
+  int mode;           // kModeSums, kModeLevels, kModeLoops or kModeNested
 };
 
 struct Scratch {

@@ -481,14 +481,17 @@ __device__ __forceinline__ void level_terms(double ph, double sp, F2 tp, F2 st, 
 // acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
 // flush sums each row over the lanes in lane order and writes the partial
 // of (chain, group).  MODE kModeLevels walks the circle, square and triangle
-// sub-loops (w[0..2], K = WLN_KL); kModeLoops writes every loop's W - 1 to
-// global memory instead of accumulating (lanes store 32 consecutive loops).
+// sub-loops (w[0..2], K = WLN_KL); kModeNested the loop through all points,
+// the even points and the points 0 mod 4; kModeLoops writes every loop's
+// W - 1 to global memory instead of accumulating (lanes store 32
+// consecutive loops).
 template <class A, int P, class WalkT, int MODE>
 __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const Tile& tile,
                          const ProfileDev& prof, bool active, volatile int* abort_flag,
                          int lane) {
   using F = typename A::F;
-  constexpr bool LV = MODE == kModeLevels;
+  constexpr bool LV = level_mode(MODE);
+  constexpr bool NEST = MODE == kModeNested;
   constexpr bool PL = MODE == kModeLoops;
   constexpr int K = LV ? kLevelComps : kComps;
   constexpr int NW = LV ? 3 : 1;
@@ -561,6 +564,37 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[0].step(v.x, v.y);
             w[0].step(v.z, v.w);
             if ((r & 3) == 3) w[0].fold();   // every 8 segments
+          }
+        } else if constexpr (NEST) {
+          // Rows in pairs hold points 4j .. 4j + 3: the full walk takes all
+          // four, the even walk 4j and 4j + 2, the quarter walk 4j.  All three
+          // start at point 0 and close back to it.
+          int r = 0;
+          if (ch == 0) {
+            const float4 a = rowp[0], v = rowp[32];
+#pragma unroll
+            for (int q = 0; q < NW; ++q) { fx[q] = a.x; fy[q] = a.y; }
+            w[0].start(a.x, a.y);
+            w[0].step(a.z, a.w);
+            w[0].step(v.x, v.y);
+            w[0].step(v.z, v.w);
+            w[1].start(a.x, a.y);
+            w[1].step(v.x, v.y);
+            w[2].start(a.x, a.y);
+            r = 2;
+          }
+          for (; r < pp.chunk_rows; r += 2) {
+            const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+            w[0].step(a.x, a.y);
+            w[0].step(a.z, a.w);
+            w[0].step(v.x, v.y);
+            w[0].step(v.z, v.w);
+            w[1].step(a.x, a.y);
+            w[1].step(v.x, v.y);
+            w[2].step(a.x, a.y);
+            if ((r & 3) == 2) {   // every 8 segments of the full walk
+              w[0].fold(); w[1].fold(); w[2].fold();
+            }
           }
         } else {
           // Rows come in pairs (chunk_rows is even): row r even holds points
@@ -641,19 +675,27 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
         } else {
           // Spin per segment is T/N' on a sub-loop of N' points: the circle's
           // sums count twice, the square's and triangle's four times, of the
-          // full loop's T/N (a constant field's spin is B T on every loop).
+          // full loop's T/N (a constant field's spin is B T on every loop);
+          // the nested walks of N, N/2 and N/4 points count 1, 2 and 4 times.
           const bool tube = prof.kind != WLN_PROFILE_CONST_B;
           double po, so, pq, sq, pt, stt;
-          walk_sums(w[0], p, tube ? 2.0 : 1.0, po, so);
-          walk_sums(w[1], p, tube ? 4.0 : 1.0, pq, sq);
+          walk_sums(w[0], p, tube ? (NEST ? 1.0 : 2.0) : 1.0, po, so);
+          walk_sums(w[1], p, tube ? (NEST ? 2.0 : 4.0) : 1.0, pq, sq);
           walk_sums(w[2], p, tube ? 4.0 : 1.0, pt, stt);
-          // W_N = e^{i (circ/2 + sq/4 + tri/4)}, W_N/2 = e^{i circ},
-          // W_N/4 = e^{i (sq + tri)/2}; the spins combine the same way.  One
-          // copy of the W arithmetic serves the three levels (registers).
+          // Paper's levels: W_N = e^{i (circ/2 + sq/4 + tri/4)}, W_N/2 = e^{i circ},
+          // W_N/4 = e^{i (sq + tri)/2}, the spins combined the same way.  Nested
+          // levels: each walk is its own level.  One copy of the W arithmetic
+          // serves the three levels (registers).
 #pragma unroll 1
           for (int L = 0; L < 3; ++L) {
-            const double ph = L == 0 ? 0.5 * po + 0.25 * (pq + pt) : (L == 1 ? po : 0.5 * (pq + pt));
-            const double sp = L == 0 ? 0.5 * so + 0.25 * (sq + stt) : (L == 1 ? so : 0.5 * (sq + stt));
+            double ph, sp;
+            if (NEST) {
+              ph = L == 0 ? po : (L == 1 ? pq : pt);
+              sp = L == 0 ? so : (L == 1 ? sq : stt);
+            } else {
+              ph = L == 0 ? 0.5 * po + 0.25 * (pq + pt) : (L == 1 ? po : 0.5 * (pq + pt));
+              sp = L == 0 ? 0.5 * so + 0.25 * (sq + stt) : (L == 1 ? so : 0.5 * (sq + stt));
+            }
             double t[2];
             level_terms<A>(ph, sp, tp, st, prof.turns_per, st_d, t);
             if (mine) {
@@ -677,13 +719,13 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 // x 1 CTA 659 ms, 4 radii x 8 warps x 2 CTAs 682 ms (spilling); the level
 // pass 3 radii x 4 warps x 2 CTAs 757 ms, 4 x 8 x 1 774 ms.
 constexpr int min_ctas(int P, int warps, int mode) {
-  return (mode == kModeLevels || P >= 8) ? 256 / (warps * 32)
+  return (level_mode(mode) || P >= 8) ? 256 / (warps * 32)
                                          : (P == 4 && warps == 4) ? 3 : 512 / (warps * 32);
 }
 
 template <class A, int P, int WARPS, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_kernel(const KParams k) {
-  constexpr int K = MODE == kModeLevels ? kLevelComps : kComps;
+  constexpr int K = level_mode(MODE) ? kLevelComps : kComps;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
 
@@ -729,8 +771,8 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
     else   // three walks per radius: Q fits in registers for up to 3 radii per lane
-      ok = run_item<A, P, Walk<A, P, MODE != kModeLevels || P <= 3>, MODE>(k, pp, acc, c, tile, prof,
-                                                                            active, &abort_flag, lane);
+      ok = run_item<A, P, Walk<A, P, !level_mode(MODE) || P <= 3>, MODE>(k, pp, acc, c, tile, prof,
+                                                                           active, &abort_flag, lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -794,7 +836,7 @@ int occupancy(size_t smem) {
 
 size_t smem_bytes(const WilsonPlan& p, int ppl) {
   const int chunk_rows = p.rows < ppl / 2 ? p.rows : ppl / 2;
-  const int K = p.mode == kModeLevels ? kLevelComps : kComps;
+  const int K = level_mode(p.mode) ? kLevelComps : kComps;
   return static_cast<size_t>(p.stages) * chunk_rows * 512 +
          static_cast<size_t>(p.warps) * p.P * K * 33 * sizeof(double) +
          2 * p.stages * sizeof(uint64_t);
@@ -807,7 +849,7 @@ size_t smem_bytes(const WilsonPlan& p, int ppl) {
 // walks per radius (4 radii per lane, FP64 1) and ignore the tuning of the
 // plain pass.
 int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode) {
-  if (mode == kModeLevels) return prec == WLN_PREC_FP64 ? 1 : 3;
+  if (level_mode(mode)) return prec == WLN_PREC_FP64 ? 1 : 3;
   if (mode == kModeLoops) return prec == WLN_PREC_FP64 ? 2 : 4;
   if (prec == WLN_PREC_FP64) return 2;
   return ctx->tune_P ? ctx->tune_P : 4;
@@ -821,7 +863,7 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
   // (4, 4): 3 CTAs per SM; levels (3, 4): 2 CTAs per SM
-  const int def_warps = (mode == kModeLevels || p.P == 4) ? 4 : 8;
+  const int def_warps = (level_mode(mode) || p.P == 4) ? 4 : 8;
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
   p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
   p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
@@ -885,6 +927,14 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
     }
     return cudaErrorInvalidConfiguration;
   }
+  if (plan.mode == kModeNested) {
+    switch (prec) {
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 3, 4, kModeNested) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 3, 4, kModeNested) break;
+      case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, kModeNested) break;
+    }
+    return cudaErrorInvalidConfiguration;
+  }
   if (plan.mode == kModeLoops) {
     switch (prec) {
       case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 4, kModeLoops) break;
@@ -943,7 +993,7 @@ cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const
                                    const double* partial, int64_t n_points, int32_t n_groups,
                                    int32_t loops_per_group, double* group_sums) {
   (void)e;
-  const int K = plan.mode == kModeLevels ? kLevelComps : kComps;
+  const int K = level_mode(plan.mode) ? kLevelComps : kComps;
   const int64_t n = n_points * n_groups * K;
   if (n == 0) return cudaSuccess;
   reduce_partials_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(

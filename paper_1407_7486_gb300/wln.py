@@ -50,6 +50,8 @@ SIGNATURES = {
                                ctypes.c_int),
     "wln_wilson_levels": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
                           ctypes.c_int),
+    "wln_wilson_levels_nested": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
+                                 ctypes.c_int),
     "wln_extrapolate": ([_P, _P, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_mapped_grid": ([_I32, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
     "wln_effective_action_full": ([_P, _P, _I32, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
@@ -336,19 +338,21 @@ class Context:
 
     def wilson_levels(self, ens: Ensemble, profiles: Sequence[Profile], rho: Sequence,
                       T: Sequence, n_groups: int, prec: str = "fp32", out=None,
-                      where: str = "device"):
+                      where: str = "device", nested: bool = False):
         """Discretisation-level group sums [n_points][n_groups][6]: W - 1
         (scalar, spinor) at N, N/2 and N/4 points per loop, from the
-        interleaved sub-loops of every loop."""
+        interleaved sub-loops of every loop as the paper combines them, or
+        (nested=True) from the nested loops through all, even and 0 mod 4
+        points."""
         rho_f, rho_off = _csr(rho)
         T_f, T_off = _csr(T)
         n_points = int(sum(len(r) * len(t) for r, t in zip(rho, T)))
         if out is None:
             out = self._empty((n_points, n_groups, WLN_KL), np.float64, where)
         profs = _profiles(profiles)
-        self._check(load().wln_wilson_levels(self.handle, ens.handle, profs, len(profiles),
-                                             _ptr(rho_f), _ptr(rho_off), _ptr(T_f), _ptr(T_off),
-                                             n_groups, PREC[prec], _ptr(out)))
+        fn = load().wln_wilson_levels_nested if nested else load().wln_wilson_levels
+        self._check(fn(self.handle, ens.handle, profs, len(profiles), _ptr(rho_f), _ptr(rho_off),
+                       _ptr(T_f), _ptr(T_off), n_groups, PREC[prec], _ptr(out)))
         return out
 
     def extrapolate(self, level_sums, n_groups: int, loops_per_group: int,

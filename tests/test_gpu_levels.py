@@ -162,3 +162,61 @@ def test_extrapolation_matches_oracle(ctx):
         np.testing.assert_allclose(got[:, x, 5], np.abs(got[:, x, 0] - m_inf), rtol=1e-10,
                                    atol=1e-15)
     ens.free()
+
+
+def _nested_bars(y32, profile, rho, T, G, tol, rel):
+    """Per-level bars for the nested levels: each level is a genuine loop
+    (all, even, 0 mod 4 points), with its own sums of |segment phase| and spin."""
+    y = y32.astype(np.float64)
+    subs = [y, np.ascontiguousarray(y[:, :, 0::2]), np.ascontiguousarray(y[:, :, 0::4])]
+    lpg = y.shape[0] // G
+    n = len(T) * len(rho)
+    out = {c: (np.zeros((n, G)), np.zeros(n)) for c in range(6)}
+    for b, t in enumerate(T):
+        for a, r in enumerate(rho):
+            p = b * len(rho) + a
+            for L, sub in enumerate(subs):
+                _, s = oracle.phase_spin(sub, profile, r, t)
+                P = oracle.phase_abs(sub, profile, r, t)
+                with np.errstate(over="ignore", invalid="ignore"):
+                    es = np.maximum(tol, rel * P)
+                    ef = np.maximum(1.0, np.cosh(s)) * np.maximum(tol, rel * (np.abs(s) + P))
+                for c, e in ((2 * L, es), (2 * L + 1, ef)):
+                    out[c][0][p] = e.reshape(G, lpg).mean(axis=1)
+                    out[c][1][p] = e.mean()
+    return out
+
+
+@pytest.mark.parametrize("case", range(len(LEVEL_CASES)))
+@pytest.mark.parametrize("prec,tol,rel", [("fp64", 1e-12, F64_REL), ("fp32", 1e-6, F32_REL)])
+def test_nested_levels_match_oracle(ctx, case, prec, tol, rel):
+    n_loops, ppl, G, prof, rho, T = LEVEL_CASES[case]
+    y32, ens = _ensemble(ctx, 141 + case, n_loops, ppl)
+    gpu = ctx.wilson_levels(ens, [prof], [rho], [T], G, prec=prec, where="host", nested=True)
+    ref = ost.nested_level_sums(oracle, y32.astype(np.float64), prof, rho, T, G)
+    _compare(gpu, ref, n_loops // G, _nested_bars(y32, prof, rho, T, G, tol, rel),
+             f"{prec} nested level case {case}")
+    ens.free()
+
+
+def test_nested_extrapolation_recovers_the_continuum(ctx):
+    # constant field: the nested levels' parabola lands on b/sinh b and b coth b
+    # within its group error, far closer than the finest level; the paper's
+    # printed combination moves away from it (its levels are no hierarchy)
+    import math
+    n_loops, N, G, B = 32768, 32, 32, 1.0
+    ens = ctx.gen_loops(3, n_loops, N)
+    prof, rho, T = I.Profile(1, B=B), [np.zeros(1)], [np.array([1.0])]
+    lpg = n_loops // G
+    cont = [B / math.sinh(B) - 1.0, B / math.tanh(B) - 1.0]
+    for nested in (True, False):
+        L = ctx.wilson_levels(ens, [prof], rho, T, G, prec="fp64", where="host", nested=nested)
+        X = ctx.extrapolate(L, G, lpg, where="host")[0]
+        for x in (0, 1):
+            m_N, m_inf, sem_inf = X[x, 0], X[x, 3], X[x, 4]
+            if nested:
+                assert abs(m_inf - cont[x]) < 5 * sem_inf, (x, m_inf, cont[x], sem_inf)
+                assert abs(m_inf - cont[x]) < 0.2 * abs(m_N - cont[x])
+            else:
+                assert abs(m_inf - cont[x]) > abs(m_N - cont[x])
+    ens.free()
