@@ -230,6 +230,12 @@ class Context:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def selftest_wait(self, timeout_ms: int = 50) -> int:
         """Run the bounded-wait self-test; returns the status (WLN_ETIMEOUT = 4)."""
         return int(load().wln_selftest_wait(self.handle, timeout_ms))
