@@ -709,7 +709,8 @@ def run_levels(args, wl: I.Workload):
                          "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
-                        "traffic": None if args.nested else _ncu_traffic(f"wilson_levels_{args.workload}"),
+                        "traffic": _ncu_traffic(("wilson_nested_" if args.nested else "wilson_levels_")
+                                                + args.workload),
                         "kernel": "wilson_kernel<F32Comp,3,4,%s>" % ("nested" if args.nested else "levels"),
                         "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
@@ -829,7 +830,8 @@ def run_correlation(args, wl: I.Workload):
                          "ppl": wl.ppl, "n_points": n_points, "n_groups": wl.n_groups,
                          "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
-                        "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": None,
+                        "unit": "T FP32 op/s", "frac": achieved / peak_ops,
+                        "traffic": _ncu_traffic(f"wilson_loops_{args.workload}"),
                         "kernel": "wilson_kernel<F32Comp,4,4,loops>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
