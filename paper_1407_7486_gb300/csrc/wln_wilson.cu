@@ -650,8 +650,11 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             double ps, pc, ss, sc, t[kComps];
             w[0].raw(p, ps, pc, ss, sc);
             wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, t);
-            reinterpret_cast<double2*>(k.loops_out)[static_cast<int64_t>(tile.p0 + p) * k.n_loops + loop] =
-                make_double2(t[0], t[1]);
+            // evict-first store: the results stream past L2 without pushing
+            // out the loop chain the CTAs are sweeping
+            __stcs(reinterpret_cast<double2*>(k.loops_out) +
+                       static_cast<int64_t>(tile.p0 + p) * k.n_loops + loop,
+                   make_double2(t[0], t[1]));
           }
         }
       }
