@@ -370,7 +370,9 @@ wln_status wln_wilson_levels_nested(wln_ctx* ctx, const wln_ensemble* ens,
 /*
  * Extrapolation to infinitely many points per loop and the discretisation
  * uncertainty (Sec. "Estimating the Discretization Uncertainties"), from the
- * level sums of wln_wilson_levels.  For x in (scalar, spinor) and each point:
+ * level sums of wln_wilson_levels or wln_wilson_levels_nested (the parabola
+ * presumes genuine levels of one loop, which the nested ones are).  For x in
+ * (scalar, spinor) and each point:
  *   m_L = mean over all loops of W - 1 at level L in (N, N/2, N/4);
  *   W_inf - 1 = 8/3 m_N - 2 m_N/2 + 1/3 m_N/4 (the parabola in 1/N through
  *   the three levels, taken at 1/N = 0);
