@@ -1,4 +1,4 @@
-"""Precision and discretisation sweep (the survey's sweep workload), through the
+"""Precision and discretisation sweep, through the
 C ABI: 8192 loops at ppl = 256, 1024, 4096 and 16384; flux tubes F in {1, 100}
 x lambda in {0.1, 1} and constant fields B in {0.1, 1, 5} at rho = 0; FP32
 naive, FP32 compensated and FP64 side by side.  Each result is compared with
