@@ -15,7 +15,6 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-from typing import Optional
 
 import numpy as np
 

@@ -18,7 +18,7 @@ import itertools
 import json
 import os
 import time
-from typing import Dict, Optional, Sequence
+from typing import Dict, Sequence
 
 import numpy as np
 

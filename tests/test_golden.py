@@ -16,7 +16,6 @@ from fractions import Fraction
 
 import numpy as np
 
-import oracle
 from oracle import stats as ost
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")

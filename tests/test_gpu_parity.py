@@ -13,7 +13,6 @@ Tolerances:
     Problem").
   * Statistics and quadrature on identical group sums: 1e-12 relative.
 """
-import math
 
 import numpy as np
 import pytest
