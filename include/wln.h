@@ -495,6 +495,19 @@ wln_status wln_effective_action_full(wln_ctx* ctx, const wln_profile* profiles,
 wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, int32_t rows,
                           int32_t stages, int32_t chain_blocks);
 
+/*
+ * The float walks evaluate theta = atan2(sqrt(D), Q0 + B) (the angle a
+ * segment subtends at the field axis, Sec. "Wilson Loop", Eqs. rhoi-Ci) in a
+ * cheaper form where every segment of a 32-loop block is known to subtend at
+ * most pi/4: 2 |d| <= sqrt(lambda^2 + (rho_cm - sqrt(T) |y|max)_+^2) with a
+ * margin, |d| the block's longest scaled segment (times 4 for the sub-loops
+ * of the discretisation levels).  Both forms give the same angle bit for bit
+ * there.  enable = 0 makes later launches on this context use the general
+ * form everywhere (for checking that equality); 1 (the default) restores the
+ * choice.  Any other value: WLN_EINVAL.
+ */
+wln_status wln_set_low_angle(wln_ctx* ctx, int32_t enable);
+
 /* -------------------------------------------------------- runtime: batches */
 
 /*

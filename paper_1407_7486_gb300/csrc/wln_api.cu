@@ -130,10 +130,13 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
   en->e.n_blocks = (n_loops + 31) / 32;
   const size_t n4 = static_cast<size_t>(en->e.n_blocks) * (ppl / 2) * 32;
   cudaError_t err = cudaMalloc(&en->e.blocks, n4 * sizeof(float4));
+  if (err == cudaSuccess)
+    err = cudaMalloc(&en->e.stats, static_cast<size_t>(en->e.n_blocks) * sizeof(float2));
   if (err == cudaSuccess && fp64)
     err = cudaMalloc(&en->e.xy64, static_cast<size_t>(n_loops) * 2 * ppl * sizeof(double));
   if (err != cudaSuccess) {
     if (en->e.blocks) cudaFree(en->e.blocks);
+    if (en->e.stats) cudaFree(en->e.stats);
     delete en;
     return cuda_fail(ctx, err, "cudaMalloc ensemble");
   }
@@ -432,7 +435,7 @@ wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_l
   int* d_deg = static_cast<int*>(ctx->scratch.ptr);
   cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
   if (err == cudaSuccess) err = launch_gen_loops(ctx->stream, seed, en->e, d_deg);
-  ctx->launches += 2;
+  ctx->launches += 3;
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "launch loop generation");
@@ -460,7 +463,7 @@ wln_status wln_gen_dloops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_
   cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
   if (err == cudaSuccess)
     err = launch_gen_dloops(ctx->stream, seed, en->e, at<double>(ctx->scratch.ptr, o_work), d_deg);
-  ctx->launches += 2;
+  ctx->launches += 3;
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "launch d-loop generation");
@@ -492,7 +495,7 @@ wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops
     src = d_xy;
   }
   if (err == cudaSuccess) err = launch_pack_loops(ctx->stream, src, en->e, d_deg);
-  ctx->launches += 2;
+  ctx->launches += 3;
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "pack loops");
@@ -505,6 +508,7 @@ wln_status wln_free_ensemble(wln_ctx* ctx, wln_ensemble* ens) {
   DeviceGuard guard(ens->device);
   if (ctx) cudaStreamSynchronize(ctx->stream);
   if (ens->e.blocks) cudaFree(ens->e.blocks);
+  if (ens->e.stats) cudaFree(ens->e.stats);
   if (ens->e.xy64) cudaFree(ens->e.xy64);
   delete ens;
   return WLN_OK;

@@ -209,6 +209,48 @@ __global__ void degenerate_kernel(const float4* blocks, int32_t n_loops, int32_t
   if (same01 || same12) atomicOr(flag, 1);
 }
 
+// Per block of 32 loops: the longest segment (closing segment included) and
+// the largest distance of a point from the loop's centre, over the block's
+// valid loops.  The Wilson kernel bounds the angle its segments subtend at
+// the field axis with them.  One CTA per block, a fixed reduction tree.
+__global__ void block_stats_kernel(const float4* blocks, int32_t n_loops, int32_t ppl,
+                                   float2* stats) {
+  __shared__ float sd[8], sr[8];
+  const int64_t rows = ppl / 2;
+  const int64_t b = blockIdx.x;
+  const float4* base = blocks + b * rows * 32;
+  float d2 = 0.f, r2 = 0.f;
+  for (int64_t i = threadIdx.x; i < rows * 32; i += blockDim.x) {
+    const int lane = static_cast<int>(i & 31);
+    const int64_t r = i >> 5;
+    if (b * 32 + lane >= n_loops) continue;
+    const float4 a = base[r * 32 + lane];
+    const float4 c = base[((r + 1) % rows) * 32 + lane];
+    const float ux = a.z - a.x, uy = a.w - a.y, vx = c.x - a.z, vy = c.y - a.w;
+    d2 = fmaxf(d2, fmaxf(ux * ux + uy * uy, vx * vx + vy * vy));
+    r2 = fmaxf(r2, fmaxf(a.x * a.x + a.y * a.y, a.z * a.z + a.w * a.w));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d2; sr[threadIdx.x >> 5] = r2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      d2 = fmaxf(d2, sd[w]);
+      r2 = fmaxf(r2, sr[w]);
+    }
+    // square roots rounded up by a relative 2^-20: bounds, not estimates
+    stats[b] = make_float2(sqrtf(d2) * (1.0f + 0x1p-20f), sqrtf(r2) * (1.0f + 0x1p-20f));
+  }
+}
+
+cudaError_t launch_block_stats(cudaStream_t s, const Ensemble& e) {
+  block_stats_kernel<<<e.n_blocks, 256, 0, s>>>(e.blocks, e.n_loops, e.ppl, e.stats);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
@@ -233,7 +275,9 @@ cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, i
   const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
   degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
                                                                           e.ppl, d_degenerate);
-  return cudaGetLastError();
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_block_stats(s, e);
 }
 
 cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
@@ -244,7 +288,9 @@ cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, 
   const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
   degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
                                                                           e.ppl, d_degenerate);
-  return cudaGetLastError();
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_block_stats(s, e);
 }
 
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate) {
@@ -256,7 +302,9 @@ cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e
   const int64_t m = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
   degenerate_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,
                                                                           e.ppl, d_degenerate);
-  return cudaGetLastError();
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_block_stats(s, e);
 }
 
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy) {

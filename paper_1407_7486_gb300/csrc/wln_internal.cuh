@@ -55,6 +55,7 @@ struct Ensemble {
   int32_t n_blocks = 0;       // ceil(n_loops / 32)
   float4* blocks = nullptr;   // [n_blocks][ppl/2][32]
   double* xy64 = nullptr;     // optional [n_loops][2][ppl]
+  float2* stats = nullptr;    // [n_blocks]: longest segment, largest |y| of the block's loops
 };
 
 // Per-profile constants used by the Wilson kernels.
@@ -105,6 +106,7 @@ struct WilsonPlan {
   int64_t n_items;    // n_chains * n_tile_groups
   int grid;           // persistent CTAs
   int mode;           // kModeSums, kModeLevels, kModeLoops or kModeNested
+  int low_angle;      // blocks whose segments all subtend <= pi/4 take the low form
 };
 
 struct Scratch {
@@ -127,6 +129,7 @@ struct wln_ctx {
   cudaEvent_t staging_done = nullptr;
   // tuning overrides (0 = automatic)
   int tune_P = 0, tune_warps = 0, tune_rows = 0, tune_stages = 0, tune_chain = 0;
+  int low_angle = 1;    // float walks may take the low-angle form of theta
 };
 
 struct wln_ensemble {

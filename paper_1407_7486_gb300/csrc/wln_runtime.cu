@@ -81,6 +81,13 @@ cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* laun
 
 extern "C" {
 
+wln_status wln_set_low_angle(wln_ctx* ctx, int32_t enable) {
+  if (!ctx) return WLN_EINVAL;
+  if (enable != 0 && enable != 1) return fail(ctx, WLN_EINVAL, "low_angle: enable must be 0 or 1");
+  ctx->low_angle = enable;
+  return WLN_OK;
+}
+
 wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, int32_t rows,
                           int32_t stages, int32_t chain_blocks) {
   if (!ctx) return WLN_EINVAL;

@@ -28,6 +28,15 @@
 // fixed order into per-(chain, group) partials; a second kernel sums the
 // partials of each group in chain order.
 //
+// Low-angle form: theta = atan2(sqrt(D), Q0 + B) is at most pi/4 whenever
+// 2 |d| <= sqrt(Q0) (D <= Q0 C and B >= -sqrt(Q0) |d|).  Every ensemble
+// carries, per 32-loop block, its longest segment and largest |y|; when they
+// guarantee this for every segment of the block at the warp's tile (T, rho,
+// lambda), the warp walks that block with the arctangent's low form, without
+// the range fold and the octant unfolding (6 of the 17 operations of theta),
+// and gets the same bits.  The choice is per block and the same on every
+// lane, so the walk has no branch per segment.
+//
 // Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
 // the same pass can instead walk the three interleaved sub-loops of every
 // loop -- circle (even points, N/2 of them), square (points 1 mod 4) and
@@ -129,9 +138,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // 1.7e-8 in exact arithmetic, within 1.3 float ulps as evaluated here);
 // then the octant is unfolded: pi/2 - atan for y > |x|, pi - angle for x < 0.
 // Inputs are finite with y > 0, so no special cases are needed.
-__device__ __forceinline__ float atan2_pos(float y, float x) {
-  const float ax = fabsf(x);
-  const float t = fminf(y, ax) * rcp_approx(fmaxf(y, ax));
+__device__ __forceinline__ float atan_unit(float t) {
   const float s = t * t;
   float q = 0.002920693f;
   q = fmaf(q, s, -0.01636793f);
@@ -141,31 +148,50 @@ __device__ __forceinline__ float atan2_pos(float y, float x) {
   q = fmaf(q, s, -0.14211056f);
   q = fmaf(q, s, 0.19993773f);
   q = fmaf(q, s, -0.33333153f);
-  float r = fmaf(t * s, q, t);
+  return fmaf(t * s, q, t);
+}
+
+__device__ __forceinline__ float atan2_pos(float y, float x) {
+  const float ax = fabsf(x);
+  float r = atan_unit(fminf(y, ax) * rcp_approx(fmaxf(y, ax)));
   r = y > ax ? 1.5707963267948966f - r : r;
   return x < 0.0f ? 3.14159265358979323846f - r : r;
 }
 
+// The same angle when 0 < y <= x (at most pi/4): no octant to unfold, and
+// bitwise equal to atan2_pos there.
+__device__ __forceinline__ float atan2_low(float y, float x) {
+  return atan_unit(y * rcp_approx(x));
+}
+
+// at2_low: the angle when every segment of a work item is known to subtend
+// at most pi/4 at the field axis (kLowAngle: the flavour has a cheaper form).
 struct F32Comp {
   using F = float;
   static constexpr bool kCompensated = true;
+  static constexpr bool kLowAngle = true;
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   __device__ static float at2(float y, float x) { return atan2_pos(y, x); }
+  __device__ static float at2_low(float y, float x) { return atan2_low(y, x); }
 };
 struct F32Naive {
   using F = float;
   static constexpr bool kCompensated = false;
+  static constexpr bool kLowAngle = true;
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   __device__ static float at2(float y, float x) { return atan2_pos(y, x); }
+  __device__ static float at2_low(float y, float x) { return atan2_low(y, x); }
 };
 struct F64 {
   using F = double;
   static constexpr bool kCompensated = false;
+  static constexpr bool kLowAngle = false;
   __device__ static double rcp(double x) { return 1.0 / x; }
   __device__ static double rsq(double x) { return rsqrt(x); }
   __device__ static double at2(double y, double x) { return atan2(y, x); }
+  __device__ static double at2_low(double y, double x) { return atan2(y, x); }
 };
 
 // Sum of segment terms: terms are added plainly into `part`, and every few
@@ -208,12 +234,34 @@ struct KParams {
   int64_t n_items;
   int* flag;
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
+  const float2* stats;   // per block: longest segment, largest |y|
+  int32_t low_angle;     // 0: the general form of theta everywhere
+};
+
+// Whether every segment of block b subtends at most pi/4 at the field axis
+// for the warp's tile, i.e. theta <= pi/4, i.e. sqrt(D) <= Q0 + B.  With |d|
+// the segment, D <= Q0 C = Q0 |d|^2 (Lagrange) and B >= -|r| |d| >= -sqrt(Q0)
+// |d|, so 2 |d| <= sqrt(Q0) is enough, and Q0 >= lambda^2 + (rho -
+// sqrt(T) |y|_max)^2 for rho > sqrt(T) |y|_max.  The segments are sqrt(T)
+// times the unit loop's (up to span of them for a sub-loop), and a margin of
+// 0.9 keeps the float comparison of the two sides on the same side.  Every
+// lane computes the same answer from the same block statistics.
+// (In float: the margin is far above its rounding.)
+struct LowAngle {
+  float two_span_sT, sT, rho_min, l2;
+  __device__ __forceinline__ bool block(const KParams& k, int b) const {
+    const float2 st = k.stats[b];
+    const float gap = fmaxf(0.0f, rho_min - sT * st.y);
+    return two_span_sT * st.x <= 0.9f * sqrtf(l2 + gap * gap);
+  }
 };
 
 // Per-lane walk of one loop for the P radii of a tile (flux tube).  CQ
 // carries Q at the current point so that theta = atan2(sqrt(D), Q0 + B)
 // (one multiply fewer per segment and radius, one register more per radius);
-// without it theta = atan2(C sqrt(D), D + B (B + C)).
+// without it theta = atan2(C sqrt(D), D + B (B + C)).  step_<true> may be
+// used when every segment subtends at most pi/4 at the axis (the caller has
+// checked): theta then needs no octant unfolding.
 template <class A, int P, bool CQ = true>
 struct Walk {
   using F = typename A::F;
@@ -242,7 +290,10 @@ struct Walk {
   }
 
   // Advance along the straight segment to unit-loop point (x1, y1).
-  __device__ __forceinline__ void step(F x1, F y1) {
+  __device__ __forceinline__ void step(F x1, F y1) { step_<false>(x1, y1); }
+
+  template <bool LOW>
+  __device__ __forceinline__ void step_(F x1, F y1) {
     const F dx = s * (x1 - ux), dy = s * (y1 - uy);
     const F C = fma(dx, dx, dy * dy);
     const F l2C = l2 * C;
@@ -261,7 +312,9 @@ struct Walk {
       const F BC = B + C;
       // atan2(C sqrt(D), D + B (B + C)) with the common factor C removed:
       // Q0 C = D + B^2 (Lagrange), so D + B (B + C) = C (Q0 + B).
-      const F theta = CQ ? A::at2(D * rsD, q[p] + B) : A::at2(C * (D * rsD), fma(B, BC, D));
+      const F ya = CQ ? D * rsD : C * (D * rsD);
+      const F xa = CQ ? q[p] + B : fma(B, BC, D);
+      const F theta = LOW ? A::at2_low(ya, xa) : A::at2(ya, xa);
       const F J1 = theta * rsD;
       ph[p].add(X * J1);
       // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
@@ -301,7 +354,9 @@ struct WalkB {
 #pragma unroll
     for (int p = 0; p < P; ++p) { rx[p] = fma(s, x0, rho[p]); ph[p].zero(); }
   }
-  __device__ __forceinline__ void step(F x1, F y1) {
+  __device__ __forceinline__ void step(F x1, F y1) { step_<false>(x1, y1); }
+  template <bool LOW>
+  __device__ __forceinline__ void step_(F x1, F y1) {
     const F dx = s * (x1 - ux), dy = s * (y1 - uy);
     const F rydx = ry * dx;
 #pragma unroll
@@ -509,6 +564,14 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   }
   const double st_d = prof.spin_per * tile.T;
   const F2 tp = split(prof.turns_per), st = split(st_d);
+  // sub-loop segments join points up to 4 apart
+  double rho_min = k.rho[tile.rho0];
+  for (int p = 1; p < tile.n_valid; ++p) rho_min = fmin(rho_min, k.rho[tile.rho0 + p]);
+  const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
+                    static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
+                    static_cast<float>(prof.l2)};
+  const bool la_ok =
+      A::kLowAngle && k.low_angle && prof.kind == WLN_PROFILE_FLUX_TUBE && tile.n_valid > 0;
   const int b0 = c * k.chain;
   const int b1 = min(b0 + k.chain, k.n_blocks);
   int g_cur = (b0 * 32) / k.lpg;
@@ -536,6 +599,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   for (int b = b0; b < b1; ++b) {
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
+    const bool low = la_ok && la.block(k, b);   // the same on every lane
     // first point of each walk, for the closing segments
     float fx[NW], fy[NW];
 #pragma unroll
@@ -543,8 +607,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     for (int ch = 0; ch < pp.chunks_per_block; ++ch) {
       const int slot = static_cast<int>(pp.kc % pp.stages);
       const uint32_t parity = static_cast<uint32_t>((pp.kc / pp.stages) & 1);
-      if (!mbar_wait(&pp.full[slot], parity)) {
-        atomicExch(k.flag, kErrTimeoutFull);
+      // every lane of the warp takes the same decision (the warp's
+      // shuffles and syncs need all 32 lanes)
+      if (!__all_sync(0xffffffffu, mbar_wait(&pp.full[slot], parity))) {
+        if (lane == 0) atomicExch(k.flag, kErrTimeoutFull);
         *abort_flag = 1;
         return false;
       }
@@ -559,11 +625,21 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[0].step(v.z, v.w);
             r = 1;
           }
-          for (; r < pp.chunk_rows; ++r) {
-            const float4 v = rowp[r * 32];
-            w[0].step(v.x, v.y);
-            w[0].step(v.z, v.w);
-            if ((r & 3) == 3) w[0].fold();   // every 8 segments
+          // low: the same walk with the angle's low form (warp-uniform flag)
+          if (low) {
+            for (; r < pp.chunk_rows; ++r) {
+              const float4 v = rowp[r * 32];
+              w[0].template step_<true>(v.x, v.y);
+              w[0].template step_<true>(v.z, v.w);
+              if ((r & 3) == 3) w[0].fold();   // every 8 segments
+            }
+          } else {
+            for (; r < pp.chunk_rows; ++r) {
+              const float4 v = rowp[r * 32];
+              w[0].step(v.x, v.y);
+              w[0].step(v.z, v.w);
+              if ((r & 3) == 3) w[0].fold();   // every 8 segments
+            }
           }
         } else if constexpr (NEST) {
           // Rows in pairs hold points 4j .. 4j + 3: the full walk takes all
@@ -583,17 +659,33 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(a.x, a.y);
             r = 2;
           }
-          for (; r < pp.chunk_rows; r += 2) {
-            const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-            w[0].step(a.x, a.y);
-            w[0].step(a.z, a.w);
-            w[0].step(v.x, v.y);
-            w[0].step(v.z, v.w);
-            w[1].step(a.x, a.y);
-            w[1].step(v.x, v.y);
-            w[2].step(a.x, a.y);
-            if ((r & 3) == 2) {   // every 8 segments of the full walk
-              w[0].fold(); w[1].fold(); w[2].fold();
+          if (low) {
+            for (; r < pp.chunk_rows; r += 2) {
+              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+              w[0].template step_<true>(a.x, a.y);
+              w[0].template step_<true>(a.z, a.w);
+              w[0].template step_<true>(v.x, v.y);
+              w[0].template step_<true>(v.z, v.w);
+              w[1].template step_<true>(a.x, a.y);
+              w[1].template step_<true>(v.x, v.y);
+              w[2].template step_<true>(a.x, a.y);
+              if ((r & 3) == 2) {   // every 8 segments of the full walk
+                w[0].fold(); w[1].fold(); w[2].fold();
+              }
+            }
+          } else {
+            for (; r < pp.chunk_rows; r += 2) {
+              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+              w[0].step(a.x, a.y);
+              w[0].step(a.z, a.w);
+              w[0].step(v.x, v.y);
+              w[0].step(v.z, v.w);
+              w[1].step(a.x, a.y);
+              w[1].step(v.x, v.y);
+              w[2].step(a.x, a.y);
+              if ((r & 3) == 2) {   // every 8 segments of the full walk
+                w[0].fold(); w[1].fold(); w[2].fold();
+              }
             }
           }
         } else {
@@ -610,14 +702,27 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(v.z, v.w);
             r = 2;
           }
-          for (; r < pp.chunk_rows; r += 2) {
-            const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-            w[0].step(a.x, a.y);
-            w[1].step(a.z, a.w);
-            w[0].step(v.x, v.y);
-            w[2].step(v.z, v.w);
-            if ((r & 7) == 6) {   // every 8 circle segments
-              w[0].fold(); w[1].fold(); w[2].fold();
+          if (low) {
+            for (; r < pp.chunk_rows; r += 2) {
+              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+              w[0].template step_<true>(a.x, a.y);
+              w[1].template step_<true>(a.z, a.w);
+              w[0].template step_<true>(v.x, v.y);
+              w[2].template step_<true>(v.z, v.w);
+              if ((r & 7) == 6) {   // every 8 circle segments
+                w[0].fold(); w[1].fold(); w[2].fold();
+              }
+            }
+          } else {
+            for (; r < pp.chunk_rows; r += 2) {
+              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+              w[0].step(a.x, a.y);
+              w[1].step(a.z, a.w);
+              w[0].step(v.x, v.y);
+              w[2].step(v.z, v.w);
+              if ((r & 7) == 6) {   // every 8 circle segments
+                w[0].fold(); w[1].fold(); w[2].fold();
+              }
             }
           }
         }
@@ -634,7 +739,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
         }
       }
       ++pp.kc;
-      if (*abort_flag) return false;
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) return false;
     }
     if (!active) continue;
 #pragma unroll
@@ -771,11 +876,13 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
     const Tile tile = k.tiles[t < k.n_tiles ? t : 0];
     const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
     const ProfileDev prof = k.profs[tile.profile];
+    // three walks per radius: Q fits in registers for up to 3 radii per lane
+    constexpr bool CQ = !level_mode(MODE) || P <= 3;
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
-    else   // three walks per radius: Q fits in registers for up to 3 radii per lane
-      ok = run_item<A, P, Walk<A, P, !level_mode(MODE) || P <= 3>, MODE>(k, pp, acc, c, tile, prof,
-                                                                           active, &abort_flag, lane);
+    else
+      ok = run_item<A, P, Walk<A, P, CQ>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag,
+                                                lane);
   }
 
   if (!ok && threadIdx.x == 0) {
@@ -863,6 +970,7 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   WilsonPlan p{};
   p.P = plan_points_per_lane(ctx, prec, mode);
   p.mode = mode;
+  p.low_angle = ctx->low_angle;
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
   // (4, 4): 3 CTAs per SM; levels (3, 4): 2 CTAs per SM
@@ -909,6 +1017,8 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
   kp.rows = plan.rows; kp.stages = plan.stages; kp.chain = plan.chain;
   kp.n_tile_groups = plan.n_tile_groups; kp.n_chains = plan.n_chains; kp.n_items = plan.n_items;
   kp.flag = d_flag;
+  kp.stats = e.stats;
+  kp.low_angle = plan.low_angle;
   const size_t smem = smem_bytes(plan, e.ppl);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

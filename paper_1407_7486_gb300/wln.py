@@ -44,6 +44,7 @@ SIGNATURES = {
     "wln_free_ensemble": ([_P, _P], ctypes.c_int),
     "wln_ensemble_info": ([_P, _P, _P, _P], ctypes.c_int),
     "wln_loops_copy": ([_P, _P, _P, _P], ctypes.c_int),
+    "wln_set_low_angle": ([_P, ctypes.c_int32], ctypes.c_int),
     "wln_philox_stream": ([_P, _U64, _I64, _I32, _I32, _P], ctypes.c_int),
     "wln_wilson_avg": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
     "wln_wilson_avg_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
@@ -252,6 +253,11 @@ class Context:
                    stages: int = 0, chain_blocks: int = 0):
         self._check(load().wln_set_tuning(self.handle, points_per_lane, warps, rows, stages,
                                           chain_blocks))
+
+    def set_low_angle(self, enable: bool = True):
+        """Whether later float walks may take the low-angle form of theta
+        where a block's segments all subtend at most pi/4 (same bits)."""
+        self._check(load().wln_set_low_angle(self.handle, 1 if enable else 0))
 
     @property
     def launch_count(self) -> int:

@@ -1,7 +1,9 @@
-"""The Wilson kernel's float arctangent (atan2_pos in csrc/wln_wilson.cu):
-the polynomial coefficients in the source, evaluated in float32 the way the
-kernel does, stay within 1.5 float ulps of the double-precision arctangent
-over every octant, and they match what gen_atan_poly.py derives."""
+"""The Wilson kernel's float arctangent (atan_unit and atan2_pos in
+csrc/wln_wilson.cu): the polynomial coefficients in the source, evaluated in
+float32 the way the kernel does, stay within 1.5 float ulps of the
+double-precision arctangent over every octant, and they match what
+gen_atan_poly.py derives.  The low-angle form (atan2_low, for 0 < y <= x) is
+the same quotient and polynomial, so it is covered by the first octant."""
 import os
 import re
 import subprocess
@@ -14,7 +16,7 @@ SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1407_7486_gb300", "cs
 
 def _coeffs():
     text = open(os.path.join(SRC, "wln_wilson.cu")).read()
-    body = text[text.index("float atan2_pos"):text.index("struct F32Comp")]
+    body = text[text.index("float atan_unit"):text.index("float atan2_pos")]
     q0 = float(re.search(r"float q = ([-0-9.e]+)f;", body).group(1))
     rest = [float(v) for v in re.findall(r"q = fmaf\(q, s, ([-0-9.e]+)f\);", body)]
     return [q0] + rest
