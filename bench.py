@@ -48,15 +48,19 @@ N_ALG_FP32_LEVELS = 18 + 17 + 11 / 3 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 # Where every segment of a block subtends at most pi/4 at the axis the kernel
 # takes the arctangent's low form, which needs neither the range fold (2) nor
-# the octant unfolding (4): 6 operations fewer per (segment, point).
+# the octant unfolding (4): 6 operations fewer per (segment, point); below
+# tan(theta) = 0.05 also three terms of the series instead of the degree-7
+# polynomial (2 instead of 8): 6 fewer again.
 N_ALG_LOW_SAVED = 6
+N_ALG_TINY_SAVED = 6
 
 
-def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float) -> float:
-    """Fraction of the flux-tube segment evaluations of one pass that the
-    kernel walks with the low form of the arctangent: the same float32 test
-    per (tile of P radii at one T, block of 32 loops) that the kernel makes
-    from the block's longest segment and largest |y| (accounting only)."""
+def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float):
+    """Fractions of the flux-tube segment evaluations of one pass that the
+    kernel walks with the low form of the arctangent, and with its short
+    series: the same float32 tests per (tile of P radii at one T, block of 32
+    loops) that the kernel makes from the block's longest segment and largest
+    |y| (accounting only).  Returns (low, short), short a part of low."""
     f = np.float32
     n_loops = y32.shape[0]
     n_blocks = (n_loops + 31) // 32
@@ -67,7 +71,7 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
     dm = np.concatenate([d, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
     rm = np.concatenate([r, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
     in_block = np.minimum(32, n_loops - 32 * np.arange(n_blocks)).astype(np.float64)
-    low = tot = 0.0
+    low = tiny = tot = 0.0
     for prof, rho, T in zip(profiles, rhos, Ts):
         if prof.kind != I.PROFILE_FLUX_TUBE:
             continue
@@ -79,11 +83,17 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
             a2 = f(2.0 * span * np.sqrt(t))
             sT = f(np.sqrt(t))
             gap = np.maximum(f(0.0), rmin[:, None] - sT * rm[None, :])
-            ok = a2 * dm[None, :] <= f(0.9) * np.sqrt(f(prof.lam * prof.lam) + gap * gap)
+            lhs = a2 * dm[None, :]
+            rhs = np.sqrt(f(prof.lam * prof.lam) + gap * gap)
             w = nval[:, None] * in_block[None, :]
-            low += float((ok * w).sum())
+            low += float(((lhs <= f(0.9) * rhs) * w).sum())
+            tiny += float(((lhs <= f(0.09) * rhs) * w).sum())
             tot += float(w.sum())
-    return low / tot if tot else 0.0
+    return (low / tot, tiny / tot) if tot else (0.0, 0.0)
+
+
+def _n_alg(base: float, fr) -> float:
+    return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_TINY_SAVED * fr[1]
 
 
 def _workload(name: str) -> I.Workload:
@@ -596,13 +606,13 @@ def main():
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
     seg = wl.segment_evals
     n_alg = N_ALG_FP32
-    f_low = 0.0
+    f_low = (0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 4, 1.0)
-        n_alg = N_ALG_FP32 - N_ALG_LOW_SAVED * f_low
+        n_alg = _n_alg(N_ALG_FP32, f_low)
     achieved = n_alg * seg / (wilson_ms / 1e3) / 1e12
     traffic = _ncu_traffic(f"wilson_kernel_{args.workload}")
     line = {
@@ -621,9 +631,10 @@ def main():
                      "kernel_ms": wilson_ms,
                      "segment_evals_per_s": seg / (wilson_ms / 1e3),
                      "n_alg_fp32_per_segment": n_alg, "n_alg_mufu_per_segment": N_ALG_MUFU,
-                     "low_angle_fraction": f_low,
+                     "low_angle_fraction": f_low[0], "short_series_fraction": f_low[1],
                      "n_alg_basis": f"{N_ALG_FP32:g} per (segment, point), "
-                                    f"{N_ALG_LOW_SAVED} fewer on the low-angle form",
+                                    f"{N_ALG_LOW_SAVED} fewer on the low-angle form, "
+                                    f"{N_ALG_TINY_SAVED} fewer again on its short series",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"},
         "e2e": {"value": loop_points * ws / e2e_s, "unit": "loop-point evals/s",
@@ -753,10 +764,11 @@ def run_batched(args, wl: I.Workload):
     y32, _ = ctx.loops_copy(ens)
     if args.prec == "fp32":
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, b.P, 1.0)
-        n_alg = N_ALG_FP32 - N_ALG_LOW_SAVED * f_low
+        n_alg = _n_alg(N_ALG_FP32, f_low)
         ach = n_alg * wl.segment_evals / (ms / 1e3) / 1e12
         line["roofline"].update({"achieved": ach, "frac": ach / line["roofline"]["peak"],
-                                 "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low})
+                                 "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
+                                 "short_series_fraction": f_low[1]})
     line["gpu_error_vs_oracle_sampled"] = sampled_oracle_error(
         y32, wl.profiles, wl.rho, wl.T, S2, wl.n_groups)
     line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
@@ -827,14 +839,16 @@ def run_levels(args, wl: I.Workload):
     # paper's levels: circle N/2 + square N/4 + triangle N/4 = N segments per
     # loop and point; nested levels: N + N/2 + N/4
     seg = wl.segment_evals * (1.75 if args.nested else 1.0)
-    n_alg, f_low = N_ALG_FP32_LEVELS, 0.0
+    n_alg, f_low = N_ALG_FP32_LEVELS, (0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         # sub-loop segments join points up to 4 apart
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 3, 4.0)
-        n_alg = N_ALG_FP32_LEVELS - N_ALG_LOW_SAVED * f_low
+        if args.nested:     # the nested pass takes the low form but not the short series
+            f_low = (f_low[0], 0.0)
+        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation"
                         + (", nested loops)" if args.nested else ")"),
@@ -850,7 +864,8 @@ def run_levels(args, wl: I.Workload):
                         "kernel": "wilson_kernel<F32Comp,3,4,%s>" % ("nested" if args.nested else "levels"),
                         "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
-                        "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low,
+                        "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
+                        "short_series_fraction": f_low[1],
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
@@ -957,13 +972,13 @@ def run_correlation(args, wl: I.Workload):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     seg = lp * wl.ppl
-    n_alg, f_low = N_ALG_FP32, 0.0
+    n_alg, f_low = N_ALG_FP32, (0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         f_low = low_angle_fraction(y32, prof, rho, T, 4, 1.0)
-        n_alg = N_ALG_FP32 - N_ALG_LOW_SAVED * f_low
+        n_alg = _n_alg(N_ALG_FP32, f_low)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (per-loop values + randomised groups + Eq. corrcoef)",
                         lp / (ms / 1e3), "loop-point evals/s", args.steps, args.warmup, ms,
@@ -977,7 +992,8 @@ def run_correlation(args, wl: I.Workload):
                         "traffic": _ncu_traffic(f"wilson_loops_{args.workload}"),
                         "kernel": "wilson_kernel<F32Comp,4,4,loops>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
-                        "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low,
+                        "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
+                        "short_series_fraction": f_low[1],
                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": lp / e2e_s, "unit": "loop-point evals/s", "h2d_bytes_per_step":

@@ -497,16 +497,20 @@ wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, 
 
 /*
  * The float walks evaluate theta = atan2(sqrt(D), Q0 + B) (the angle a
- * segment subtends at the field axis, Sec. "Wilson Loop", Eqs. rhoi-Ci) in a
- * cheaper form where every segment of a 32-loop block is known to subtend at
- * most pi/4: 2 |d| <= sqrt(lambda^2 + (rho_cm - sqrt(T) |y|max)_+^2) with a
- * margin, |d| the block's longest scaled segment (times 4 for the sub-loops
- * of the discretisation levels).  Both forms give the same angle bit for bit
- * there.  enable = 0 makes later launches on this context use the general
- * form everywhere (for checking that equality); 1 (the default) restores the
- * choice.  Any other value: WLN_EINVAL.
+ * segment subtends at the field axis, Sec. "Wilson Loop", Eqs. rhoi-Ci) in
+ * cheaper forms where every segment of a 32-loop block is known to subtend a
+ * small angle.  With u = |d| / sqrt(lambda^2 + (rho_cm - sqrt(T) |y|max)_+^2),
+ * |d| the block's longest scaled segment (times 4 for the sub-loops of the
+ * discretisation levels), theta <= atan(u / (1 - u)):
+ *   level 1: blocks with u <= 0.45 (theta <= pi/4) skip the arctangent's
+ *            range fold and octant unfolding -- the same angle bit for bit;
+ *   level 2: blocks with u <= 0.045 (tan theta < 0.05) also take three terms
+ *            of the series of atan (relative remainder below 2.2e-9, so the
+ *            angle moves by float rounding only).
+ * Later launches on this context use forms up to `level`: 0 = the general
+ * form everywhere, 1, or 2 (the default).  Any other value: WLN_EINVAL.
  */
-wln_status wln_set_low_angle(wln_ctx* ctx, int32_t enable);
+wln_status wln_set_low_angle(wln_ctx* ctx, int32_t level);
 
 /* -------------------------------------------------------- runtime: batches */
 

@@ -75,7 +75,6 @@ DeviceGuard::~DeviceGuard() {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 

@@ -106,7 +106,7 @@ struct WilsonPlan {
   int64_t n_items;    // n_chains * n_tile_groups
   int grid;           // persistent CTAs
   int mode;           // kModeSums, kModeLevels, kModeLoops or kModeNested
-  int low_angle;      // blocks whose segments all subtend <= pi/4 take the low form
+  int low_angle;      // highest cheaper form of theta a block may take (0, 1 or 2)
 };
 
 struct Scratch {
@@ -129,7 +129,7 @@ struct wln_ctx {
   cudaEvent_t staging_done = nullptr;
   // tuning overrides (0 = automatic)
   int tune_P = 0, tune_warps = 0, tune_rows = 0, tune_stages = 0, tune_chain = 0;
-  int low_angle = 1;    // float walks may take the low-angle form of theta
+  int low_angle = 2;    // highest cheaper form of theta the float walks may take
 };
 
 struct wln_ensemble {

@@ -81,10 +81,10 @@ cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* laun
 
 extern "C" {
 
-wln_status wln_set_low_angle(wln_ctx* ctx, int32_t enable) {
+wln_status wln_set_low_angle(wln_ctx* ctx, int32_t level) {
   if (!ctx) return WLN_EINVAL;
-  if (enable != 0 && enable != 1) return fail(ctx, WLN_EINVAL, "low_angle: enable must be 0 or 1");
-  ctx->low_angle = enable;
+  if (level < 0 || level > 2) return fail(ctx, WLN_EINVAL, "low_angle: level must be 0, 1 or 2");
+  ctx->low_angle = level;
   return WLN_OK;
 }
 

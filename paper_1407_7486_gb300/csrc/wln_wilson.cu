@@ -28,14 +28,18 @@
 // fixed order into per-(chain, group) partials; a second kernel sums the
 // partials of each group in chain order.
 //
-// Low-angle form: theta = atan2(sqrt(D), Q0 + B) is at most pi/4 whenever
-// 2 |d| <= sqrt(Q0) (D <= Q0 C and B >= -sqrt(Q0) |d|).  Every ensemble
-// carries, per 32-loop block, its longest segment and largest |y|; when they
-// guarantee this for every segment of the block at the warp's tile (T, rho,
-// lambda), the warp walks that block with the arctangent's low form, without
-// the range fold and the octant unfolding (6 of the 17 operations of theta),
-// and gets the same bits.  The choice is per block and the same on every
-// lane, so the walk has no branch per segment.
+// Low-angle forms: with u = |d| / sqrt(Q0), tan(theta) <= u / (1 - u)
+// (D <= Q0 C and B >= -sqrt(Q0) |d|).  Every ensemble carries, per 32-loop
+// block, its longest segment and largest |y|, which bound u for every
+// segment of the block at the warp's tile (T, rho, lambda).  For u <= 0.45
+// (theta <= pi/4) the warp walks the block with the arctangent's low form,
+// without the range fold and the octant unfolding (6 of the 17 operations of
+// theta; the same bits); for u <= 0.045 (tan(theta) < 0.05) with three terms
+// of its series instead of the degree-7 polynomial (6 fewer again; the angle
+// moves by rounding only).  The choice is per block and the same on every
+// lane, so the walk has no branch per segment: the row loop exists once per
+// form (twice for the nested levels, whose long loop pays more for a third
+// copy in instruction fetch than the series saves).
 //
 // Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
 // the same pass can instead walk the three interleaved sub-loops of every
@@ -164,16 +168,27 @@ __device__ __forceinline__ float atan2_low(float y, float x) {
   return atan_unit(y * rcp_approx(x));
 }
 
-// at2_low: the angle when every segment of a work item is known to subtend
-// at most pi/4 at the field axis (kLowAngle: the flavour has a cheaper form).
+// The angle when 0 < y <= 0.05 x: the Taylor series t - t^3/3 + t^5/5 of
+// atan t, whose remainder (below t^7/7) is under 2.2e-9 of atan t there.
+__device__ __forceinline__ float atan2_tiny(float y, float x) {
+  const float t = y * rcp_approx(x);
+  const float s = t * t;
+  return fmaf(t * s, fmaf(s, 0.2f, -0.333333343f), t);
+}
+
+// at2_form<1>: the angle when every segment of a block is known to subtend
+// at most pi/4 at the field axis; at2_form<2>: at most atan(0.05) (kLowAngle:
+// the flavour has these cheaper forms); at2_form<0> is the general angle.
 struct F32Comp {
   using F = float;
   static constexpr bool kCompensated = true;
   static constexpr bool kLowAngle = true;
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
-  __device__ static float at2(float y, float x) { return atan2_pos(y, x); }
-  __device__ static float at2_low(float y, float x) { return atan2_low(y, x); }
+  template <int FORM>
+  __device__ static float at2_form(float y, float x) {
+    return FORM == 2 ? atan2_tiny(y, x) : (FORM == 1 ? atan2_low(y, x) : atan2_pos(y, x));
+  }
 };
 struct F32Naive {
   using F = float;
@@ -181,8 +196,10 @@ struct F32Naive {
   static constexpr bool kLowAngle = true;
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
-  __device__ static float at2(float y, float x) { return atan2_pos(y, x); }
-  __device__ static float at2_low(float y, float x) { return atan2_low(y, x); }
+  template <int FORM>
+  __device__ static float at2_form(float y, float x) {
+    return FORM == 2 ? atan2_tiny(y, x) : (FORM == 1 ? atan2_low(y, x) : atan2_pos(y, x));
+  }
 };
 struct F64 {
   using F = double;
@@ -190,8 +207,8 @@ struct F64 {
   static constexpr bool kLowAngle = false;
   __device__ static double rcp(double x) { return 1.0 / x; }
   __device__ static double rsq(double x) { return rsqrt(x); }
-  __device__ static double at2(double y, double x) { return atan2(y, x); }
-  __device__ static double at2_low(double y, double x) { return atan2(y, x); }
+  template <int FORM>
+  __device__ static double at2_form(double y, double x) { return atan2(y, x); }
 };
 
 // Sum of segment terms: terms are added plainly into `part`, and every few
@@ -235,7 +252,7 @@ struct KParams {
   int* flag;
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
   const float2* stats;   // per block: longest segment, largest |y|
-  int32_t low_angle;     // 0: the general form of theta everywhere
+  int32_t low_angle;     // highest form of theta a block may take (0: general everywhere)
 };
 
 // Whether every segment of block b subtends at most pi/4 at the field axis
@@ -246,22 +263,27 @@ struct KParams {
 // times the unit loop's (up to span of them for a sub-loop), and a margin of
 // 0.9 keeps the float comparison of the two sides on the same side.  Every
 // lane computes the same answer from the same block statistics.
-// (In float: the margin is far above its rounding.)
+// The same bound gives t = tan(theta) <= u / (1 - u), u = |d| / sqrt(Q0);
+// for u <= 0.045, t < 0.05 and three terms of the series of atan t suffice.
+// Returns the form of theta for the block: 2, 1 or 0 (general).  (In float:
+// the margins are far above its rounding.)
 struct LowAngle {
   float two_span_sT, sT, rho_min, l2;
-  __device__ __forceinline__ bool block(const KParams& k, int b) const {
+  __device__ __forceinline__ int block(const KParams& k, int b) const {
     const float2 st = k.stats[b];
     const float gap = fmaxf(0.0f, rho_min - sT * st.y);
-    return two_span_sT * st.x <= 0.9f * sqrtf(l2 + gap * gap);
+    const float lhs = two_span_sT * st.x, rhs = sqrtf(l2 + gap * gap);
+    return lhs <= 0.09f * rhs ? 2 : (lhs <= 0.9f * rhs ? 1 : 0);
   }
 };
 
 // Per-lane walk of one loop for the P radii of a tile (flux tube).  CQ
 // carries Q at the current point so that theta = atan2(sqrt(D), Q0 + B)
 // (one multiply fewer per segment and radius, one register more per radius);
-// without it theta = atan2(C sqrt(D), D + B (B + C)).  step_<true> may be
-// used when every segment subtends at most pi/4 at the axis (the caller has
-// checked): theta then needs no octant unfolding.
+// without it theta = atan2(C sqrt(D), D + B (B + C)).  step_<1> may be used
+// when every segment subtends at most pi/4 at the axis, step_<2> when at most
+// atan(0.05) (the caller has checked): theta then needs no octant unfolding,
+// and in the second case only three terms of its series.
 template <class A, int P, bool CQ = true>
 struct Walk {
   using F = typename A::F;
@@ -290,9 +312,9 @@ struct Walk {
   }
 
   // Advance along the straight segment to unit-loop point (x1, y1).
-  __device__ __forceinline__ void step(F x1, F y1) { step_<false>(x1, y1); }
+  __device__ __forceinline__ void step(F x1, F y1) { step_<0>(x1, y1); }
 
-  template <bool LOW>
+  template <int FORM>
   __device__ __forceinline__ void step_(F x1, F y1) {
     const F dx = s * (x1 - ux), dy = s * (y1 - uy);
     const F C = fma(dx, dx, dy * dy);
@@ -314,7 +336,7 @@ struct Walk {
       // Q0 C = D + B^2 (Lagrange), so D + B (B + C) = C (Q0 + B).
       const F ya = CQ ? D * rsD : C * (D * rsD);
       const F xa = CQ ? q[p] + B : fma(B, BC, D);
-      const F theta = LOW ? A::at2_low(ya, xa) : A::at2(ya, xa);
+      const F theta = A::template at2_form<FORM>(ya, xa);
       const F J1 = theta * rsD;
       ph[p].add(X * J1);
       // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
@@ -354,8 +376,8 @@ struct WalkB {
 #pragma unroll
     for (int p = 0; p < P; ++p) { rx[p] = fma(s, x0, rho[p]); ph[p].zero(); }
   }
-  __device__ __forceinline__ void step(F x1, F y1) { step_<false>(x1, y1); }
-  template <bool LOW>
+  __device__ __forceinline__ void step(F x1, F y1) { step_<0>(x1, y1); }
+  template <int FORM>
   __device__ __forceinline__ void step_(F x1, F y1) {
     const F dx = s * (x1 - ux), dy = s * (y1 - uy);
     const F rydx = ry * dx;
@@ -532,6 +554,55 @@ __device__ __forceinline__ void level_terms(double ph, double sp, F2 tp, F2 st, 
 }
 
 // One work item for one warp: its tile against every loop of the chain.
+// The rows of one staged chunk from row r on, with theta in form FORM
+// (0: general, 1: at most pi/4, 2: at most atan(0.05)).
+// Whole loops: a row holds two consecutive points.
+template <int FORM, class WalkT>
+__device__ __forceinline__ void rows_plain(WalkT* w, const float4* rowp, int r, int n) {
+  for (; r < n; ++r) {
+    const float4 v = rowp[r * 32];
+    w[0].template step_<FORM>(v.x, v.y);
+    w[0].template step_<FORM>(v.z, v.w);
+    if ((r & 3) == 3) w[0].fold();   // every 8 segments
+  }
+}
+
+// Nested loops: rows in pairs hold points 4j .. 4j + 3; the full walk takes
+// all four, the even walk 4j and 4j + 2, the quarter walk 4j.
+template <int FORM, class WalkT>
+__device__ __forceinline__ void rows_nested(WalkT* w, const float4* rowp, int r, int n) {
+  for (; r < n; r += 2) {
+    const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+    w[0].template step_<FORM>(a.x, a.y);
+    w[0].template step_<FORM>(a.z, a.w);
+    w[0].template step_<FORM>(v.x, v.y);
+    w[0].template step_<FORM>(v.z, v.w);
+    w[1].template step_<FORM>(a.x, a.y);
+    w[1].template step_<FORM>(v.x, v.y);
+    w[2].template step_<FORM>(a.x, a.y);
+    if ((r & 3) == 2) {   // every 8 segments of the full walk
+      w[0].fold(); w[1].fold(); w[2].fold();
+    }
+  }
+}
+
+// The paper's sub-loops: row r even holds points 2r (circle) and 2r + 1 =
+// 1 mod 4 (square), row r + 1 holds 2r + 2 (circle) and 2r + 3 = 3 mod 4
+// (triangle).
+template <int FORM, class WalkT>
+__device__ __forceinline__ void rows_levels(WalkT* w, const float4* rowp, int r, int n) {
+  for (; r < n; r += 2) {
+    const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
+    w[0].template step_<FORM>(a.x, a.y);
+    w[1].template step_<FORM>(a.z, a.w);
+    w[0].template step_<FORM>(v.x, v.y);
+    w[2].template step_<FORM>(v.z, v.w);
+    if ((r & 7) == 6) {   // every 8 circle segments
+      w[0].fold(); w[1].fold(); w[2].fold();
+    }
+  }
+}
+
 // Per-lane W terms are added into the warp's shared-memory accumulators
 // acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
 // flush sums each row over the lanes in lane order and writes the partial
@@ -599,7 +670,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   for (int b = b0; b < b1; ++b) {
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
-    const bool low = la_ok && la.block(k, b);   // the same on every lane
+    const int form = la_ok ? min(la.block(k, b), k.low_angle) : 0;   // the same on every lane
     // first point of each walk, for the closing segments
     float fx[NW], fy[NW];
 #pragma unroll
@@ -625,22 +696,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[0].step(v.z, v.w);
             r = 1;
           }
-          // low: the same walk with the angle's low form (warp-uniform flag)
-          if (low) {
-            for (; r < pp.chunk_rows; ++r) {
-              const float4 v = rowp[r * 32];
-              w[0].template step_<true>(v.x, v.y);
-              w[0].template step_<true>(v.z, v.w);
-              if ((r & 3) == 3) w[0].fold();   // every 8 segments
-            }
-          } else {
-            for (; r < pp.chunk_rows; ++r) {
-              const float4 v = rowp[r * 32];
-              w[0].step(v.x, v.y);
-              w[0].step(v.z, v.w);
-              if ((r & 3) == 3) w[0].fold();   // every 8 segments
-            }
-          }
+          // the form of theta for this block is the same on every lane
+          if (form == 2) rows_plain<2>(w, rowp, r, pp.chunk_rows);
+          else if (form == 1) rows_plain<1>(w, rowp, r, pp.chunk_rows);
+          else rows_plain<0>(w, rowp, r, pp.chunk_rows);
         } else if constexpr (NEST) {
           // Rows in pairs hold points 4j .. 4j + 3: the full walk takes all
           // four, the even walk 4j and 4j + 2, the quarter walk 4j.  All three
@@ -659,35 +718,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(a.x, a.y);
             r = 2;
           }
-          if (low) {
-            for (; r < pp.chunk_rows; r += 2) {
-              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-              w[0].template step_<true>(a.x, a.y);
-              w[0].template step_<true>(a.z, a.w);
-              w[0].template step_<true>(v.x, v.y);
-              w[0].template step_<true>(v.z, v.w);
-              w[1].template step_<true>(a.x, a.y);
-              w[1].template step_<true>(v.x, v.y);
-              w[2].template step_<true>(a.x, a.y);
-              if ((r & 3) == 2) {   // every 8 segments of the full walk
-                w[0].fold(); w[1].fold(); w[2].fold();
-              }
-            }
-          } else {
-            for (; r < pp.chunk_rows; r += 2) {
-              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-              w[0].step(a.x, a.y);
-              w[0].step(a.z, a.w);
-              w[0].step(v.x, v.y);
-              w[0].step(v.z, v.w);
-              w[1].step(a.x, a.y);
-              w[1].step(v.x, v.y);
-              w[2].step(a.x, a.y);
-              if ((r & 3) == 2) {   // every 8 segments of the full walk
-                w[0].fold(); w[1].fold(); w[2].fold();
-              }
-            }
-          }
+          // two copies only: a third of this long loop costs more in
+          // instruction fetch than the short series saves
+          if (form >= 1) rows_nested<1>(w, rowp, r, pp.chunk_rows);
+          else rows_nested<0>(w, rowp, r, pp.chunk_rows);
         } else {
           // Rows come in pairs (chunk_rows is even): row r even holds points
           // 2r (circle) and 2r + 1 = 1 mod 4 (square), row r + 1 holds
@@ -702,29 +736,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(v.z, v.w);
             r = 2;
           }
-          if (low) {
-            for (; r < pp.chunk_rows; r += 2) {
-              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-              w[0].template step_<true>(a.x, a.y);
-              w[1].template step_<true>(a.z, a.w);
-              w[0].template step_<true>(v.x, v.y);
-              w[2].template step_<true>(v.z, v.w);
-              if ((r & 7) == 6) {   // every 8 circle segments
-                w[0].fold(); w[1].fold(); w[2].fold();
-              }
-            }
-          } else {
-            for (; r < pp.chunk_rows; r += 2) {
-              const float4 a = rowp[r * 32], v = rowp[(r + 1) * 32];
-              w[0].step(a.x, a.y);
-              w[1].step(a.z, a.w);
-              w[0].step(v.x, v.y);
-              w[2].step(v.z, v.w);
-              if ((r & 7) == 6) {   // every 8 circle segments
-                w[0].fold(); w[1].fold(); w[2].fold();
-              }
-            }
-          }
+          if (form == 2) rows_levels<2>(w, rowp, r, pp.chunk_rows);
+          else if (form == 1) rows_levels<1>(w, rowp, r, pp.chunk_rows);
+          else rows_levels<0>(w, rowp, r, pp.chunk_rows);
         }
       }
       __syncwarp();

@@ -254,10 +254,11 @@ class Context:
         self._check(load().wln_set_tuning(self.handle, points_per_lane, warps, rows, stages,
                                           chain_blocks))
 
-    def set_low_angle(self, enable: bool = True):
-        """Whether later float walks may take the low-angle form of theta
-        where a block's segments all subtend at most pi/4 (same bits)."""
-        self._check(load().wln_set_low_angle(self.handle, 1 if enable else 0))
+    def set_low_angle(self, level: int = 2):
+        """The cheaper forms of theta later float walks may take on blocks
+        whose segments all subtend small angles: 0 none, 1 without the
+        octant unfolding (same bits), 2 also the short series (default)."""
+        self._check(load().wln_set_low_angle(self.handle, int(level)))
 
     @property
     def launch_count(self) -> int:

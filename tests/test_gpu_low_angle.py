@@ -1,18 +1,24 @@
-"""The low-angle form of theta changes no bit.
+"""The cheaper forms of theta (wln_set_low_angle).
 
-Where every segment of a 32-loop block subtends at most pi/4 at the field
-axis, the float walks skip the arctangent's range fold and octant unfolding.
-On the grids below the smallest proper times certainly qualify (2 sqrt(T)
-|d|max ~ 0.02 against 0.9 lambda; |d|max ~ 0.3 for 512-point loops) and
-T = 50 at the axis certainly does not (~4), so a pass mixes both forms; its
-results must equal, bit for bit, those of the same pass with the low form
-switched off (wln_set_low_angle), in every mode and float precision.
+Where every segment of a 32-loop block subtends a small angle at the field
+axis, the float walks skip the arctangent's range fold and octant unfolding
+(level 1) and, below tan(theta) = 0.05, take three terms of its series
+(level 2, the default).  On the grids below the smallest proper times
+certainly qualify for both (u = sqrt(T) |d|max / lambda ~ 0.01 for 512-point
+loops, |d|max ~ 0.3) and T = 50 at the axis certainly does not (u ~ 2), so
+a pass mixes the forms.
+  * Level 1 gives the same angle bit for bit: every mode and float precision
+    equals the general form (level 0) exactly.
+  * Level 2 moves the angle by float rounding only: group sums and per-loop
+    values stay within the per-loop rounding bars of the parity tests.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1407_7486_gb300 import inputs as I
 from paper_1407_7486_gb300 import wln
+from test_gpu_parity import F32_REL, _bars, _compare
 
 pytestmark = pytest.mark.gpu
 
@@ -20,16 +26,18 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+N_LOOPS, PPL, G = 333, 512, 9       # ragged last block
+
 
 @pytest.fixture(scope="module")
 def setup():
     from paper_1407_7486_gb300 import build
     build.build()
     c = wln.Context(0)
-    ens = c.gen_loops(12, 333, 512)          # ragged last block
-    yield c, ens
+    y32 = oracle.gen_loops(12, N_LOOPS, PPL).astype(np.float32)
+    ens = c.ensemble_from_host(y32)
+    yield c, y32, ens
     ens.free()
-    c.set_low_angle(True)
     c.close()
 
 
@@ -38,29 +46,46 @@ RHOS = [I.lin_grid(0.0, 8.0, 23), I.lin_grid(0.0, 3.0, 9), np.zeros(1)]
 TS = [I.log_grid(1e-3, 50.0, 13), I.log_grid(1e-3, 20.0, 7), I.log_grid(0.01, 5.0, 4)]
 
 
+def _run(ctx, ens, mode, prec, level, profs=PROFS, rhos=RHOS, Ts=TS):
+    ctx.set_low_angle(level)
+    try:
+        if mode == "sums":
+            return ctx.wilson_avg(ens, profs, rhos, Ts, G, prec=prec, where="host")
+        if mode in ("levels", "nested"):
+            return ctx.wilson_levels(ens, profs, rhos, Ts, G, prec=prec, where="host",
+                                     nested=mode == "nested")
+        return ctx.wilson_loops(ens, profs, rhos, Ts, prec=prec, where="host")
+    finally:
+        ctx.set_low_angle(2)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp32_naive"])
 @pytest.mark.parametrize("mode", ["sums", "levels", "nested", "loops"])
-def test_low_angle_form_is_bitwise_neutral(setup, prec, mode):
-    ctx, ens = setup
-
-    def run():
-        if mode == "sums":
-            return ctx.wilson_avg(ens, PROFS, RHOS, TS, 9, prec=prec, where="host")
-        if mode in ("levels", "nested"):
-            return ctx.wilson_levels(ens, PROFS, RHOS, TS, 9, prec=prec, where="host",
-                                     nested=mode == "nested")
-        return ctx.wilson_loops(ens, PROFS, RHOS, TS, prec=prec, where="host")
-
-    ctx.set_low_angle(True)
-    a = run()
-    ctx.set_low_angle(False)
-    b = run()
-    ctx.set_low_angle(True)
+def test_level1_is_bitwise_neutral(setup, prec, mode):
+    ctx, _, ens = setup
+    a = _run(ctx, ens, mode, prec, 1)
+    b = _run(ctx, ens, mode, prec, 0)
     assert np.isfinite(a).any()
     assert np.array_equal(a, b, equal_nan=True)
 
 
-def test_low_angle_switch_rejects_other_values(setup):
-    ctx, _ = setup
+@pytest.mark.parametrize("mode", ["sums", "loops"])
+def test_level2_within_rounding_bars(setup, mode):
+    ctx, y32, ens = setup
+    prof, rho, T = PROFS[0], RHOS[0], TS[0]
+    a = _run(ctx, ens, mode, "fp32", 2, [prof], [rho], [T])
+    b = _run(ctx, ens, mode, "fp32", 0, [prof], [rho], [T])
+    if mode == "sums":
+        _compare(a, b, N_LOOPS // G, _bars(y32, prof, rho, T, G, 1e-6, F32_REL), what="level 2")
+    else:
+        bars = _bars(y32, prof, rho, T, N_LOOPS, 1e-6, F32_REL)      # groups of one loop
+        for c in (0, 1):
+            assert np.all(np.abs(a[:, :, c] - b[:, :, c]) <= bars[c][0]), c
+
+
+def test_low_angle_rejects_other_levels(setup):
+    ctx, _, _ = setup
     from paper_1407_7486_gb300.wln import load
-    assert load().wln_set_low_angle(ctx.handle, 2) != 0
+    assert load().wln_set_low_angle(ctx.handle, 3) != 0
+    assert load().wln_set_low_angle(ctx.handle, -1) != 0
+    ctx.set_low_angle(2)
