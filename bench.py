@@ -49,10 +49,12 @@ N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 # Where every segment of a block subtends at most pi/4 at the axis the kernel
 # takes the arctangent's low form, which needs neither the range fold (2) nor
 # the octant unfolding (4): 6 operations fewer per (segment, point); below
-# tan(theta) = 0.05 also three terms of the series instead of the degree-7
-# polynomial (2 instead of 8): 6 fewer again.
+# tan(theta) = 0.05 it takes int dt/Q = r (1 - t^2/3 + t^4/5), r = 1/(Q0 + B),
+# t^2 = D r^2, instead of sqrt(D) (1), the quotient (1), the degree-7
+# polynomial (8 + 1) and theta/sqrt(D), and 1/D instead of (1/sqrt(D))^2 (1):
+# 9 fewer again.
 N_ALG_LOW_SAVED = 6
-N_ALG_TINY_SAVED = 6
+N_ALG_TINY_SAVED = 9
 
 
 def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float):

@@ -34,9 +34,10 @@
 // segment of the block at the warp's tile (T, rho, lambda).  For u <= 0.45
 // (theta <= pi/4) the warp walks the block with the arctangent's low form,
 // without the range fold and the octant unfolding (6 of the 17 operations of
-// theta; the same bits); for u <= 0.045 (tan(theta) < 0.05) with three terms
-// of its series instead of the degree-7 polynomial (6 fewer again; the angle
-// moves by rounding only).  The choice is per block and the same on every
+// theta; the same bits); for u <= 0.045 (tan(theta) < 0.05) it takes
+// int dt/Q = theta / sqrt(D) from three terms of the series of atan(t)/t,
+// without 1/sqrt(D) (the spin then takes 1/D; the result moves by rounding
+// only).  The choice is per block and the same on every
 // lane, so the walk has no branch per segment: the row loop exists once per
 // form (twice for the nested levels, whose long loop pays more for a third
 // copy in instruction fetch than the series saves).
@@ -170,6 +171,8 @@ __device__ __forceinline__ float atan2_low(float y, float x) {
 
 // The angle when 0 < y <= 0.05 x: the Taylor series t - t^3/3 + t^5/5 of
 // atan t, whose remainder (below t^7/7) is under 2.2e-9 of atan t there.
+// (The walk's short-series form uses the same series for theta / sqrt(D)
+// directly; this one serves walks that do not carry Q.)
 __device__ __forceinline__ float atan2_tiny(float y, float x) {
   const float t = y * rcp_approx(x);
   const float s = t * t;
@@ -330,19 +333,31 @@ struct Walk {
       const F B = fma(rx[p], dx, rydy);
       const F X = fma(rx[p], dy, -rydx);
       const F D = fma(X, X, l2C);
-      const F rsD = A::rsq(D);
       const F BC = B + C;
-      // atan2(C sqrt(D), D + B (B + C)) with the common factor C removed:
-      // Q0 C = D + B^2 (Lagrange), so D + B (B + C) = C (Q0 + B).
-      const F ya = CQ ? D * rsD : C * (D * rsD);
-      const F xa = CQ ? q[p] + B : fma(B, BC, D);
-      const F theta = A::template at2_form<FORM>(ya, xa);
-      const F J1 = theta * rsD;
-      ph[p].add(X * J1);
-      // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
-      // cancellation between the two quotients.
-      const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
-      sp[p].add(br * (rsD * rsD));
+      if constexpr (FORM == 2 && CQ) {
+        // tan(theta) = t < 0.05 with t^2 = D r^2, r = 1/(Q0 + B): int dt/Q =
+        // theta / sqrt(D) = r atan(t) / t = r (1 - t^2/3 + t^4/5), without
+        // 1/sqrt(D); the spin takes 1/D instead.
+        const F r = A::rcp(q[p] + B);
+        const F t2 = D * (r * r);
+        const F J1 = r * fma(t2, fma(t2, F(0.2), F(-0.333333343)), F(1));
+        ph[p].add(X * J1);
+        const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
+        sp[p].add(br * A::rcp(D));
+      } else {
+        const F rsD = A::rsq(D);
+        // atan2(C sqrt(D), D + B (B + C)) with the common factor C removed:
+        // Q0 C = D + B^2 (Lagrange), so D + B (B + C) = C (Q0 + B).
+        const F ya = CQ ? D * rsD : C * (D * rsD);
+        const F xa = CQ ? q[p] + B : fma(B, BC, D);
+        const F theta = A::template at2_form<FORM>(ya, xa);
+        const F J1 = theta * rsD;
+        ph[p].add(X * J1);
+        // (C + B)/Q1 - B/Q0 = (D - B (B + C)) / (Q0 Q1), free of the
+        // cancellation between the two quotients.
+        const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
+        sp[p].add(br * (rsD * rsD));
+      }
       rx[p] = rx1;
       if (CQ) q[p] = q1;
       rq[p] = rq1;
