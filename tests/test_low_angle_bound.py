@@ -1,0 +1,98 @@
+"""The bound behind the Wilson kernel's low-angle forms, checked on the CPU.
+
+For a segment from r to r + d and Q(t) = lambda^2 + |r + t d|^2, the angle
+theta = atan2(sqrt(D), Q0 + B) (B = r.d, D = lambda^2 |d|^2 + (r x d)^2)
+obeys tan(theta) <= u / (1 - u) with u = |d| / sqrt(Q0): sqrt(D) <=
+sqrt(Q0) |d| (Lagrange) and Q0 + B >= Q0 - sqrt(Q0) |d|.  The kernel takes the
+low form (no octant unfolding) for 2u <= 0.9 and the short series for
+2u <= 0.09, with u bounded per block through |d| <= sqrt(T) |d|max and
+Q0 >= lambda^2 + (rho - sqrt(T) |y|max)_+^2.  Checked here:
+  * the bound itself, by brute force over random and adversarial segments
+    (short and long, near and across the axis, thin and wide tubes);
+  * that the two thresholds give theta <= pi/4 and tan(theta) < 0.05;
+  * the remainder of the series 1 - t^2/3 + t^4/5 of atan(t)/t below t^6/7;
+  * the per-block reading of u on a real ensemble against every segment's u;
+  * the bench's accounting of the forms at the extremes (all or nothing).
+"""
+import numpy as np
+
+import oracle
+from paper_1407_7486_gb300 import inputs as I
+
+
+def _theta_u(r, d, lam):
+    B = np.sum(r * d, axis=-1)
+    X = r[..., 0] * d[..., 1] - r[..., 1] * d[..., 0]
+    C = np.sum(d * d, axis=-1)
+    D = lam * lam * C + X * X
+    Q0 = lam * lam + np.sum(r * r, axis=-1)
+    theta = np.arctan2(np.sqrt(D), Q0 + B)
+    u = np.sqrt(C / Q0)
+    return theta, u
+
+
+def test_tan_theta_bound_brute_force():
+    rng = np.random.default_rng(5)
+    n = 400000
+    for lam in (1e-3, 0.1, 1.0, 10.0):
+        r = rng.normal(size=(n, 2)) * 10.0 ** rng.uniform(-3, 1, size=(n, 1))
+        d = rng.normal(size=(n, 2)) * 10.0 ** rng.uniform(-4, 1, size=(n, 1))
+        # adversarial: segments pointing straight at the axis
+        d[: n // 4] = -r[: n // 4] * rng.uniform(0.0, 0.9, size=(n // 4, 1))
+        theta, u = _theta_u(r, d, lam)
+        ok = u < 1.0
+        assert np.all(np.tan(theta[ok]) <= u[ok] / (1.0 - u[ok]) * (1 + 1e-12) + 1e-300)
+
+
+def test_thresholds_give_the_forms():
+    rng = np.random.default_rng(6)
+    n = 400000
+    r = rng.normal(size=(n, 2)) * 10.0 ** rng.uniform(-2, 1, size=(n, 1))
+    d = rng.normal(size=(n, 2))
+    d *= (10.0 ** rng.uniform(-3, 0, size=(n, 1))) / np.linalg.norm(d, axis=1, keepdims=True)
+    theta, u = _theta_u(r, d, 0.7)
+    low, short = 2 * u <= 0.9, 2 * u <= 0.09
+    assert low.any() and short.any() and (~low).any()
+    assert np.all(theta[low] <= np.pi / 4)
+    assert np.all(np.tan(theta[short]) < 0.05)
+
+
+def test_series_remainder():
+    t = np.linspace(1e-6, 0.05, 20001)
+    series = 1.0 - t * t / 3.0 + t ** 4 / 5.0
+    # an alternating series: the remainder is below the first omitted term
+    # (plus the double rounding of both sides, a few ulps of 1)
+    assert np.all(np.abs(np.arctan(t) / t - series) <= t ** 6 / 7.0 + 1e-15)
+    assert (0.05 ** 6) / 7.0 < 2.3e-9
+
+
+def test_block_bound_covers_every_segment():
+    y = oracle.gen_loops(3, 96, 256)                       # 3 blocks of 32 loops
+    d = np.roll(y, -1, axis=2) - y
+    seg = np.sqrt(np.sum(d * d, axis=1))                   # [loop][segment]
+    rad = np.sqrt(np.sum(y * y, axis=1))
+    lam = 0.5
+    for T in (1e-3, 0.3, 4.0):
+        for rho in (0.0, 1.0, 6.0):
+            for b in range(3):
+                sl = slice(32 * b, 32 * b + 32)
+                dm, rm = seg[sl].max(), rad[sl].max()
+                gap = max(0.0, rho - np.sqrt(T) * rm)
+                u_block = np.sqrt(T) * dm / np.sqrt(lam * lam + gap * gap)
+                r = np.stack([rho + np.sqrt(T) * y[sl, 0], np.sqrt(T) * y[sl, 1]], axis=-1)
+                dd = np.sqrt(T) * np.stack([d[sl, 0], d[sl, 1]], axis=-1)
+                _, u = _theta_u(r, dd, lam)
+                assert np.all(u <= u_block * (1 + 1e-12))
+
+
+def test_accounting_extremes():
+    import bench
+    y32 = oracle.gen_loops(4, 64, 128).astype(np.float32)
+    prof = I.Profile(I.PROFILE_FLUX_TUBE, F=10.0, lam=1.0)
+    rho = I.lin_grid(0.0, 3.0, 7)
+    low, short = bench.low_angle_fraction(y32, [prof], [rho], [np.array([1e-8])], 4, 1.0)
+    assert low == 1.0 and short == 1.0
+    low, short = bench.low_angle_fraction(y32, [prof], [np.zeros(1)], [np.array([1e4])], 4, 1.0)
+    assert low == 0.0 and short == 0.0
+    const = I.Profile(I.PROFILE_CONST_B, B=1.0)
+    assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0)
