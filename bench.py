@@ -637,6 +637,12 @@ def main():
                      "n_alg_basis": f"{N_ALG_FP32:g} per (segment, point), "
                                     f"{N_ALG_LOW_SAVED} fewer on the low-angle form, "
                                     f"{N_ALG_TINY_SAVED} fewer again on its short series",
+                     # context only: the same launch counted as if every segment
+                     # took the general form (the rate of segment evaluations in
+                     # units of the general formula's operations)
+                     "general_form_equivalent": {
+                         "achieved": N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12,
+                         "frac": N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12 / peak_ops},
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"},
         "e2e": {"value": loop_points * ws / e2e_s, "unit": "loop-point evals/s",
