@@ -629,7 +629,7 @@ def main():
                    "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                      "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "wilson_kernel<F32Comp,4,4>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
+                     "kernel": "wilson_kernel<F32Comp,4,8>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
                      "kernel_ms": wilson_ms,
                      "segment_evals_per_s": seg / (wilson_ms / 1e3),
                      "n_alg_fp32_per_segment": n_alg, "n_alg_mufu_per_segment": N_ALG_MUFU,

@@ -484,10 +484,11 @@ wln_status wln_effective_action_full(wln_ctx* ctx, const wln_profile* profiles,
 /*
  * Work decomposition of later Wilson launches on this context (0 = automatic):
  * points_per_lane (radii held by one lane) and warps per CTA, one of the
- * shapes (2, 8), (4, 4), (4, 8), (8, 8) (automatic: (4, 4), three CTAs per
- * SM), rows (float4 rows of loop data per staged chunk, a power of two),
- * stages (chunks in flight, 2..8) and chain_blocks (consecutive 32-loop
- * blocks per work item).  The paper has no counterpart (its kernel used one
+ * shapes (2, 8), (4, 4), (4, 8), (8, 8) (automatic: (4, 8), two CTAs per
+ * SM, with 64 rows and 2 stages), rows (float4 rows of loop data per staged
+ * chunk, a power of two), stages (chunks in flight, 2..8) and chain_blocks
+ * (consecutive 32-loop blocks per work item).  The paper has no counterpart
+ * (its kernel used one
  * thread per loop and one launch per point); the autotuner sets these.  The
  * FP64 path, the discretisation levels and the per-loop values keep their
  * own shapes.

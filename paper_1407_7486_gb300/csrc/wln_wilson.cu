@@ -1002,11 +1002,15 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   p.low_angle = ctx->low_angle;
   const bool f64 = prec == WLN_PREC_FP64;
   const bool fixed = f64 || mode != kModeSums;   // shapes that ignore the tuning
-  // (4, 4): 3 CTAs per SM; levels (3, 4): 2 CTAs per SM
-  const int def_warps = (level_mode(mode) || p.P == 4) ? 4 : 8;
+  // Group sums: 4 radii x 8 warps, 2 CTAs per SM, 64-row chunks, 2 stages
+  // (537 ms on the paper workload against 560 ms for 4 x 4 warps, 3 CTAs per
+  // SM, 32 rows, 3 stages, once the low-angle forms made the walk lighter).
+  // Per-loop values keep (4, 4); the levels (3, 4), 2 CTAs per SM.
+  const bool wide = !fixed && p.P == 4;
+  const int def_warps = (level_mode(mode) || (p.P == 4 && !wide)) ? 4 : 8;
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
-  p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : 32;
-  p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : 3;
+  p.rows = (!fixed && ctx->tune_rows) ? ctx->tune_rows : (wide ? 64 : 32);
+  p.stages = (!fixed && ctx->tune_stages) ? ctx->tune_stages : (wide ? 2 : 3);
   p.n_tiles = n_tiles;
   p.n_tile_groups = (n_tiles + p.warps - 1) / p.warps;
   if (ctx->tune_chain && !fixed) {
