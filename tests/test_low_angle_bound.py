@@ -96,3 +96,32 @@ def test_accounting_extremes():
     assert low == 0.0 and short == 0.0
     const = I.Profile(I.PROFILE_CONST_B, B=1.0)
     assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0)
+
+
+def test_short_series_form_of_int_dt_over_q():
+    """The kernel's short-series form: int_0^1 dt/Q = theta / sqrt(D) =
+    r (1 - t^2/3 + t^4/5), r = 1/(Q0 + B), t^2 = D r^2, on segments with
+    2u <= 0.09 -- checked against the closed form and against a 400-point
+    Gauss-Legendre rule of the integral itself."""
+    rng = np.random.default_rng(8)
+    n = 20000
+    lam = 0.8
+    r = rng.normal(size=(n, 2)) * 3.0
+    d = rng.normal(size=(n, 2))
+    Q0 = lam * lam + np.sum(r * r, axis=1)
+    d *= (0.045 * np.sqrt(Q0) * rng.uniform(0.01, 1.0, size=n) / np.linalg.norm(d, axis=1))[:, None]
+    theta, u = _theta_u(r, d, lam)
+    assert np.all(2 * u <= 0.09 * (1 + 1e-12))
+    B = np.sum(r * d, axis=1)
+    X = r[:, 0] * d[:, 1] - r[:, 1] * d[:, 0]
+    D = lam * lam * np.sum(d * d, axis=1) + X * X
+    rr = 1.0 / (Q0 + B)
+    t2 = D * rr * rr
+    series = rr * (1.0 - t2 / 3.0 + t2 * t2 / 5.0)
+    closed = theta / np.sqrt(D)
+    assert np.all(np.abs(series - closed) <= 2.3e-9 * closed + 1e-15 * closed)
+    x, w = np.polynomial.legendre.leggauss(400)
+    tq = 0.5 * (x + 1.0)
+    Q = lam * lam + np.sum((r[:, None, :] + tq[None, :, None] * d[:, None, :]) ** 2, axis=2)
+    quad = 0.5 * np.sum(w[None, :] / Q, axis=1)
+    assert np.all(np.abs(series - quad) <= 2.3e-9 * quad + 1e-14 * quad)
