@@ -556,8 +556,9 @@ wln_status wln_batch_free(wln_ctx* ctx, wln_batch* batch);
  * proper times.  Its working memory (partial sums, results) comes from a
  * device arena of arena_bytes owned by the server; requests are admitted in
  * arrival order as arena space frees up.  Each wln_server_step launches one
- * Wilson kernel over up to tile_groups_per_step tile groups (8 tiles of 4
- * radii each), taken from the oldest admitted requests first, so work of
+ * Wilson kernel over up to tile_groups_per_step tile groups (one tile per
+ * warp of a CTA: by default 8 tiles of 4 radii each), taken from the oldest
+ * admitted requests first, so work of
  * several requests shares a launch; at most two steps are in flight.  When
  * all of a request's tile groups are done, its group sums, statistics and
  * effective action are computed on a second stream and copied to pinned host
