@@ -235,11 +235,20 @@ wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
  * than 64 MiB returns WLN_EINVAL with the size it needed: the partial sums take
  * (chains + n_groups) * n_points * WLN_K * 8 bytes.
  * The first call on a device looks up the array's device address (and may load
- * the library's device code); make that first call before any CUDA stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * every word a call reads is written by that call first, so nothing needs
- * clearing, but calls whose GPU work overlaps in time (other streams, other
- * threads) race on it and must be serialised by the caller.
+ * the library's device code).  The call must not be made inside a CUDA stream
+ * capture: it copies its inputs from host memory and, for a host output,
+ * synchronises the stream.  All calls share the array and it keeps the last
+ * call's contents: every word a call reads is written by that call first, so
+ * nothing needs clearing, but calls whose GPU work overlaps in time (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ *
+ * Inputs (profiles, grids, offsets) may be reused as soon as the call returns:
+ * pageable host inputs are staged by the copy itself, and when any input is
+ * page-locked the call waits until the stream has read it.  Errors of a
+ * bounded device wait: with a host output the call waits for the stream and
+ * returns WLN_ETIMEOUT (and clears the device flag, so later calls start
+ * clean); with a device output the flag is read by the next synchronising
+ * call, as for wln_wilson_avg.
  */
 wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* ens,
                                   const wln_profile* profiles, int32_t n_profiles,

@@ -73,6 +73,23 @@ DeviceGuard::~DeviceGuard() {
   if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
 }
 
+// Reads (and clears) the device error flag after the stream's work is done.
+wln_status check_flag(wln_ctx* ctx) {
+  int h = 0;
+  cudaError_t err = cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "synchronize");
+  if (h != 0) {
+    cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, WLN_ETIMEOUT,
+                h == kErrTimeoutFull    ? "a staged-copy wait ran out (device)"
+                : h == kErrTimeoutEmpty ? "a buffer-release wait ran out (device)"
+                                        : "the self-test wait ran out (device), as intended");
+  }
+  return WLN_OK;
+}
+
 namespace {
 
 
@@ -92,22 +109,6 @@ struct Carve {
 template <class T>
 T* at(void* base, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(base) + off);
-}
-
-wln_status check_flag(wln_ctx* ctx) {
-  int h = 0;
-  cudaError_t err = cudaMemcpyAsync(&h, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "synchronize");
-  if (h != 0) {
-    cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
-    return fail(ctx, WLN_ETIMEOUT,
-                h == kErrTimeoutFull    ? "a staged-copy wait ran out (device)"
-                : h == kErrTimeoutEmpty ? "a buffer-release wait ran out (device)"
-                                        : "the self-test wait ran out (device), as intended");
-  }
-  return WLN_OK;
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }

@@ -143,6 +143,9 @@ namespace wln {
 wln_status fail(wln_ctx* ctx, wln_status st, const std::string& msg);
 wln_status cuda_fail(wln_ctx* ctx, cudaError_t err, const char* what);
 bool is_device_ptr(const void* p);
+// Waits for the context's stream, then reads and clears the device error
+// flag: WLN_ETIMEOUT when a bounded device wait ran out since the last check.
+wln_status check_flag(wln_ctx* ctx);
 wln_status ensure_scratch(wln_ctx* ctx, size_t bytes);
 wln_status ensure_pinned(wln_ctx* ctx, size_t bytes);
 

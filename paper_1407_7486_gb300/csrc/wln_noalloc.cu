@@ -44,6 +44,15 @@ wln_status scratch_address(wln_ctx* ctx, void** out) {
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
+bool is_pinned_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 // Per-profile constants and tile / point offsets (one thread: few profiles).
 // Same formulas and tile order as the host-side batch of wln_wilson_avg.
 __global__ void noalloc_profiles_kernel(const wln_profile* prof, int32_t n_profiles,
@@ -115,31 +124,18 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
                                              const double* T, const int32_t* T_off,
                                              int32_t n_groups, wln_prec prec,
                                              double* group_sums) {
-  if (!ctx || !ens || !group_sums || !profiles || !rho_cm || !rho_off || !T || !T_off)
-    return fail(ctx, WLN_EINVAL, "null argument");
+  if (!ctx || !ens || !group_sums) return fail(ctx, WLN_EINVAL, "null argument");
   if (prec != WLN_PREC_FP64 && prec != WLN_PREC_FP32_COMP && prec != WLN_PREC_FP32_NAIVE)
     return fail(ctx, WLN_EINVAL, "unknown precision");
   if (ens->device != ctx->device) return fail(ctx, WLN_EINVAL, "ensemble lives on another device");
   if (n_groups < 2 || ens->e.n_loops % n_groups != 0)
     return fail(ctx, WLN_EINVAL, "n_groups must be >= 2 and divide n_loops");
-  if (n_profiles < 1 || rho_off[0] != 0 || T_off[0] != 0)
-    return fail(ctx, WLN_EINVAL, "profiles and offsets starting at 0 are required");
+  wln_status st = check_batch(ctx, profiles, n_profiles, rho_cm, rho_off, T, T_off);
+  if (st != WLN_OK) return st;
   const int P = plan_points_per_lane(ctx, prec);
   int64_t n_tiles = 0, n_points = 0;
   for (int q = 0; q < n_profiles; ++q) {
-    const wln_profile& pr = profiles[q];
-    if (pr.kind != WLN_PROFILE_FLUX_TUBE && pr.kind != WLN_PROFILE_CONST_B)
-      return fail(ctx, WLN_EINVAL, "unknown profile kind");
-    if (pr.kind == WLN_PROFILE_FLUX_TUBE && !(pr.lambda > 0.0 && std::isfinite(pr.lambda) && std::isfinite(pr.F)))
-      return fail(ctx, WLN_EINVAL, "flux tube needs finite F and lambda > 0");
-    if (pr.kind == WLN_PROFILE_CONST_B && !std::isfinite(pr.B))
-      return fail(ctx, WLN_EINVAL, "constant field needs finite B");
     const int nr = rho_off[q + 1] - rho_off[q], nt = T_off[q + 1] - T_off[q];
-    if (nr < 1 || nt < 1) return fail(ctx, WLN_EINVAL, "every profile needs at least one rho and one T");
-    for (int i = rho_off[q]; i < rho_off[q + 1]; ++i)
-      if (!(rho_cm[i] >= 0.0 && std::isfinite(rho_cm[i]))) return fail(ctx, WLN_EINVAL, "rho_cm must be finite and >= 0");
-    for (int i = T_off[q]; i < T_off[q + 1]; ++i)
-      if (!(T[i] > 0.0 && std::isfinite(T[i]))) return fail(ctx, WLN_EINVAL, "T must be finite and > 0");
     n_tiles += static_cast<int64_t>(nt) * ((nr + P - 1) / P);
     n_points += static_cast<int64_t>(nr) * nt;
   }
@@ -176,7 +172,7 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
   cudaGetDevice(&prev);
   if (prev != ctx->device) cudaSetDevice(ctx->device);
   void* base = nullptr;
-  wln_status st = scratch_address(ctx, &base);
+  st = scratch_address(ctx, &base);
   if (st != WLN_OK) {
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return st;
@@ -220,14 +216,29 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
     ++launches;
   }
   ctx->launches += launches;
-  int flag = 0;
-  if (err == cudaSuccess && host_out) {
+  // Inputs in page-locked host memory are read by the stream later, not
+  // during the copy call: wait until the stream has read them, so that the
+  // caller may reuse them on return (pageable inputs are staged by the copy
+  // call itself).  The context's staging event is recorded, not created.
+  bool pinned_inputs = false;
+  for (const void* q : {static_cast<const void*>(profiles), static_cast<const void*>(rho_off),
+                        static_cast<const void*>(T_off), static_cast<const void*>(rho_cm),
+                        static_cast<const void*>(T)})
+    pinned_inputs = pinned_inputs || is_pinned_host(q);
+  if (err == cudaSuccess && host_out)
     err = cudaMemcpyAsync(group_sums, out, out_bytes, cudaMemcpyDeviceToHost, s);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess && !host_out && pinned_inputs) {
+    err = cudaEventRecord(ctx->staging_done, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(ctx->staging_done);
   }
+  if (err != cudaSuccess) {
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return cuda_fail(ctx, err, "no-alloc Wilson group sums");
+  }
+  // A host output waits for the stream and reads (and clears) the device
+  // error flag, as wln_wilson_avg does; with a device output the flag is read
+  // by the next synchronising call (wln_synchronize).
+  st = host_out ? check_flag(ctx) : WLN_OK;
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "no-alloc Wilson group sums");
-  if (flag != 0) return fail(ctx, WLN_ETIMEOUT, "a bounded device-side wait ran out");
-  return WLN_OK;
+  return st;
 }

@@ -26,6 +26,7 @@ C_SCAL, C_FERM, C_SIN, C_SCAL_SQ, C_FERM_SQ = range(5)
 PREC = {"fp64": 0, "fp32": 1, "fp32_comp": 1, "fp32_naive": 2}
 STATUS = {0: "WLN_OK", 1: "WLN_EINVAL", 2: "WLN_ENOMEM", 3: "WLN_ECUDA",
           4: "WLN_ETIMEOUT", 5: "WLN_EBUSY"}
+WLN_OK, WLN_EINVAL, WLN_ENOMEM, WLN_ECUDA, WLN_ETIMEOUT, WLN_EBUSY = range(6)
 
 # Every entry point declared in include/wln.h, with its ctypes signature.
 _P, _I32, _I64, _U64, _D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,

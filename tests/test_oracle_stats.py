@@ -3,7 +3,10 @@
   * Grouped jackknife (Sec. "Grouping Worldlines"): brute-force delete-one
     group means on small G; the delete-one variance equals the squared group
     standard error for a mean (an algebraic identity); the covariance
-    diagonal is that square; group means reproduce the loop mean.
+    diagonal is that square; every off-diagonal entry equals the explicit
+    double sum over groups (brute force on G <= 4, and the closed form
+    (m_1(p) - m_2(p)) (m_1(q) - m_2(q)) / 4 at G = 2) and the delete-one
+    jackknife covariance; group means reproduce the loop mean.
   * Simpson's rule (Sec. "Computing an Effective Action"): exact on cubics
     for every point count, including the trailing 3/8 panel for even counts.
   * The effective-action quadrature (Eq. cylEA) of the locally constant
@@ -55,6 +58,46 @@ def test_covariance_diagonal_and_symmetry():
     assert np.allclose(np.diag(C), sem ** 2, rtol=1e-13)
     assert np.array_equal(C, C.T)
     assert np.all(np.linalg.eigvalsh(C) > -1e-15)
+
+
+@pytest.mark.parametrize("G", [2, 3, 4])
+def test_covariance_off_diagonal_brute_force(G):
+    """Each C(p, q), p != q, against the explicit double sum over groups of the
+    products of deviations from the ensemble mean, divided by G (G - 1), and
+    against the delete-one-group jackknife covariance (Sec. "Grouping
+    Worldlines"; a linear statistic, so the two agree exactly)."""
+    rng = np.random.default_rng(100 + G)
+    lpg, n_points = 3, 5
+    S, w = _fake_sums(rng, n_points, G, lpg)
+    S[:, :, 0] += rng.normal(size=(n_points, G)) * 0.7   # uneven group means
+    C = ost.covariance(S, lpg, 0)
+    assert C.shape == (n_points, n_points)
+    m = [[S[p, g, 0] / lpg for g in range(G)] for p in range(n_points)]
+    for p in range(n_points):
+        for q in range(n_points):
+            mp, mq = sum(m[p]) / G, sum(m[q]) / G
+            brute = sum((m[p][g] - mp) * (m[q][g] - mq) for g in range(G)) / (G * (G - 1))
+            assert C[p, q] == pytest.approx(brute, rel=1e-12, abs=1e-15)
+            loo_p = [(G * mp - m[p][g]) / (G - 1) for g in range(G)]
+            loo_q = [(G * mq - m[q][g]) / (G - 1) for g in range(G)]
+            jk = (G - 1) / G * sum((a - mp) * (b - mq) for a, b in zip(loo_p, loo_q))
+            assert C[p, q] == pytest.approx(jk, rel=1e-11, abs=1e-15)
+            if G == 2:
+                closed = (m[p][0] - m[p][1]) * (m[q][0] - m[q][1]) / 4
+                assert C[p, q] == pytest.approx(closed, rel=1e-12, abs=1e-15)
+    off = C[~np.eye(n_points, dtype=bool)]
+    assert np.any(np.abs(off) > 1e-3)   # the cross terms are exercised
+
+
+def test_covariance_hand_values():
+    """Three points, two groups of one loop each, values chosen by hand:
+    group means (1, 3), (2, 2), (0, -4) give deviations (-1, 1), (0, 0),
+    (2, -2); C(p, q) = sum_g dev_p dev_q / 2 = [[1, 0, -2], [0, 0, 0],
+    [-2, 0, 4]]."""
+    S = np.zeros((3, 2, 5))
+    S[:, :, 0] = [[1.0, 3.0], [2.0, 2.0], [0.0, -4.0]]
+    C = ost.covariance(S, 1, 0)
+    assert np.array_equal(C, np.array([[1.0, 0.0, -2.0], [0.0, 0.0, 0.0], [-2.0, 0.0, 4.0]]))
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8, 16, 17, 64, 128])

@@ -3,10 +3,16 @@
 Callers that cannot allocate device memory (their framework's allocator owns
 the device memory, or they must avoid cudaMalloc's implicit synchronisation)
 use this entry point; its working memory is a fixed array inside the
-library.  These checks call it through the C ABI twice in a row, on
-different problems, and compare each result with wln_wilson_avg at the
-FP32 parity bar of the other tests (1e-6 on a group mean of W - 1).  The
-file is collected last so that a run stopping at the first failure has
+library.  These checks call it through the C ABI:
+  * twice in a row, on different problems, and again on the first one after
+    the array held the second: each result equals wln_wilson_avg bit for bit
+    (the same kernels and the same work decomposition);
+  * on a fresh context, before any other Wilson call: the device's free
+    memory does not change across the call;
+  * after a bounded device wait has run out (the self-test wait): the next
+    calls return WLN_OK, so a timeout does not stick to the context;
+  * with a problem beyond the array: a clear error naming the size.
+The file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
 import numpy as np
@@ -21,7 +27,9 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-TOL = 1e-6   # FP32 bar on a group mean of W - 1 (see test_gpu_parity.py)
+FIRST = ([I.Profile(0, F=10.0, lam=1.0)], [I.lin_grid(0, 5, 13)], [I.log_grid(0.01, 10, 9)], 8)
+SECOND = ([I.Profile(0, F=50.0, lam=0.7), I.Profile(1, B=0.5)],
+          [I.lin_grid(0, 3, 6), np.zeros(1)], [I.log_grid(0.1, 5, 4), I.log_grid(0.1, 2, 3)], 5)
 
 
 @pytest.fixture(scope="module")
@@ -33,28 +41,47 @@ def ctx():
     c.close()
 
 
-def _check(a, b, lpg):
-    a = a.cpu().numpy() if hasattr(a, "cpu") else a
-    b = b.cpu().numpy() if hasattr(b, "cpu") else b
-    scale = np.maximum(1.0, np.abs(b) / lpg)
-    assert np.all(np.abs(a - b) / lpg <= TOL * scale)
+def _np(a):
+    return a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
 
 
 def test_noalloc_matches_wilson_avg_twice_in_a_row(ctx):
     ens = ctx.gen_loops(21, 640, 256)
-    first = ([I.Profile(0, F=10.0, lam=1.0)], [I.lin_grid(0, 5, 13)], [I.log_grid(0.01, 10, 9)], 8)
-    second = ([I.Profile(0, F=50.0, lam=0.7), I.Profile(1, B=0.5)],
-              [I.lin_grid(0, 3, 6), np.zeros(1)], [I.log_grid(0.1, 5, 4), I.log_grid(0.1, 2, 3)], 5)
-    for args, where in ((first, "device"), (second, "host")):
-        lpg = ens.n_loops // args[3]
+    for args, where in ((FIRST, "device"), (SECOND, "host")):
         ref = ctx.wilson_avg(ens, *args, prec="fp32", where=where)
         got = ctx.wilson_avg_noalloc(ens, *args, prec="fp32", where=where)
         torch.cuda.synchronize()
-        _check(got, ref, lpg)
+        assert np.array_equal(_np(got), _np(ref))
     # and the first problem again, after the array held the second one
-    ref = ctx.wilson_avg(ens, *first, prec="fp32", where="host")
-    got = ctx.wilson_avg_noalloc(ens, *first, prec="fp32", where="host")
-    _check(got, ref, ens.n_loops // first[3])
+    ref = ctx.wilson_avg(ens, *FIRST, prec="fp64", where="host")
+    got = ctx.wilson_avg_noalloc(ens, *FIRST, prec="fp64", where="host")
+    assert np.array_equal(got, ref)
+    ens.free()
+
+
+def test_noalloc_allocates_nothing(ctx):
+    ens = ctx.gen_loops(23, 320, 128)
+    ctx.wilson_avg_noalloc(ens, *FIRST, prec="fp32", where="host")   # array looked up
+    fresh = wln.Context(0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    a = fresh.wilson_avg_noalloc(ens, *SECOND, prec="fp32", where="host")
+    b = fresh.wilson_avg_noalloc(ens, *FIRST, prec="fp32", where="host")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory moved by {free0 - free1} bytes"
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    fresh.close()
+    ens.free()
+
+
+def test_noalloc_after_a_timed_out_wait(ctx):
+    ens = ctx.gen_loops(24, 320, 128)
+    assert ctx.selftest_wait(20) == wln.WLN_ETIMEOUT
+    ref = ctx.wilson_avg(ens, *FIRST, prec="fp32", where="host")
+    for _ in range(2):
+        got = ctx.wilson_avg_noalloc(ens, *FIRST, prec="fp32", where="host")
+        assert np.array_equal(got, ref)
     ens.free()
 
 
