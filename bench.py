@@ -33,8 +33,17 @@ sys.path.insert(0, ROOT)
 from paper_1407_7486_gb300 import inputs as I  # noqa: E402
 
 METRIC = "loop-point evals/s (Wilson loops, FP32-compensated, |d<W>| <= 1e-6)"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# FP64 FMA lanes per SM: GB300's double-precision pipe issues at 1/64 of the
+# FP32 rate (128 / 64 = 2 per SM and clock; 152 SMs x 2 x 2 flops x 2.07 GHz
+# = 1.26 TFLOP/s, the part's nominal FP64 figure).
+FP64_LANES_PER_SM = 2
+
+
+def sm_count(dev: int = 0) -> int:
+    """Streaming multiprocessors of the device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 # Algorithmic FP32 operations per (segment, point) of the compensated walk,
 # counted from the formulas in csrc/wln_wilson.cu (an FMA, a min/max or a
 # select each count 1): 18 per radius for the geometry, the closed-form
@@ -46,6 +55,9 @@ FP32_LANES_PER_SM = 128
 N_ALG_FP32 = 18 + 17 + 11 / 4 + 1
 N_ALG_FP32_LEVELS = 18 + 17 + 11 / 3 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
+# The FP64 comparison walk (2 radii per lane): the general form throughout,
+# the shared part over 2 radii, no compensated folds.
+N_ALG_FP64 = 18 + 17 + 11 / 2
 # Where every segment of a block subtends at most pi/4 at the axis the kernel
 # takes the arctangent's low form, which needs neither the range fold (2) nor
 # the octant unfolding (4): 6 operations fewer per (segment, point); below
@@ -586,7 +598,7 @@ def main():
     bufs = host_buffers(wl)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = args.steps
     h2d = d2h = 0
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
@@ -605,7 +617,7 @@ def main():
 
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
+    peak_ops = sm_count() * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
     seg = wl.segment_evals
     n_alg = N_ALG_FP32
     f_low = (0.0, 0.0)
@@ -643,7 +655,7 @@ def main():
                      "general_form_equivalent": {
                          "achieved": N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12,
                          "frac": N_ALG_FP32 * seg / (wilson_ms / 1e3) / 1e12 / peak_ops},
-                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                     "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"},
         "e2e": {"value": loop_points * ws / e2e_s, "unit": "loop-point evals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -681,9 +693,23 @@ def main():
         b.record(stream)
         stream.synchronize()
         n_lp = wl.n_loops * len(sub_rho[0]) * len(sub_T[0])
-        line["fp64_gpu"] = {"value": n_lp / (a.elapsed_time(b) / 1e3), "unit": "loop-point evals/s",
+        f64_s = a.elapsed_time(b) / 1e3
+        # the same algorithmic count as the float walk's general form, in FP64
+        # operations, against the FP64 pipe (the library's atan2, division and
+        # square root take more operations than counted, which shows as a
+        # lower fraction)
+        f64_peak = sm_count() * FP64_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+        f64_ach = N_ALG_FP64 * n_lp * wl.ppl / f64_s / 1e12
+        line["fp64_gpu"] = {"value": n_lp / f64_s, "unit": "loop-point evals/s",
                             "sample": f"F={wl.profiles[q].F}, {len(sub_rho[0])} rho x "
-                                      f"{len(sub_T[0])} T, all loops, Wilson kernel only"}
+                                      f"{len(sub_T[0])} T, all loops, Wilson kernel only",
+                            "roofline": {"bound": "fp64", "achieved": f64_ach, "peak": f64_peak,
+                                         "unit": "T FP64 op/s", "frac": f64_ach / f64_peak,
+                                         "n_alg_fp64_per_segment": N_ALG_FP64,
+                                         "peak_basis": f"{sm_count()} SMs x {FP64_LANES_PER_SM} "
+                                                       f"FP64 lanes x {sm_mhz:.0f} MHz"},
+                            # Wilson kernel rates, FP32 compensated over FP64
+                            "fp32_over_fp64_rate": (wl.loop_points / (wilson_ms / 1e3)) / (n_lp / f64_s)}
         ens.free()
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl, ctx)
@@ -742,7 +768,7 @@ def run_batched(args, wl: I.Workload):
     S, st, g = b.results()
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    peak_ops = sm_count() * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     seg = wl.segment_evals
     achieved = N_ALG_FP32 * seg / (ms / 1e3) / 1e12
     line = _common_line(METRIC, wl.loop_points / (ms / 1e3), "loop-point evals/s", args.steps,
@@ -843,7 +869,7 @@ def run_levels(args, wl: I.Workload):
     d2h = Lh.nbytes + Xh.nbytes
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    peak_ops = sm_count() * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     # paper's levels: circle N/2 + square N/4 + triangle N/4 = N segments per
     # loop and point; nested levels: N + N/2 + N/4
     seg = wl.segment_evals * (1.75 if args.nested else 1.0)
@@ -874,7 +900,7 @@ def run_levels(args, wl: I.Workload):
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
                         "short_series_fraction": f_low[1],
-                        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                        "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
@@ -978,7 +1004,7 @@ def run_correlation(args, wl: I.Workload):
     lp = wl.n_loops * n_points
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    peak_ops = sm_count() * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     seg = lp * wl.ppl
     n_alg, f_low = N_ALG_FP32, (0.0, 0.0)
     if args.prec == "fp32":
@@ -1002,7 +1028,7 @@ def run_correlation(args, wl: I.Workload):
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
                         "short_series_fraction": f_low[1],
-                        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                        "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": lp / e2e_s, "unit": "loop-point evals/s", "h2d_bytes_per_step":
                    int(sum(a.nbytes for a in rho + T)), "d2h_bytes_per_step": int(3 * n_points * 8)}

@@ -30,9 +30,8 @@ CANDIDATES = {"shape": ((2, 8), (4, 4), (4, 8), (8, 8)), "rows": (16, 32, 64),
               "stages": (2, 3, 4)}
 
 
-def _key(ens: "wln.Ensemble", prec: str) -> str:
-    import torch
-    return f"{torch.cuda.get_device_name()}|ppl={ens.ppl}|{prec}"
+def _key(device_name: str, ppl: int, prec: str) -> str:
+    return f"{device_name}|ppl={ppl}|{prec}"
 
 
 def _load_cache() -> Dict[str, dict]:
@@ -67,41 +66,64 @@ def _probe(profiles, rho, T, n_loops, ppl, seg_per_s, seconds):
     return P, R, TT, n
 
 
+def candidates():
+    """Every (P, warps, rows, stages) the search times, in a fixed order."""
+    return [(P, w, r, st) for (P, w), r, st in itertools.product(
+        CANDIDATES["shape"], CANDIDATES["rows"], CANDIDATES["stages"])]
+
+
+def _gpu_timer(ctx, ens, pr, r, t, n_groups, prec):
+    """Time one candidate (already set on ctx) with CUDA events: a warm-up run,
+    then the mean of two runs of the probe batch on the context's stream."""
+    import torch
+
+    def measure() -> float:
+        b = wln.Batch(ctx, ens, pr, r, t, n_groups, prec=prec)
+        try:
+            b.run(graph=False)                       # warm-up
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            for _ in range(2):
+                b.run(graph=False)
+            z.record(ctx.stream)
+            z.synchronize()
+            return a.elapsed_time(z) / 2
+        finally:
+            b.free()
+    return measure
+
+
 def tune(ctx: "wln.Context", ens: "wln.Ensemble", profiles: Sequence[Profile], rho, T,
          n_groups: int, prec: str = "fp32", probe_seconds: float = 0.05, use_cache: bool = True,
-         verbose: bool = False) -> dict:
+         verbose: bool = False, timer=None, device_name: str = None) -> dict:
     """Pick (P, warps, rows, stages) for this ensemble and precision; returns the choice
-    and the probe timings, and leaves it set on ctx."""
-    import torch
+    and the probe timings, and leaves it set on ctx.  `timer` (a function of no
+    arguments returning milliseconds for the candidate currently set on ctx)
+    replaces the CUDA-event timing of the probe; `device_name` the GPU's name in
+    the cache key."""
     if prec == "fp64":
         ctx.set_tuning()
         return {"P": 2, "warps": 4, "rows": 32, "stages": 3, "source": "fixed for fp64"}
-    key = _key(ens, prec)
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name()
+    key = _key(device_name, ens.ppl, prec)
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
             ctx.set_tuning(hit["P"], hit.get("warps", 8), hit["rows"], hit["stages"], 0)
             return dict(hit, source="cache")
     pr, r, t, n_pts = _probe(profiles, rho, T, ens.n_loops, ens.ppl, 7e11, probe_seconds)
-    stream = ctx.stream
+    if timer is None:
+        timer = _gpu_timer(ctx, ens, pr, r, t, n_groups, prec)
     results = []
     t0 = time.perf_counter()
-    for (P, warps), rows, stages in itertools.product(CANDIDATES["shape"], CANDIDATES["rows"],
-                                                      CANDIDATES["stages"]):
+    for P, warps, rows, stages in candidates():
         ctx.set_tuning(P, warps, rows, stages, 0)
-        b = wln.Batch(ctx, ens, pr, r, t, n_groups, prec=prec)
-        b.run(graph=False)                       # warm-up
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(2):
-            b.run(graph=False)
-        z.record(stream)
-        z.synchronize()
-        ms = a.elapsed_time(z) / 2
+        ms = float(timer())
         seg = n_pts * ens.n_loops * ens.ppl / (ms / 1e3)
         results.append({"P": P, "warps": warps, "rows": rows, "stages": stages, "ms": ms,
                         "seg_per_s": seg})
-        b.free()
         if verbose:
             print(results[-1])
     best = max(results, key=lambda x: x["seg_per_s"])

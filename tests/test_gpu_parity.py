@@ -259,3 +259,48 @@ def test_invalid_arguments_raise(ctx):
         ctx.ensemble_from_host(xy)                        # zero-length segments
     # the context is still usable
     ctx.wilson_avg(ens, [I.Profile(0, F=1.0, lam=1.0)], [[0.0]], [[1.0]], 4, where="host")
+
+
+# Every launch shape the library instantiates for the float paths, as the
+# autotuner (and wln_set_tuning) can select them: (radii per lane, warps per
+# CTA) x float4 rows per staged chunk x chunks in flight.
+SHAPES = [(P, w, r, st) for (P, w) in ((2, 8), (4, 4), (4, 8), (8, 8))
+          for r in (16, 32, 64) for st in (2, 3, 4)]
+
+
+def _naive_rel(ppl):
+    # The naive flavour sums ppl/8 partials of 8 terms without compensation
+    # (worst case (ppl/8) float ulps, 2^-24 each, of the summed magnitudes) on
+    # top of the per-term rounding of the compensated bar.
+    return F32_REL + (ppl / 8) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_every_launch_shape_matches_oracle(ctx, case):
+    """All 36 float shapes (with the low-angle forms on) against the oracle at
+    the parity bar, FP32 compensated; FP32 naive on the four (radii, warps)
+    shapes.  Warps per CTA, rows per chunk and stages change how the work is
+    scheduled, not the arithmetic of a radius, so at fixed radii per lane the
+    sums are also bitwise equal across them."""
+    n_loops, ppl, G, prof, rho, T = CASES[case]
+    y32, ens = _ensemble_from_oracle(ctx, 11 + case, n_loops, ppl)
+    ref = oracle.group_sums(y32.astype(np.float64), prof, rho, T, G)
+    bars = _bars(y32, prof, rho, T, G, 1e-6, F32_REL)
+    nbars = _bars(y32, prof, rho, T, G, 1e-6, _naive_rel(ppl))
+    ctx.set_low_angle(2)
+    by_P = {}
+    try:
+        for P, w, r, st in SHAPES:
+            ctx.set_tuning(P, w, r, st, 0)
+            gpu = ctx.wilson_avg(ens, [prof], [rho], [T], G, prec="fp32", where="host")
+            _compare(gpu, ref, n_loops // G, bars, what=f"case {case} shape {(P, w, r, st)}")
+            if P in by_P:
+                assert np.array_equal(gpu, by_P[P]), (P, w, r, st)
+            else:
+                by_P[P] = gpu
+            if r == 32 and st == 3:
+                nv = ctx.wilson_avg(ens, [prof], [rho], [T], G, prec="fp32_naive", where="host")
+                _compare(nv, ref, n_loops // G, nbars, what=f"naive case {case} shape {(P, w)}")
+    finally:
+        ctx.set_tuning()
+    ens.free()

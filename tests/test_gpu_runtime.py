@@ -1,6 +1,9 @@
 """GPU tests of the runtime around the Wilson kernel: reusable batches with
 CUDA-graph replay, and the continuous-batching request server.
 
+  * Batch and server group sums against the FP64 oracle on the same loops,
+    at the parity bar of test_gpu_parity.py (every profile of a batch; every
+    request of the server, alone and mixed).
   * A batch's group sums equal wln_wilson_avg's bitwise, its statistics and
     effective action equal wln_jackknife's and wln_effective_action's, and a
     graph replay reproduces a direct run bitwise.
@@ -15,8 +18,10 @@ CUDA-graph replay, and the continuous-batching request server.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1407_7486_gb300 import inputs as I
 from paper_1407_7486_gb300 import wln
+from test_gpu_parity import F32_REL, _bars, _compare
 
 pytestmark = pytest.mark.gpu
 
@@ -56,12 +61,27 @@ def _profiles():
     return profs, rhos, Ts
 
 
+def _oracle_check(ctx, ens, profs, rhos, Ts, G, S, what):
+    y32, _ = ctx.loops_copy(ens)
+    y = y32.astype(np.float64)
+    lpg = ens.n_loops // G
+    off = 0
+    for q, (p, r, t) in enumerate(zip(profs, rhos, Ts)):
+        n = len(r) * len(t)
+        ref = oracle.group_sums(y, p, r, t, G)
+        _compare(S[off:off + n], ref, lpg, _bars(y32, p, r, t, G, 1e-6, F32_REL),
+                 what=f"{what} profile {q}")
+        off += n
+    assert off == S.shape[0]
+
+
 def test_batch_matches_one_shot_calls_and_graph_replay(ctx, ens):
     profs, rhos, Ts = _profiles()
     G, lpg = 8, ens.n_loops // 8
     b = wln.Batch(ctx, ens, profs, rhos, Ts, G, prec="fp32")
     b.run(graph=False)
     S0, st0, g0 = b.results()
+    _oracle_check(ctx, ens, profs, rhos, Ts, G, S0, "batch")
     ref = ctx.wilson_avg(ens, profs, rhos, Ts, G, prec="fp32", where="host")
     assert np.array_equal(S0, ref)
     js = ctx.jackknife(ref, G, lpg, 0, jk_var=False, where="host")
@@ -109,6 +129,8 @@ def test_server_results_are_the_same_alone_and_mixed(ctx, ens):
     for q, rid in enumerate(ids):
         for a, m in zip(alone[q], mixed[rid]):
             assert np.array_equal(a, m), q
+        _oracle_check(ctx, ens, [profs[q]], [rhos[q]], [Ts[q]], G, mixed[rid][0],
+                      f"server request {q}")
         ref = ctx.wilson_avg(ens, [profs[q]], [rhos[q]], [Ts[q]], G, prec="fp32", where="host")
         lpg = ens.n_loops // G
         scale = np.maximum(1.0, np.abs(ref) / lpg)
