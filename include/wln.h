@@ -211,12 +211,49 @@ wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t
  * profiles, rho_cm, rho_off, T, T_off: host arrays.
  * Rules: n_groups >= 2 divides n_loops; T > 0; rho_cm >= 0; lambda > 0 for
  * flux tubes; every profile has at least one rho and one T.
+ *
+ * Precision guard (WLN_PREC_FP32_COMP, flux tubes, groups of a whole number
+ * of 32-loop blocks, at most 64 of them; see wln_set_precision_guard): the
+ * spinor sums (WLN_C_FERM, WLN_C_FERM_SQ) of a group are dominated by its
+ * loops of largest spin, whose float rounding cosh(spin) magnifies (Sec.
+ * "Uncertainties and the Fermion Problem").  The float pass estimates each
+ * group's spinor error from a rounding model of the float walk; where it
+ * exceeds half of 1e-6 max(1, <cosh spin>) it recomputes the loops carrying
+ * most of it in double-float (~2^-44) and corrects the sums.  The other
+ * components stay float.  A group with more than 64 such loops per radius
+ * keeps the rest in float (counted in wln_precision_guard_stats).  The
+ * corrections are applied in a fixed order, so results stay independent of
+ * the batch and of scheduling.  If the queue of loops to recompute fills
+ * (more than n_points * n_loops / 512 of them, at least 65536) the call
+ * returns WLN_ENOMEM, at the next synchronising call for a device output.
  */
 wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
                           const wln_profile* profiles, int32_t n_profiles,
                           const double* rho_cm, const int32_t* rho_off,
                           const double* T, const int32_t* T_off,
                           int32_t n_groups, wln_prec prec, double* group_sums);
+
+/*
+ * The precision guard of the FP32-compensated group sums (wln_wilson_avg,
+ * wln_wilson_avg_noalloc, batches created afterwards, servers created
+ * afterwards): enabled = 1 (the default) or 0.  enabled = 2 recomputes every
+ * loop of the blocks it records (those reaching spin 2), up to 64 per group
+ * and radius, whatever the error estimate: a check of the double-float walk
+ * against the oracle, not for production.  No paper counterpart: the paper
+ * runs FP32 throughout.
+ */
+wln_status wln_set_precision_guard(wln_ctx* ctx, int32_t enabled);
+
+/*
+ * Running totals of the precision guard over the guarded launches on this
+ * context (and on batches and servers created from it): loops recomputed in
+ * double-float, launches, (group, radius) selections dropped because the
+ * queue was full, and (group, radius) selections left in float because 64
+ * loops would not bring the estimate under the budget.  Waits for the context's
+ * stream; reset = 1 zeroes the totals.  Any pointer may be NULL.
+ */
+wln_status wln_precision_guard_stats(wln_ctx* ctx, int64_t* escalated_loops, int64_t* launches,
+                                     int64_t* overflows, int64_t* saturated, int32_t reset);
 
 /*
  * wln_wilson_avg without any allocation: the same group sums, with the same

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwln.so")
-SOURCES = ["wln_api.cu", "wln_gen.cu", "wln_wilson.cu", "wln_stats.cu", "wln_noalloc.cu", "wln_runtime.cu"]
+SOURCES = ["wln_api.cu", "wln_gen.cu", "wln_wilson.cu", "wln_stats.cu", "wln_noalloc.cu", "wln_runtime.cu", "wln_guard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -131,7 +131,8 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
   const size_t n4 = static_cast<size_t>(en->e.n_blocks) * (ppl / 2) * 32;
   cudaError_t err = cudaMalloc(&en->e.blocks, n4 * sizeof(float4));
   if (err == cudaSuccess)
-    err = cudaMalloc(&en->e.stats, static_cast<size_t>(en->e.n_blocks) * sizeof(float2));
+    err = cudaMalloc(&en->e.stats, static_cast<size_t>(en->e.n_blocks) * (sizeof(float2) + sizeof(float)));
+  if (err == cudaSuccess) en->e.maxlen = reinterpret_cast<float*>(en->e.stats + en->e.n_blocks);
   if (err == cudaSuccess && fp64)
     err = cudaMalloc(&en->e.xy64, static_cast<size_t>(n_loops) * 2 * ppl * sizeof(double));
   if (err != cudaSuccess) {
@@ -366,8 +367,11 @@ wln_status wln_create(wln_ctx** out, int device, void* cuda_stream) {
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  err = cudaMalloc(&ctx->d_flag, sizeof(int));
-  if (err == cudaSuccess) err = cudaMemset(ctx->d_flag, 0, sizeof(int));
+  // the device error flag and the precision guard's running totals
+  err = cudaMalloc(&ctx->d_flag, 64);
+  if (err == cudaSuccess) err = cudaMemset(ctx->d_flag, 0, 64);
+  if (err == cudaSuccess)
+    ctx->d_guard_totals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->d_flag) + 8);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
@@ -417,6 +421,31 @@ wln_status wln_selftest_wait(wln_ctx* ctx, int32_t timeout_ms) {
   ++ctx->launches;
   if (err != cudaSuccess) return cuda_fail(ctx, err, "self-test launch");
   return check_flag(ctx);
+}
+
+wln_status wln_set_precision_guard(wln_ctx* ctx, int32_t enabled) {
+  if (!ctx) return WLN_EINVAL;
+  if (enabled < 0 || enabled > 2) return fail(ctx, WLN_EINVAL, "precision guard: 0, 1 or 2");
+  ctx->guard = enabled;
+  return WLN_OK;
+}
+
+wln_status wln_precision_guard_stats(wln_ctx* ctx, int64_t* escalated_loops, int64_t* launches,
+                                     int64_t* overflows, int64_t* saturated, int32_t reset) {
+  if (!ctx) return WLN_EINVAL;
+  DeviceGuard guard(ctx->device);
+  unsigned long long h[4] = {0, 0, 0, 0};
+  cudaError_t err = cudaMemcpyAsync(h, ctx->d_guard_totals, sizeof(h), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+  if (err == cudaSuccess && reset)
+    err = cudaMemsetAsync(ctx->d_guard_totals, 0, sizeof(h), ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard statistics");
+  if (escalated_loops) *escalated_loops = static_cast<int64_t>(h[0]);
+  if (overflows) *overflows = static_cast<int64_t>(h[1]);
+  if (saturated) *saturated = static_cast<int64_t>(h[2]);
+  if (launches) *launches = static_cast<int64_t>(h[3]);
+  return WLN_OK;
 }
 
 wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_loops,
@@ -597,9 +626,14 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   const int P = plan_points_per_lane(ctx, prec, mode);
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl, P, bt);
   if (bt.n_points > (int64_t(1) << 31) - 1) return fail(ctx, WLN_EINVAL, "too many points");
-  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, mode);
+  const bool use_guard =
+      guard_applies(ctx, prec, mode, ens->e.n_loops, n_groups, profiles, n_profiles);
+  const int bpg = guard_layout_bpg(prec, mode, ens->e.n_loops, n_groups);
+  const WilsonPlan plan =
+      make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, mode, bpg);
 
-  // Device layout of this call: work list | profiles | radii | partials | (host output)
+  // Device layout of this call: work list | profiles | radii | partials |
+  // (precision guard: per-warp records, queue, counters) | (host output)
   Carve cv;
   const size_t o_tiles = cv.take<Tile>(bt.tiles.size());
   const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
@@ -608,6 +642,19 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   const size_t n_partial =
       per_loop ? 0 : static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
   const size_t o_part = cv.take<double>(n_partial);
+  GuardBufs gb;
+  size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
+  int64_t gcap = 0;
+  if (use_guard) {
+    gb.on = 1;
+    gb.bpg = bpg;
+    gb.warp_bytes = guard_warp_bytes(bpg, plan.P);
+    gcap = guard_capacity(bt.n_points, ens->e.n_loops);
+    o_gscr = cv.take<char>(static_cast<size_t>(wilson_grid(plan, ens->e, prec)) * plan.warps *
+                           gb.warp_bytes);
+    o_gq = cv.take<char>(guard_queue_bytes(gcap));
+    o_gcnt = cv.take<int>(4);
+  }
   const size_t n_out = per_loop ? static_cast<size_t>(bt.n_points) * ens->e.n_loops * 2
                                 : static_cast<size_t>(bt.n_points) * n_groups * K;
   Out out = plan_out(cv, group_sums, n_out);
@@ -633,10 +680,22 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
     if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
   } else {
     const int32_t lpg = ens->e.n_loops / n_groups;
+    if (use_guard) {
+      guard_bind(gb, d + o_gscr, d + o_gq, gcap, at<int>(d, o_gcnt));
+      guard_attach(gb, ctx);
+      err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), ctx->stream);
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard counters");
+    }
     err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
                         at<ProfileDev>(d, o_profs), at<double>(d, o_rho), n_groups, lpg, prec,
-                        at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches);
+                        at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches,
+                        use_guard ? &gb : nullptr);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+    if (use_guard) {
+      err = launch_guard(ctx->stream, gb, ens->e, at<Tile>(d, o_tiles), at<ProfileDev>(d, o_profs),
+                         at<double>(d, o_rho), at<double>(d, o_part), ctx->num_sms, &launches);
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard");
+    }
     err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
                                  n_groups, lpg, static_cast<double*>(out.dev));
     ++launches;

@@ -214,12 +214,14 @@ __global__ void degenerate_kernel(const float4* blocks, int32_t n_loops, int32_t
 // valid loops.  The Wilson kernel bounds the angle its segments subtend at
 // the field axis with them.  One CTA per block, a fixed reduction tree.
 __global__ void block_stats_kernel(const float4* blocks, int32_t n_loops, int32_t ppl,
-                                   float2* stats) {
-  __shared__ float sd[8], sr[8];
+                                   float2* stats, float* maxlen) {
+  __shared__ float sd[8], sr[8], sl[8][32];
   const int64_t rows = ppl / 2;
   const int64_t b = blockIdx.x;
   const float4* base = blocks + b * rows * 32;
-  float d2 = 0.f, r2 = 0.f;
+  float d2 = 0.f, r2 = 0.f, len = 0.f;
+  // thread t walks lane t & 31 (blockDim is a multiple of 32): the partial
+  // lengths of one loop sit in the same lane of every warp
   for (int64_t i = threadIdx.x; i < rows * 32; i += blockDim.x) {
     const int lane = static_cast<int>(i & 31);
     const int64_t r = i >> 5;
@@ -227,27 +229,38 @@ __global__ void block_stats_kernel(const float4* blocks, int32_t n_loops, int32_
     const float4 a = base[r * 32 + lane];
     const float4 c = base[((r + 1) % rows) * 32 + lane];
     const float ux = a.z - a.x, uy = a.w - a.y, vx = c.x - a.z, vy = c.y - a.w;
-    d2 = fmaxf(d2, fmaxf(ux * ux + uy * uy, vx * vx + vy * vy));
+    const float du = ux * ux + uy * uy, dv = vx * vx + vy * vy;
+    d2 = fmaxf(d2, fmaxf(du, dv));
     r2 = fmaxf(r2, fmaxf(a.x * a.x + a.y * a.y, a.z * a.z + a.w * a.w));
+    len += sqrtf(du) + sqrtf(dv);
   }
+  sl[threadIdx.x >> 5][threadIdx.x & 31] = len;
   for (int o = 16; o > 0; o >>= 1) {
     d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
     r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
   }
   if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d2; sr[threadIdx.x >> 5] = r2; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
-      d2 = fmaxf(d2, sd[w]);
-      r2 = fmaxf(r2, sr[w]);
+  if (threadIdx.x < 32) {
+    // one loop's length over the warps, then the longest loop of the block
+    float l = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) l += sl[w][threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) l = fmaxf(l, __shfl_xor_sync(0xffffffffu, l, o));
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+        d2 = fmaxf(d2, sd[w]);
+        r2 = fmaxf(r2, sr[w]);
+      }
+      // square roots and the length rounded up by a relative 2^-20 (the
+      // length also by the float sum's rounding, ppl 2^-24): bounds, not estimates
+      stats[b] = make_float2(sqrtf(d2) * (1.0f + 0x1p-20f), sqrtf(r2) * (1.0f + 0x1p-20f));
+      maxlen[b] = l * (1.0f + 0x1p-20f + static_cast<float>(ppl) * 0x1p-24f);
     }
-    // square roots rounded up by a relative 2^-20: bounds, not estimates
-    stats[b] = make_float2(sqrtf(d2) * (1.0f + 0x1p-20f), sqrtf(r2) * (1.0f + 0x1p-20f));
   }
 }
 
 cudaError_t launch_block_stats(cudaStream_t s, const Ensemble& e) {
-  block_stats_kernel<<<e.n_blocks, 256, 0, s>>>(e.blocks, e.n_loops, e.ppl, e.stats);
+  block_stats_kernel<<<e.n_blocks, 256, 0, s>>>(e.blocks, e.n_loops, e.ppl, e.stats, e.maxlen);
   return cudaGetLastError();
 }
 

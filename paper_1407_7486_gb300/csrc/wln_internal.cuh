@@ -56,6 +56,8 @@ struct Ensemble {
   float4* blocks = nullptr;   // [n_blocks][ppl/2][32]
   double* xy64 = nullptr;     // optional [n_loops][2][ppl]
   float2* stats = nullptr;    // [n_blocks]: longest segment, largest |y| of the block's loops
+  float* maxlen = nullptr;    // [n_blocks]: longest loop (sum of its segment lengths), in
+                              // the same allocation as stats
 };
 
 // Per-profile constants used by the Wilson kernels.
@@ -109,6 +111,35 @@ struct WilsonPlan {
   int low_angle;      // highest cheaper form of theta a block may take (0, 1 or 2)
 };
 
+// Precision guard of the FP32-compensated group sums (wln_guard.cu): a
+// queued loop to recompute in double-float, the partial sum its correction
+// belongs to, and the buffers of one Wilson launch.
+struct GuardItem {
+  int32_t tile;     // tile index in the launch's work list; -1: not filled
+  int32_t p_loop;   // radius within the tile << 24 | loop index
+  double f1;        // the float pass's W_ferm - 1 of this loop and radius
+};
+struct GuardSlot {
+  int64_t dst;      // index (in doubles) of the partial's first component
+  int32_t item0;    // its queued loops: items [item0, item0 + n)
+  int32_t n;
+};
+constexpr int kGuardSel = 64;   // loops a warp may select per (group, radius)
+struct GuardBufs {
+  int on = 0;
+  int all = 0;                  // select every recorded loop (a check of the double-float walk)
+  int bpg = 0;                  // 32-loop blocks per group
+  char* scratch = nullptr;      // per warp (guard_warp_bytes): block maxima, per-lane
+                                // |spin|, sin(phase), float W_ferm - 1, selection list
+  size_t warp_bytes = 0;
+  GuardItem* items = nullptr;
+  double2* out = nullptr;       // per item: corrections of W_ferm - 1 and of its square
+  GuardSlot* slots = nullptr;
+  int64_t cap = 0;              // items (and slots) the queue holds
+  int* counters = nullptr;      // this launch: items, slots, overflows, saturated selections
+  unsigned long long* totals = nullptr;   // the context's running totals (wln_precision_guard_stats)
+};
+
 struct Scratch {
   void* ptr = nullptr;
   size_t bytes = 0;
@@ -130,6 +161,9 @@ struct wln_ctx {
   // tuning overrides (0 = automatic)
   int tune_P = 0, tune_warps = 0, tune_rows = 0, tune_stages = 0, tune_chain = 0;
   int low_angle = 2;    // highest cheaper form of theta the float walks may take
+  int guard = 1;        // precision guard of the FP32-compensated group sums (2: every
+                        // recorded loop, a check of the double-float walk)
+  unsigned long long* d_guard_totals = nullptr;   // escalated loops, overflows, saturated, launches
 };
 
 struct wln_ensemble {
@@ -180,14 +214,38 @@ cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, 
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
 
-// Wilson loops (wln_wilson.cu).
+// Wilson loops (wln_wilson.cu).  guard_bpg > 0 aligns the chains of blocks to
+// groups of that many blocks, as the precision guard needs.
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
-                     int mode = kModeSums);
+                     int mode = kModeSums, int guard_bpg = 0);
+// The persistent grid a Wilson launch of this plan uses.
+int wilson_grid(const WilsonPlan& plan, const Ensemble& e, wln_prec prec);
 int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode = kModeSums);
 cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
-                          double* partial, int64_t n_points, int* d_flag, int64_t* launches);
+                          double* partial, int64_t n_points, int* d_flag, int64_t* launches,
+                          const GuardBufs* guard = nullptr);
+
+// Precision guard (wln_guard.cu).  The blocks per group when the pass's
+// layout admits it (FP32-compensated group sums, groups of a whole number of
+// 32-loop blocks, at most 64), else 0: the plan aligns its chains to them
+// whether or not the guard runs, so the guard changes only the loops it
+// recomputes.  Whether a pass takes it: that layout, the context's setting,
+// and some flux-tube profile.
+int guard_layout_bpg(wln_prec prec, int mode, int32_t n_loops, int32_t n_groups);
+bool guard_applies(const wln_ctx* ctx, wln_prec prec, int mode, int32_t n_loops,
+                   int32_t n_groups, const wln_profile* profiles, int32_t n_profiles);
+size_t guard_warp_bytes(int bpg, int P);
+int64_t guard_capacity(int64_t n_points, int32_t n_loops);
+size_t guard_queue_bytes(int64_t cap);
+void guard_bind(GuardBufs& g, void* scratch, void* queue, int64_t cap, int* counters);
+// The context's mode and running totals into g.
+void guard_attach(GuardBufs& g, const wln_ctx* ctx);
+// Recomputes the queued loops and adds the corrections to their partials.
+cudaError_t launch_guard(cudaStream_t s, const GuardBufs& g, const Ensemble& e,
+                         const Tile* tiles, const ProfileDev* profs, const double* rho,
+                         double* partial, int num_sms, int64_t* launches);
 // Per-loop values: out[p][loop][2] = (W_scal - 1, W_ferm - 1), p the point.
 cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                                 const Tile* tiles, const ProfileDev* profs, const double* rho,

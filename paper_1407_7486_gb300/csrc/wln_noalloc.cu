@@ -142,7 +142,11 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
   if (n_tiles > (int64_t(1) << 30) || n_points > (int64_t(1) << 30))
     return fail(ctx, WLN_EINVAL, "too many points");
   const int32_t n_rho = rho_off[n_profiles], n_T = T_off[n_profiles];
-  const WilsonPlan plan = make_plan(ctx, ens->e, static_cast<int>(n_tiles), prec);
+  const bool use_guard =
+      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles);
+  const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
+  const WilsonPlan plan =
+      make_plan(ctx, ens->e, static_cast<int>(n_tiles), prec, kModeSums, bpg);
   const bool host_out = !is_device_ptr(group_sums);
 
   // Layout inside the array: inputs copied from the host, the work list built
@@ -162,6 +166,20 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
                              n_points * WLN_K);
   const size_t out_bytes = sizeof(double) * static_cast<size_t>(n_points) * n_groups * WLN_K;
   const size_t o_out = host_out ? take(out_bytes) : 0;
+  // the precision guard's per-warp records, queue and counters
+  GuardBufs gb;
+  size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
+  int64_t gcap = 0;
+  if (use_guard) {
+    gb.on = 1;
+    gb.bpg = bpg;
+    gb.warp_bytes = guard_warp_bytes(bpg, plan.P);
+    gcap = guard_capacity(n_points, ens->e.n_loops);
+    o_gscr = take(static_cast<size_t>(wilson_grid(plan, ens->e, prec)) * plan.warps *
+                  gb.warp_bytes);
+    o_gq = take(guard_queue_bytes(gcap));
+    o_gcnt = take(4 * sizeof(int));
+  }
   if (off > kNoAllocBytes)
     return fail(ctx, WLN_EINVAL,
                 "problem needs " + std::to_string(off >> 20) + " MiB of working memory; the "
@@ -205,11 +223,22 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
   const int32_t lpg = ens->e.n_loops / n_groups;
   double* out = host_out ? reinterpret_cast<double*>(d + o_out) : group_sums;
   int64_t launches = 2;
+  if (use_guard) {
+    guard_bind(gb, d + o_gscr, d + o_gq, gcap, reinterpret_cast<int*>(d + o_gcnt));
+    guard_attach(gb, ctx);
+    if (err == cudaSuccess) err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), s);
+  }
   if (err == cudaSuccess)
     err = launch_wilson(s, plan, ens->e, reinterpret_cast<const Tile*>(d + o_tiles),
                         reinterpret_cast<const ProfileDev*>(d + o_pd),
                         reinterpret_cast<const double*>(d + o_rho), n_groups, lpg, prec,
-                        reinterpret_cast<double*>(d + o_part), n_points, ctx->d_flag, &launches);
+                        reinterpret_cast<double*>(d + o_part), n_points, ctx->d_flag, &launches,
+                        use_guard ? &gb : nullptr);
+  if (err == cudaSuccess)
+    err = launch_guard(s, gb, ens->e, reinterpret_cast<const Tile*>(d + o_tiles),
+                       reinterpret_cast<const ProfileDev*>(d + o_pd),
+                       reinterpret_cast<const double*>(d + o_rho),
+                       reinterpret_cast<double*>(d + o_part), ctx->num_sms, &launches);
   if (err == cudaSuccess) {
     err = launch_reduce_partials(s, plan, ens->e, reinterpret_cast<const double*>(d + o_part),
                                  n_points, n_groups, lpg, out);

@@ -49,13 +49,22 @@ struct wln_batch {
   bool has_action = false;
   cudaGraphExec_t graph = nullptr;
   int64_t kernels_per_run = 0;
+  GuardBufs guard;            // precision guard (FP32 compensated, whole-block groups)
+  int num_sms = 0;
 };
 
 namespace {
 
 cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* launches) {
-  cudaError_t err = launch_wilson(s, b->plan, b->ens->e, b->tiles, b->profs, b->rho, b->n_groups,
-                                  b->lpg, b->prec, b->partial, b->n_points, flag, launches);
+  cudaError_t err = cudaSuccess;
+  if (b->guard.on) err = cudaMemsetAsync(b->guard.counters, 0, 4 * sizeof(int), s);
+  if (err != cudaSuccess) return err;
+  err = launch_wilson(s, b->plan, b->ens->e, b->tiles, b->profs, b->rho, b->n_groups, b->lpg,
+                      b->prec, b->partial, b->n_points, flag, launches,
+                      b->guard.on ? &b->guard : nullptr);
+  if (err != cudaSuccess) return err;
+  err = launch_guard(s, b->guard, b->ens->e, b->tiles, b->profs, b->rho, b->partial, b->num_sms,
+                     launches);
   if (err != cudaSuccess) return err;
   err = launch_reduce_partials(s, b->plan, b->ens->e, b->partial, b->n_points, b->n_groups,
                                b->lpg, b->sums);
@@ -134,7 +143,11 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl,
               plan_points_per_lane(ctx, prec), bt);
   b->n_points = bt.n_points;
-  b->plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec);
+  const bool use_guard =
+      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles);
+  const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
+  b->plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, kModeSums, bpg);
+  b->num_sms = ctx->num_sms;
   std::vector<QuadProfile> qp;
   b->has_action = build_quad(profiles, n_profiles, rho_cm, rho_off, T, T_off, qp, nullptr);
 
@@ -153,6 +166,18 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   const size_t o_stats = take(sizeof(double) * kStats * static_cast<size_t>(b->n_points));
   const size_t o_gg = take(sizeof(double) * 2 * static_cast<size_t>(n_profiles) * n_groups);
   const size_t o_gamma = take(sizeof(double) * 4 * static_cast<size_t>(n_profiles));
+  size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
+  int64_t gcap = 0;
+  if (use_guard) {
+    b->guard.on = 1;
+    b->guard.bpg = bpg;
+    b->guard.warp_bytes = guard_warp_bytes(bpg, b->plan.P);
+    gcap = guard_capacity(b->n_points, ens->e.n_loops);
+    o_gscr = take(static_cast<size_t>(wilson_grid(b->plan, ens->e, prec)) * b->plan.warps *
+                  b->guard.warp_bytes);
+    o_gq = take(guard_queue_bytes(gcap));
+    o_gcnt = take(4 * sizeof(int));
+  }
   cudaError_t err = cudaMalloc(&b->mem, off);
   if (err != cudaSuccess) {
     delete b;
@@ -169,6 +194,10 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   b->stats = reinterpret_cast<double*>(d + o_stats);
   b->gg = reinterpret_cast<double*>(d + o_gg);
   b->gamma = reinterpret_cast<double*>(d + o_gamma);
+  if (use_guard) {
+    guard_bind(b->guard, d + o_gscr, d + o_gq, gcap, reinterpret_cast<int*>(d + o_gcnt));
+    guard_attach(b->guard, ctx);   // mode and statistics of the creating context
+  }
   std::vector<char> h(upload, 0);
   std::memcpy(h.data() + o_tiles, bt.tiles.data(), sizeof(Tile) * bt.tiles.size());
   std::memcpy(h.data() + o_profs, bt.profs.data(), sizeof(ProfileDev) * bt.profs.size());
@@ -357,6 +386,10 @@ struct wln_server {
   std::vector<std::pair<int64_t, int32_t>> inflight[2];
   int cur = 0;
   int64_t steps = 0;
+  // precision guard: per-warp records shared by the steps (they run in stream
+  // order), a queue and counters per step slot
+  GuardBufs guard[2];
+  char* d_guard = nullptr;
 };
 
 namespace {
@@ -530,11 +563,19 @@ wln_status launch_step(wln_server* sv, int slot) {
   plan.n_tile_groups = static_cast<int>(pick.size());
   plan.n_items = static_cast<int64_t>(plan.n_chains) * plan.n_tile_groups;
   int64_t launches = 0;
+  const GuardBufs& gb = sv->guard[slot];
+  if (err == cudaSuccess && gb.on) err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), s);
   if (err == cudaSuccess)
     err = launch_wilson(s, plan, sv->ens->e, reinterpret_cast<Tile*>(d + o_tiles),
                         reinterpret_cast<ProfileDev*>(d + o_profs),
                         reinterpret_cast<double*>(d + o_rho), sv->G, sv->lpg, sv->prec,
-                        reinterpret_cast<double*>(sv->arena), 0, sv->ctx->d_flag, &launches);
+                        reinterpret_cast<double*>(sv->arena), 0, sv->ctx->d_flag, &launches,
+                        gb.on ? &gb : nullptr);
+  if (err == cudaSuccess)
+    err = launch_guard(s, gb, sv->ens->e, reinterpret_cast<Tile*>(d + o_tiles),
+                       reinterpret_cast<ProfileDev*>(d + o_profs),
+                       reinterpret_cast<double*>(d + o_rho), reinterpret_cast<double*>(sv->arena),
+                       sv->ctx->num_sms, &launches);
   sv->ctx->launches += launches;
   if (err == cudaSuccess) err = cudaEventRecord(sv->step_done[slot], s);
   if (err != cudaSuccess) return cuda_fail(sv->ctx, err, "server step");
@@ -569,7 +610,10 @@ wln_status wln_server_create(wln_ctx* ctx, const wln_ensemble* ens, int32_t n_gr
   sv->tg_per_step = tile_groups_per_step;
   // One fixed work decomposition (chain length) for every step, so a request's
   // sums are accumulated in the same order whatever it is batched with.
-  sv->base = make_plan(ctx, ens->e, tile_groups_per_step * 8, prec);
+  const wln_profile tube{WLN_PROFILE_FLUX_TUBE, 0, 1.0, 1.0, 0.0};
+  const bool use_guard = guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, &tube, 1);
+  const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
+  sv->base = make_plan(ctx, ens->e, tile_groups_per_step * 8, prec, kModeSums, bpg);
   sv->P = sv->base.P;
   sv->warps = sv->base.warps;
   sv->arena_bytes = static_cast<size_t>(arena_bytes);
@@ -583,6 +627,23 @@ wln_status wln_server_create(wln_ctx* ctx, const wln_ensemble* ens, int32_t n_gr
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&sv->step_done[i], cudaEventDisableTiming);
   }
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&sv->fin_stream, cudaStreamNonBlocking);
+  if (err == cudaSuccess && use_guard) {
+    const size_t scr = align256(static_cast<size_t>(wilson_grid(sv->base, ens->e, prec)) *
+                                sv->base.warps * guard_warp_bytes(bpg, sv->P));
+    const int64_t cap = guard_capacity(static_cast<int64_t>(tile_groups_per_step) * sv->warps *
+                                           sv->P, ens->e.n_loops);
+    const size_t q = align256(guard_queue_bytes(cap)), cnt = 256;
+    err = cudaMalloc(reinterpret_cast<void**>(&sv->d_guard), scr + 2 * (q + cnt));
+    for (int i = 0; i < 2 && err == cudaSuccess; ++i) {
+      GuardBufs& g = sv->guard[i];
+      g.on = 1;
+      g.bpg = bpg;
+      g.warp_bytes = guard_warp_bytes(bpg, sv->P);
+      guard_bind(g, sv->d_guard, sv->d_guard + scr + i * (q + cnt), cap,
+                 reinterpret_cast<int*>(sv->d_guard + scr + i * (q + cnt) + q));
+      guard_attach(g, ctx);
+    }
+  }
   if (err != cudaSuccess) {
     wln_server_free(sv);
     return cuda_fail(ctx, err, "server allocation");
@@ -749,6 +810,9 @@ wln_status wln_server_free(wln_server* sv) {
   }
   for (int i = 0; i < 2; ++i) {
     if (sv->d_step[i]) cudaFree(sv->d_step[i]);
+  }
+  if (sv->d_guard) cudaFree(sv->d_guard);
+  for (int i = 0; i < 2; ++i) {
     if (sv->h_step[i]) cudaFreeHost(sv->h_step[i]);
     if (sv->step_done[i]) cudaEventDestroy(sv->step_done[i]);
   }

@@ -51,6 +51,7 @@
 // even point and the square (i even) or the triangle (i odd) with its odd
 // point, so the levels cost the same N segments per loop and radius.
 #include <cfloat>
+#include <type_traits>
 
 #include "wln_internal.cuh"
 
@@ -65,33 +66,32 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
+// mbarrier helpers take the barrier's shared-memory address.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
@@ -104,7 +104,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Bounded wait on an mbarrier phase: gives up after limit_ns of wall time
 // (2 s by default), or after 2^26 polls whatever the clock says.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -116,11 +116,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
+                                          uint32_t bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
@@ -255,7 +255,9 @@ struct KParams {
   int* flag;
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
   const float2* stats;   // per block: longest segment, largest |y|
+  const float* maxlen;   // per block: longest loop
   int32_t low_angle;     // highest form of theta a block may take (0: general everywhere)
+  GuardBufs guard;       // precision guard (FP32 compensated group sums)
 };
 
 // Whether every segment of block b subtends at most pi/4 at the field axis
@@ -451,7 +453,7 @@ __device__ __forceinline__ double cosh_m1_f64(double x) {
 template <class A>
 __device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp_s, double sp_c,
                                              F2 tp, F2 st, double tp_d, double st_d,
-                                             double* w) {
+                                             double* w, float* spin_abs = nullptr) {
   if constexpr (sizeof(typename A::F) == 8) {
     const double turns = ph_s * tp_d;
     const double fr = turns - rint(turns);
@@ -476,6 +478,7 @@ __device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp
     const float sgn = copysignf(1.0f, sv.hi);
     sv.hi *= sgn;
     sv.lo *= sgn;
+    if (spin_abs) *spin_abs = sv.hi;
     double ferm_m1;
     if (sv.hi < 80.0f) {
       const float em1 = expm1f(sv.hi);
@@ -504,17 +507,20 @@ __device__ __forceinline__ void wilson_terms(double ph_s, double ph_c, double sp
 }
 
 // Shared pipeline state of a CTA: a ring of staged chunks with full/empty
-// mbarriers; thread 0 also refills it.
+// mbarriers (kept as 32-bit shared-memory addresses); thread 0 also refills
+// it, with its bookkeeping in shared memory (no other thread needs it, so it
+// takes no registers in the walking threads).
 struct Pipe {
   float4* ring;
-  uint64_t* full;
-  uint64_t* empty;
-  int stages, chunk_rows, chunks_per_block, rows_per_block;
-  uint32_t chunk_bytes;
-  int32_t kc = 0, issued = 0, total = 0;
-  int32_t prod_item = 0;
-  int prod_blk = 0, prod_chunk = 0;
+  uint32_t full, empty;   // shared addresses of the mbarrier arrays
+  int stages, chunk_rows, chunks_per_block;
+  int32_t kc = 0;
 };
+
+struct ProdState {
+  int32_t issued, total, item, blk, chunk;
+};
+__shared__ ProdState s_prod;
 
 __device__ __forceinline__ int blocks_in_item(const KParams& k, int64_t item) {
   const int c = static_cast<int>(item / k.n_tile_groups);
@@ -522,20 +528,23 @@ __device__ __forceinline__ int blocks_in_item(const KParams& k, int64_t item) {
   return min(b0 + k.chain, k.n_blocks) - b0;
 }
 
-__device__ __forceinline__ void issue_next(const KParams& k, Pipe& pp, int slot) {
-  const int c = static_cast<int>(pp.prod_item / k.n_tile_groups);
-  const int b = c * k.chain + pp.prod_blk;
-  const float4* src = k.blocks + (static_cast<size_t>(b) * pp.rows_per_block +
-                                  static_cast<size_t>(pp.prod_chunk) * pp.chunk_rows) * 32;
-  mbar_arrive_expect_tx(&pp.full[slot], pp.chunk_bytes);
-  bulk_load(pp.ring + static_cast<size_t>(slot) * pp.chunk_rows * 32, src, pp.chunk_bytes,
-            &pp.full[slot]);
-  ++pp.issued;
-  if (++pp.prod_chunk == pp.chunks_per_block) {
-    pp.prod_chunk = 0;
-    if (++pp.prod_blk == blocks_in_item(k, pp.prod_item)) {
-      pp.prod_blk = 0;
-      pp.prod_item += gridDim.x;
+// Thread 0: the next chunk of the CTA's item sequence into ring slot `slot`.
+__device__ __forceinline__ void issue_next(const KParams& k, const Pipe& pp, int slot) {
+  ProdState& ps = s_prod;
+  const int c = static_cast<int>(ps.item / k.n_tile_groups);
+  const int b = c * k.chain + ps.blk;
+  const uint32_t bytes = static_cast<uint32_t>(pp.chunk_rows) * 512u;
+  const float4* src = k.blocks + (static_cast<size_t>(b) * (k.ppl / 2) +
+                                  static_cast<size_t>(ps.chunk) * pp.chunk_rows) * 32;
+  mbar_arrive_expect_tx(pp.full + 8u * slot, bytes);
+  bulk_load(pp.ring + static_cast<size_t>(slot) * pp.chunk_rows * 32, src, bytes,
+            pp.full + 8u * slot);
+  ++ps.issued;
+  if (++ps.chunk == pp.chunks_per_block) {
+    ps.chunk = 0;
+    if (++ps.blk == blocks_in_item(k, ps.item)) {
+      ps.blk = 0;
+      ps.item += gridDim.x;
     }
   }
 }
@@ -618,6 +627,178 @@ __device__ __forceinline__ void rows_levels(WalkT* w, const float4* rowp, int r,
   }
 }
 
+// ------------------------------------------------------- precision guard
+// A model of the float walk's rounding (measured against the oracle on
+// GB300, 640 loops of 2048 points, flux tubes F = 10..100, lambda = 0.1..1,
+// T up to 20): a loop's phase is off by a random amount of rms
+// c_ph * (sum of |segment phases|) / sqrt(N), c_ph <= 1.9e-7, and its spin by
+// a relative 3.6e-8 at most (systematic: the float scale sqrt(T) and the
+// approximate reciprocals) plus a random part that averages over the loops.
+// The model takes c_ph = 2e-7 and a spin error beta |spin|, beta = 5e-8,
+// counted as systematic.  The sum of
+// |segment phases| of a loop in block b at radius rho is at most
+// calF sqrt(T) L_b h, L_b the block's longest unit loop and h the largest
+// rho/(lambda^2 + rho^2) over the block's reach, 1/(2 lambda) if the block
+// comes within lambda of the axis.  Loops below kGuardFloor have cosh(spin)
+// < 3.77 and are not recorded; the model counts them in bulk.
+constexpr float kGuardFloor = 2.0f;
+constexpr float kCoshFloor = 3.76219569f;   // cosh(2)
+constexpr float kGuardBeta = 5e-8f;
+constexpr float kGuardCph = 2e-7f;
+constexpr float kGuardBudget = 0.5e-6f;     // half of the 1e-6 bar
+constexpr float kGuardSigmas = 2.0f;        // random part counted at 2 sigma
+
+struct GuardScratch {
+  float* bmax;   // [bpg][P]: the block's largest |spin|, -1 below the floor
+  float* s;      // [bpg][P][32]: |spin|, then the loop's systematic error share
+  float* sn;     // [bpg][P][32]: sin(phase), then the loop's random error share
+  double* f1;    // [bpg][P][32]: the float W_ferm - 1
+  int* sel;      // [kGuardSel]: selected (block << 5 | lane)
+  __device__ GuardScratch(char* base, int bpg, int P) {
+    const int recs = bpg * P;
+    bmax = reinterpret_cast<float*>(base);
+    s = reinterpret_cast<float*>(base + (recs * 4 + 15) / 16 * 16);
+    sn = s + recs * 32;
+    f1 = reinterpret_cast<double*>(sn + recs * 32);
+    sel = reinterpret_cast<int*>(f1 + recs * 32);
+  }
+};
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Bound on a loop's random phase error (rms) in block b at radius rho.
+__device__ __forceinline__ float guard_sigma(const KParams& k, int b, float sT, float rho,
+                                             float calF, float l2, float lam, float inv_sqrtN) {
+  const float gap = fmaxf(0.0f, rho - sT * k.stats[b].y);
+  const float h = gap >= lam ? gap / (l2 + gap * gap) : 0.5f / lam;
+  return kGuardCph * calF * sT * k.maxlen[b] * h * inv_sqrtN;
+}
+
+// End of a group for the warp's tile: per radius, the error estimate of the
+// group's spinor sum against the budget 0.5e-6 max(lpg, sum of cosh(spin)),
+// all quantities relative to cosh of the group's largest spin; while it is
+// over, select the recorded loop with the largest share (ties: lowest block,
+// then lane).  If kGuardSel loops bring it under the budget they are queued;
+// if not (the error is spread over many loops of similar spin, as in fields
+// nearly constant across the loops) nothing is, and the group is counted as
+// saturated.  Every lane takes part; the order is fixed.
+template <int P>
+__device__ __forceinline__ void guard_select(const KParams& k, char* scr, const Tile& tile,
+                                             const ProfileDev& prof, int t_index, int c, int g,
+                                             int lane) {
+  const GuardBufs& G = k.guard;
+  const int bpg = G.bpg;
+  GuardScratch R(scr, bpg, P);
+  __syncwarp();
+  const float sT = sqrtf(static_cast<float>(tile.T));
+  const float calF = static_cast<float>(6.283185307179586 * prof.turns_per);
+  const float l2 = static_cast<float>(prof.l2), lam = sqrtf(l2);
+  const float inv_sqrtN = rsqrtf(static_cast<float>(k.ppl));
+  for (int p = 0; p < tile.n_valid; ++p) {
+    float smax = -1.0f;
+    for (int bi = 0; bi < bpg; ++bi) smax = fmaxf(smax, R.bmax[bi * P + p]);
+    if (smax < kGuardFloor) continue;
+    const float rho = static_cast<float>(k.rho[tile.rho0 + p]);
+    const float e2m = __expf(-2.0f * smax);
+    const float inv = 2.0f * __expf(-smax) / (1.0f + e2m);   // 1 / cosh(smax)
+    float csum = 0.0f, sys = 0.0f, rnd2 = 0.0f, sig_nc = 0.0f;
+    int n_nc = 0;
+    for (int bi = 0; bi < bpg; ++bi) {
+      const float sig = guard_sigma(k, g * bpg + bi, sT, rho, calF, l2, lam, inv_sqrtN);
+      if (R.bmax[bi * P + p] < kGuardFloor) {
+        n_nc += 32;
+        sig_nc = fmaxf(sig_nc, sig);
+        continue;
+      }
+      const int r = (bi * P + p) * 32 + lane;
+      const float sp = R.s[r], sn = R.sn[r];
+      // cosh(sp) / cosh(smax), sp <= smax
+      const float w = __expf(sp - smax) * (1.0f + __expf(-2.0f * sp)) / (1.0f + e2m);
+      const float es = w * kGuardBeta * sp, er = w * fabsf(sn) * sig;
+      csum += w;
+      sys += es;
+      rnd2 += er * er;
+      R.s[r] = es;    // the shares replace the inputs
+      R.sn[r] = er;
+    }
+    csum = warp_sum_f(csum);
+    sys = warp_sum_f(sys);
+    rnd2 = warp_sum_f(rnd2);
+    const float nc = static_cast<float>(n_nc);
+    csum += nc * inv;
+    sys += nc * kCoshFloor * inv * kGuardBeta * kGuardFloor;
+    rnd2 += nc * (kCoshFloor * inv * sig_nc) * (kCoshFloor * inv * sig_nc);
+    const float budget = kGuardBudget * fmaxf(static_cast<float>(k.lpg) * inv, csum);
+    int n = 0;
+    uint64_t taken = 0;   // this lane's loop, blocks already selected
+    while ((G.all || sys + kGuardSigmas * sqrtf(fmaxf(rnd2, 0.0f)) > budget) && n < kGuardSel) {
+      float best = -1.0f;
+      int bbi = 0;
+      for (int bi = 0; bi < bpg; ++bi) {
+        if (R.bmax[bi * P + p] < kGuardFloor || ((taken >> bi) & 1)) continue;
+        const int r = (bi * P + p) * 32 + lane;
+        const float key = R.s[r] + kGuardSigmas * R.sn[r];
+        if (key > best) { best = key; bbi = bi; }
+      }
+      // warp argmax of (key, -(block, lane)): keys are >= 0 or -1 (none)
+      uint64_t v = best < 0.0f ? 0ull
+                               : (static_cast<uint64_t>(__float_as_uint(best) + 1u) << 32) |
+                                     (0xFFFFFFFFu - static_cast<uint32_t>(bbi * 32 + lane));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+      }
+      if ((v >> 32) == 0ull || (!G.all && (v >> 32) == 1ull)) break;   // none left / zero shares
+      const int idx = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(v & 0xFFFFFFFFull));
+      const int wbi = idx >> 5, wl = idx & 31;
+      if (lane == wl) taken |= 1ull << wbi;
+      const int r = (wbi * P + p) * 32 + wl;
+      sys -= R.s[r];
+      rnd2 -= R.sn[r] * R.sn[r];
+      if (lane == 0) R.sel[n] = idx;
+      ++n;
+    }
+    if (!G.all && sys + kGuardSigmas * sqrtf(fmaxf(rnd2, 0.0f)) > budget) {
+      if (lane == 0) atomicAdd(&G.counters[3], 1);
+      n = 0;
+    }
+    if (n == 0) continue;
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&G.counters[0], n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const bool fits = static_cast<int64_t>(base) + n <= G.cap;
+    for (int j = lane; j < n; j += 32) {
+      if (static_cast<int64_t>(base) + j >= G.cap) continue;
+      const int idx = R.sel[j], bi = idx >> 5, ln = idx & 31;
+      GuardItem it;
+      it.tile = fits ? t_index : -1;
+      it.p_loop = (p << 24) | ((g * bpg + bi) * 32 + ln);
+      it.f1 = R.f1[(bi * P + p) * 32 + ln];
+      G.items[base + j] = it;
+    }
+    if (lane == 0) {
+      if (fits) {
+        const int si = atomicAdd(&G.counters[1], 1);
+        GuardSlot sl;
+        sl.dst = tile.part_base +
+                 (static_cast<int64_t>(c + g) * tile.part_stride + tile.p0 + p) * kComps;
+        sl.item0 = base;
+        sl.n = n;
+        G.slots[si] = sl;
+      } else {
+        atomicAdd(&G.counters[2], 1);   // counted; these loops keep float precision
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Per-lane W terms are added into the warp's shared-memory accumulators
 // acc[j][lane] (j = radius * K + component, rows padded to 33 doubles); a
 // flush sums each row over the lanes in lane order and writes the partial
@@ -626,11 +807,22 @@ __device__ __forceinline__ void rows_levels(WalkT* w, const float4* rowp, int r,
 // the even points and the points 0 mod 4; kModeLoops writes every loop's
 // W - 1 to global memory instead of accumulating (lanes store 32
 // consecutive loops).
+// The tile and profile are read where they are needed rather than held in
+// registers across the walk (the row loop is register-bound).
 template <class A, int P, class WalkT, int MODE>
 __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const Tile& tile,
                          const ProfileDev& prof, bool active, volatile int* abort_flag,
-                         int lane) {
+                         int lane, int t_index) {
   using F = typename A::F;
+  // precision guard: FP32-compensated group sums of flux tubes
+  constexpr bool GUARD = std::is_same<A, F32Comp>::value && MODE == kModeSums;
+  const bool guard_tile = GUARD && k.guard.on && active && prof.kind == WLN_PROFILE_FLUX_TUBE;
+  // this warp's guard records (derived when used: no register across the walk)
+  auto gscr = [&]() {
+    return k.guard.scratch +
+           (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) *
+               k.guard.warp_bytes;
+  };
   constexpr bool LV = level_mode(MODE);
   constexpr bool NEST = MODE == kModeNested;
   constexpr bool PL = MODE == kModeLoops;
@@ -648,16 +840,21 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       w[q].rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
     }
   }
-  const double st_d = prof.spin_per * tile.T;
-  const F2 tp = split(prof.turns_per), st = split(st_d);
-  // sub-loop segments join points up to 4 apart
-  double rho_min = k.rho[tile.rho0];
-  for (int p = 1; p < tile.n_valid; ++p) rho_min = fmin(rho_min, k.rho[tile.rho0 + p]);
-  const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
-                    static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
-                    static_cast<float>(prof.l2)};
-  const bool la_ok =
-      A::kLowAngle && k.low_angle && prof.kind == WLN_PROFILE_FLUX_TUBE && tile.n_valid > 0;
+  // the spin's scale T spin_per and the phase's turns per unit sum, as
+  // double and double-float, formed where W is formed
+  auto st_d = [&]() { return prof.spin_per * tile.T; };
+  // the form of theta for block b (the same on every lane), from the block's
+  // statistics; sub-loop segments join points up to 4 apart
+  auto block_form = [&](int b) {
+    if (!(A::kLowAngle && k.low_angle && prof.kind == WLN_PROFILE_FLUX_TUBE && tile.n_valid > 0))
+      return 0;
+    double rho_min = k.rho[tile.rho0];
+    for (int p = 1; p < tile.n_valid; ++p) rho_min = fmin(rho_min, k.rho[tile.rho0 + p]);
+    const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
+                      static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
+                      static_cast<float>(prof.l2)};
+    return min(la.block(k, b), k.low_angle);
+  };
   const int b0 = c * k.chain;
   const int b1 = min(b0 + k.chain, k.n_blocks);
   int g_cur = (b0 * 32) / k.lpg;
@@ -685,7 +882,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   for (int b = b0; b < b1; ++b) {
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
-    const int form = la_ok ? min(la.block(k, b), k.low_angle) : 0;   // the same on every lane
+    const int form = block_form(b);
     // first point of each walk, for the closing segments
     float fx[NW], fy[NW];
 #pragma unroll
@@ -695,7 +892,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       const uint32_t parity = static_cast<uint32_t>((pp.kc / pp.stages) & 1);
       // every lane of the warp takes the same decision (the warp's
       // shuffles and syncs need all 32 lanes)
-      if (!__all_sync(0xffffffffu, mbar_wait(&pp.full[slot], parity))) {
+      if (!__all_sync(0xffffffffu, mbar_wait(pp.full + 8u * slot, parity))) {
         if (lane == 0) atomicExch(k.flag, kErrTimeoutFull);
         *abort_flag = 1;
         return false;
@@ -757,10 +954,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&pp.empty[slot]);
-      if (threadIdx.x == 0 && pp.issued < pp.total) {
+      if (lane == 0) mbar_arrive(pp.empty + 8u * slot);
+      if (threadIdx.x == 0 && s_prod.issued < s_prod.total) {
         // The slot just released is the next one to refill.
-        if (!mbar_wait(&pp.empty[slot], parity)) {
+        if (!mbar_wait(pp.empty + 8u * slot, parity)) {
           atomicExch(k.flag, kErrTimeoutEmpty);
           *abort_flag = 1;
         } else {
@@ -783,7 +980,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
           if (p < tile.n_valid) {
             double ps, pc, ss, sc, t[kComps];
             w[0].raw(p, ps, pc, ss, sc);
-            wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, t);
+            wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_d()), prof.turns_per,
+                            st_d(), t);
             // evict-first store: the results stream past L2 without pushing
             // out the loop chain the CTAs are sweeping
             __stcs(reinterpret_cast<double2*>(k.loops_out) +
@@ -798,17 +996,41 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const int g_lo = (b * 32) / k.lpg;
     const int g_hi = min(b * 32 + 31, k.n_loops - 1) / k.lpg;
     for (int g = g_lo; g <= g_hi; ++g) {
-      if (g != g_cur) { flush(g_cur); g_cur = g; }
+      if (g != g_cur) {
+        if constexpr (GUARD) {
+          if (guard_tile) guard_select<P>(k, gscr(), tile, prof, t_index, c, g_cur, lane);
+        }
+        flush(g_cur);
+        g_cur = g;
+      }
       const bool mine = g_lane == g;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         if constexpr (!LV) {
           double ps, pc, ss, sc, t[K];
+          float sabs = 0.0f;
           w[0].raw(p, ps, pc, ss, sc);
-          wilson_terms<A>(ps, pc, ss, sc, tp, st, prof.turns_per, st_d, t);
+          wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_d()), prof.turns_per,
+                          st_d(), t, &sabs);
 #pragma unroll
           for (int q = 0; q < K; ++q)
             if (mine) acc[(p * K + q) * 33 + lane] += t[q];
+          if constexpr (GUARD) {
+            // the block's largest spin; above the floor, every loop's spin,
+            // sin(phase) and float W_ferm - 1 for the group-end selection
+            if (guard_tile && p < tile.n_valid) {
+              const float sv = valid ? sabs : 0.0f;
+              const float bm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(sv)));
+              GuardScratch R(gscr(), k.guard.bpg, P);
+              const int idx = (b - g * k.guard.bpg) * P + p;
+              if (bm >= kGuardFloor) {
+                R.s[idx * 32 + lane] = sv;
+                R.sn[idx * 32 + lane] = static_cast<float>(t[2]);
+                R.f1[idx * 32 + lane] = t[1];
+              }
+              if (lane == 0) R.bmax[idx] = bm >= kGuardFloor ? bm : -1.0f;
+            }
+          }
         } else {
           // Spin per segment is T/N' on a sub-loop of N' points: the circle's
           // sums count twice, the square's and triangle's four times, of the
@@ -834,7 +1056,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
               sp = L == 0 ? 0.5 * so + 0.25 * (sq + stt) : (L == 1 ? so : 0.5 * (sq + stt));
             }
             double t[2];
-            level_terms<A>(ph, sp, tp, st, prof.turns_per, st_d, t);
+            level_terms<A>(ph, sp, split(prof.turns_per), split(st_d()), prof.turns_per, st_d(),
+                           t);
             if (mine) {
               acc[(p * K + 2 * L) * 33 + lane] += t[0];
               acc[(p * K + 2 * L + 1) * 33 + lane] += t[1];
@@ -843,6 +1066,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
         }
       }
     }
+  }
+  if constexpr (GUARD) {
+    if (guard_tile) guard_select<P>(k, gscr(), tile, prof, t_index, c, g_cur, lane);
   }
   flush(g_cur);
   return true;
@@ -868,56 +1094,58 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Pipe pp;
-  pp.rows_per_block = k.ppl / 2;
-  pp.chunk_rows = k.rows < pp.rows_per_block ? k.rows : pp.rows_per_block;
-  pp.chunks_per_block = pp.rows_per_block / pp.chunk_rows;
-  pp.chunk_bytes = static_cast<uint32_t>(pp.chunk_rows) * 512u;
+  const int rows_per_block = k.ppl / 2;
+  pp.chunk_rows = k.rows < rows_per_block ? k.rows : rows_per_block;
+  pp.chunks_per_block = rows_per_block / pp.chunk_rows;
   pp.stages = k.stages;
   pp.ring = reinterpret_cast<float4*>(smem);
   const size_t ring_bytes = static_cast<size_t>(k.stages) * pp.chunk_rows * 512;
   double* acc = reinterpret_cast<double*>(smem + ring_bytes) + warp * (P * K * 33);
-  pp.full = reinterpret_cast<uint64_t*>(smem + ring_bytes + WARPS * P * K * 33 * sizeof(double));
-  pp.empty = pp.full + k.stages;
+  pp.full = smem_u32(smem + ring_bytes + WARPS * P * K * 33 * sizeof(double));
+  pp.empty = pp.full + 8u * k.stages;
   for (int j = 0; j < P * K; ++j) acc[j * 33 + lane] = 0.0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < k.stages; ++s) {
-      mbar_init(&pp.full[s], 1);
-      mbar_init(&pp.empty[s], WARPS);
+      mbar_init(pp.full + 8u * s, 1);
+      mbar_init(pp.empty + 8u * s, WARPS);
     }
     abort_flag = 0;
+    int32_t total = 0;
+    for (int64_t it = blockIdx.x; it < k.n_items; it += gridDim.x)
+      total += blocks_in_item(k, it) * pp.chunks_per_block;
+    s_prod.issued = 0;
+    s_prod.total = total;
+    s_prod.item = blockIdx.x;
+    s_prod.blk = 0;
+    s_prod.chunk = 0;
     fence_mbar_init();
+    for (int s = 0; s < k.stages && s_prod.issued < s_prod.total; ++s) issue_next(k, pp, s);
   }
   __syncthreads();
-
-  for (int64_t it = blockIdx.x; it < k.n_items; it += gridDim.x)
-    pp.total += blocks_in_item(k, it) * pp.chunks_per_block;
-  pp.prod_item = blockIdx.x;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < k.stages && pp.issued < pp.total; ++s) issue_next(k, pp, s);
-  }
 
   bool ok = true;
   for (int64_t item = blockIdx.x; item < k.n_items && ok; item += gridDim.x) {
     const int c = static_cast<int>(item / k.n_tile_groups);
     const int tg = static_cast<int>(item % k.n_tile_groups);
     const int t = tg * WARPS + warp;
-    const Tile tile = k.tiles[t < k.n_tiles ? t : 0];
+    const Tile& tile = k.tiles[t < k.n_tiles ? t : 0];
     const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
-    const ProfileDev prof = k.profs[tile.profile];
+    const ProfileDev& prof = k.profs[tile.profile];
     // three walks per radius: Q fits in registers for up to 3 radii per lane
     constexpr bool CQ = !level_mode(MODE) || P <= 3;
     if (prof.kind == WLN_PROFILE_CONST_B)
-      ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane);
+      ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane,
+                                             t);
     else
       ok = run_item<A, P, Walk<A, P, CQ>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag,
-                                                lane);
+                                                lane, t);
   }
 
   if (!ok && threadIdx.x == 0) {
     // Let copies already in flight land before the CTA's shared memory goes away.
-    for (int32_t q = pp.kc; q < pp.issued; ++q)
-      (void)mbar_wait(&pp.full[q % pp.stages], static_cast<uint32_t>((q / pp.stages) & 1));
+    for (int32_t q = pp.kc; q < s_prod.issued; ++q)
+      (void)mbar_wait(pp.full + 8u * (q % pp.stages), static_cast<uint32_t>((q / pp.stages) & 1));
   }
 }
 
@@ -927,11 +1155,12 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
 __global__ void selftest_wait_kernel(int* flag, uint64_t limit_ns) {
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(smem_u32(&bar), 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(flag, kErrTimeoutSelfTest);
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, limit_ns))
+    atomicExch(flag, kErrTimeoutSelfTest);
 }
 
 // Sum the partials of each group over its chains, in chain order.
@@ -995,7 +1224,7 @@ int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode) {
 }
 
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
-                     int mode) {
+                     int mode, int guard_bpg) {
   WilsonPlan p{};
   p.P = plan_points_per_lane(ctx, prec, mode);
   p.mode = mode;
@@ -1029,6 +1258,8 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
     while (chain > 1 && chain * block_bytes > (int64_t(16) << 20)) chain = (chain + 1) / 2;
     p.chain = chain;
   }
+  // the precision guard sees whole groups in one item
+  if (guard_bpg > 0) p.chain = p.chain < guard_bpg ? guard_bpg : p.chain / guard_bpg * guard_bpg;
   p.n_chains = (e.n_blocks + p.chain - 1) / p.chain;
   p.n_items = static_cast<int64_t>(p.n_chains) * p.n_tile_groups;
   return p;
@@ -1040,7 +1271,7 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
                        const Tile* tiles, const ProfileDev* profs, const double* rho,
                        int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                        double* partial, int64_t n_points, int* d_flag, int64_t* launches,
-                       double* loops_out) {
+                       double* loops_out, const GuardBufs* guard, int* grid_out = nullptr) {
   WilsonPlan plan = plan_in;
   KParams kp{};
   kp.loops_out = loops_out;
@@ -1051,7 +1282,9 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
   kp.n_tile_groups = plan.n_tile_groups; kp.n_chains = plan.n_chains; kp.n_items = plan.n_items;
   kp.flag = d_flag;
   kp.stats = e.stats;
+  kp.maxlen = e.maxlen;
   kp.low_angle = plan.low_angle;
+  if (guard) kp.guard = *guard;
   const size_t smem = smem_bytes(plan, e.ppl);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1061,6 +1294,7 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
     const int occ = occupancy<A, P_, W_, M_>(smem);                                  \
     const int64_t g = static_cast<int64_t>(sms) * occ;                               \
     const int grid = static_cast<int>(g < plan.n_items ? g : plan.n_items);          \
+    if (grid_out) { *grid_out = grid; return cudaSuccess; }                          \
     ++*launches;                                                                     \
     return launch_t<A, P_, W_, M_>(s, kp, grid, smem);                               \
   }
@@ -1117,9 +1351,19 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
 cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
-                          double* partial, int64_t n_points, int* d_flag, int64_t* launches) {
+                          double* partial, int64_t n_points, int* d_flag, int64_t* launches,
+                          const GuardBufs* guard) {
   return launch_any(s, plan, e, tiles, profs, rho, n_groups, loops_per_group, prec, partial,
-                    n_points, d_flag, launches, nullptr);
+                    n_points, d_flag, launches, nullptr, guard);
+}
+
+int wilson_grid(const WilsonPlan& plan, const Ensemble& e, wln_prec prec) {
+  int grid = 0;
+  int64_t none = 0;
+  if (launch_any(nullptr, plan, e, nullptr, nullptr, nullptr, 1, e.n_loops, prec, nullptr, 0,
+                 nullptr, &none, nullptr, nullptr, &grid) != cudaSuccess)
+    return 0;
+  return grid;
 }
 
 cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
@@ -1127,7 +1371,7 @@ cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const En
                                 wln_prec prec, double* out, int* d_flag, int64_t* launches) {
   // groups play no part; lpg = n_loops keeps the group arithmetic in range
   return launch_any(s, plan, e, tiles, profs, rho, 1, e.n_loops, prec, nullptr, 0, d_flag,
-                    launches, out);
+                    launches, out, nullptr);
 }
 
 cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns) {

@@ -46,6 +46,9 @@ SIGNATURES = {
     "wln_ensemble_info": ([_P, _P, _P, _P], ctypes.c_int),
     "wln_loops_copy": ([_P, _P, _P, _P], ctypes.c_int),
     "wln_set_low_angle": ([_P, ctypes.c_int32], ctypes.c_int),
+    "wln_set_precision_guard": ([_P, _I32], ctypes.c_int),
+    "wln_precision_guard_stats": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                   ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I32], ctypes.c_int),
     "wln_philox_stream": ([_P, _U64, _I64, _I32, _I32, _P], ctypes.c_int),
     "wln_wilson_avg": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
     "wln_wilson_avg_noalloc": ([_P, _P, _P, _I32, _P, _P, _P, _P, _I32, ctypes.c_int, _P],
@@ -254,6 +257,24 @@ class Context:
                    stages: int = 0, chain_blocks: int = 0):
         self._check(load().wln_set_tuning(self.handle, points_per_lane, warps, rows, stages,
                                           chain_blocks))
+
+    def set_precision_guard(self, enabled=True):
+        """The precision guard of the FP32-compensated group sums (on by
+        default): loops whose float rounding would move a spinor group mean by
+        more than half of 1e-6 max(1, <cosh spin>) are recomputed in
+        double-float.  enabled="all" recomputes every recorded loop (a check
+        of the double-float walk)."""
+        mode = 2 if enabled == "all" else int(bool(enabled))
+        self._check(load().wln_set_precision_guard(self.handle, mode))
+
+    def precision_guard_stats(self, reset: bool = False) -> dict:
+        """Running totals of the guard: loops recomputed, launches, queue
+        overflows, selections that stopped at 64 loops."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        self._check(load().wln_precision_guard_stats(self.handle, *[ctypes.byref(x) for x in v],
+                                                     int(bool(reset))))
+        return dict(zip(("escalated_loops", "launches", "overflows", "saturated"),
+                        (x.value for x in v)))
 
     def set_low_angle(self, level: int = 2):
         """The cheaper forms of theta later float walks may take on blocks
