@@ -564,6 +564,7 @@ def main():
     wk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     launches0 = ctx.launch_count
+    ctx.precision_guard_stats(reset=True)
     _barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk, torch.cuda.stream(stream):
@@ -587,6 +588,7 @@ def main():
     torch.cuda.synchronize()
     _barrier(ws)
     launches = ctx.launch_count - launches0
+    guard = ctx.precision_guard_stats(reset=True)
     ms = e0.elapsed_time(e1) / args.steps
     ms = _max_over_ranks(ms, ws)
     wilson_ms = statistics.mean(a.elapsed_time(b) for a, b in wk)
@@ -661,6 +663,13 @@ def main():
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        # loops the precision guard recomputed in double-float (per step), as a
+        # fraction of the step's loop-point evaluations
+        "precision_guard": {
+            "escalated_loops_per_step": guard["escalated_loops"] / args.steps,
+            "fraction_of_loop_points": guard["escalated_loops"] / args.steps / loop_points,
+            "saturated_per_step": guard["saturated"] / args.steps,
+            "overflows": guard["overflows"]} if args.prec == "fp32" else None,
     }
     if wl.meta.get("quad"):
         # the step's physics: spinor effective action per flux tube, mean +- group

@@ -370,8 +370,10 @@ wln_status wln_create(wln_ctx** out, int device, void* cuda_stream) {
   // the device error flag and the precision guard's running totals
   err = cudaMalloc(&ctx->d_flag, 64);
   if (err == cudaSuccess) err = cudaMemset(ctx->d_flag, 0, 64);
-  if (err == cudaSuccess)
+  if (err == cudaSuccess) {
     ctx->d_guard_totals = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->d_flag) + 8);
+    ctx->d_items = reinterpret_cast<int*>(reinterpret_cast<char*>(ctx->d_flag) + 48);
+  }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
@@ -675,7 +677,7 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   if (per_loop) {
     err = launch_wilson_loops(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
                               at<ProfileDev>(d, o_profs), at<double>(d, o_rho), prec,
-                              static_cast<double*>(out.dev), ctx->d_flag, &launches);
+                              static_cast<double*>(out.dev), ctx->d_flag, &launches, ctx->d_items);
     ctx->launches += launches;
     if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
   } else {
@@ -689,7 +691,7 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
     err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
                         at<ProfileDev>(d, o_profs), at<double>(d, o_rho), n_groups, lpg, prec,
                         at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches,
-                        use_guard ? &gb : nullptr);
+                        use_guard ? &gb : nullptr, ctx->d_items);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
     if (use_guard) {
       err = launch_guard(ctx->stream, gb, ens->e, at<Tile>(d, o_tiles), at<ProfileDev>(d, o_profs),

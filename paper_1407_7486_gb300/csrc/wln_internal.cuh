@@ -164,6 +164,7 @@ struct wln_ctx {
   int guard = 1;        // precision guard of the FP32-compensated group sums (2: every
                         // recorded loop, a check of the double-float walk)
   unsigned long long* d_guard_totals = nullptr;   // escalated loops, overflows, saturated, launches
+  int* d_items = nullptr;   // a Wilson launch's item counter (dynamic schedule), zeroed per launch
 };
 
 struct wln_ensemble {
@@ -214,7 +215,11 @@ cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, 
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);
 
-// Wilson loops (wln_wilson.cu).  guard_bpg > 0 aligns the chains of blocks to
+// Wilson loops (wln_wilson.cu).  A launch given an item counter (device int,
+// zeroed by the launch on its stream) schedules items dynamically: each CTA
+// starts with its own index and claims the next free item when it starts
+// staging one, so CTAs that finish early take more (results do not depend
+// on which CTA walks an item).  guard_bpg > 0 aligns the chains of blocks to
 // groups of that many blocks, as the precision guard needs.
 WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_prec prec,
                      int mode = kModeSums, int guard_bpg = 0);
@@ -225,7 +230,7 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                           double* partial, int64_t n_points, int* d_flag, int64_t* launches,
-                          const GuardBufs* guard = nullptr);
+                          const GuardBufs* guard = nullptr, int* item_counter = nullptr);
 
 // Precision guard (wln_guard.cu).  The blocks per group when the pass's
 // layout admits it (FP32-compensated group sums, groups of a whole number of
@@ -249,7 +254,8 @@ cudaError_t launch_guard(cudaStream_t s, const GuardBufs& g, const Ensemble& e,
 // Per-loop values: out[p][loop][2] = (W_scal - 1, W_ferm - 1), p the point.
 cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                                 const Tile* tiles, const ProfileDev* profs, const double* rho,
-                                wln_prec prec, double* out, int* d_flag, int64_t* launches);
+                                wln_prec prec, double* out, int* d_flag, int64_t* launches,
+                                int* item_counter = nullptr);
 // Group sums [n_points][G][WLN_K] of per-loop values [n_points][n_loops][2],
 // contiguous groups or (shuffle) a Fisher-Yates permutation per point;
 // perm: [n_points][n_loops] scratch (and output) for the shuffled order.

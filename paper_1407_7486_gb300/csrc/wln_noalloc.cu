@@ -233,7 +233,7 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
                         reinterpret_cast<const ProfileDev*>(d + o_pd),
                         reinterpret_cast<const double*>(d + o_rho), n_groups, lpg, prec,
                         reinterpret_cast<double*>(d + o_part), n_points, ctx->d_flag, &launches,
-                        use_guard ? &gb : nullptr);
+                        use_guard ? &gb : nullptr, ctx->d_items);
   if (err == cudaSuccess)
     err = launch_guard(s, gb, ens->e, reinterpret_cast<const Tile*>(d + o_tiles),
                        reinterpret_cast<const ProfileDev*>(d + o_pd),

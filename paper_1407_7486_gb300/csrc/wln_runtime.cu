@@ -51,6 +51,7 @@ struct wln_batch {
   int64_t kernels_per_run = 0;
   GuardBufs guard;            // precision guard (FP32 compensated, whole-block groups)
   int num_sms = 0;
+  int* items = nullptr;       // the Wilson launch's item counter (the creating context's)
 };
 
 namespace {
@@ -61,7 +62,7 @@ cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* laun
   if (err != cudaSuccess) return err;
   err = launch_wilson(s, b->plan, b->ens->e, b->tiles, b->profs, b->rho, b->n_groups, b->lpg,
                       b->prec, b->partial, b->n_points, flag, launches,
-                      b->guard.on ? &b->guard : nullptr);
+                      b->guard.on ? &b->guard : nullptr, b->items);
   if (err != cudaSuccess) return err;
   err = launch_guard(s, b->guard, b->ens->e, b->tiles, b->profs, b->rho, b->partial, b->num_sms,
                      launches);
@@ -148,6 +149,7 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
   b->plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, kModeSums, bpg);
   b->num_sms = ctx->num_sms;
+  b->items = ctx->d_items;
   std::vector<QuadProfile> qp;
   b->has_action = build_quad(profiles, n_profiles, rho_cm, rho_off, T, T_off, qp, nullptr);
 
@@ -570,7 +572,7 @@ wln_status launch_step(wln_server* sv, int slot) {
                         reinterpret_cast<ProfileDev*>(d + o_profs),
                         reinterpret_cast<double*>(d + o_rho), sv->G, sv->lpg, sv->prec,
                         reinterpret_cast<double*>(sv->arena), 0, sv->ctx->d_flag, &launches,
-                        gb.on ? &gb : nullptr);
+                        gb.on ? &gb : nullptr, sv->ctx->d_items);
   if (err == cudaSuccess)
     err = launch_guard(s, gb, sv->ens->e, reinterpret_cast<Tile*>(d + o_tiles),
                        reinterpret_cast<ProfileDev*>(d + o_profs),

@@ -256,6 +256,8 @@ struct KParams {
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
   const float2* stats;   // per block: longest segment, largest |y|
   const float* maxlen;   // per block: longest loop
+  int* item_counter;     // items claimed beyond the first wave (zeroed before the launch);
+                         // nullptr: the static round-robin schedule
   int32_t low_angle;     // highest form of theta a block may take (0: general everywhere)
   GuardBufs guard;       // precision guard (FP32 compensated group sums)
 };
@@ -518,9 +520,16 @@ struct Pipe {
 };
 
 struct ProdState {
-  int32_t issued, total, item, blk, chunk;
+  int32_t issued;     // chunks issued
+  int32_t blk, chunk; // position within the current item
+  int64_t item;       // the item being issued
+  int32_t started, done;
 };
 __shared__ ProdState s_prod;
+// The item of each staged chunk, or -1 once the items are exhausted (written
+// by thread 0 before the chunk's barrier completes, read by the warps after).
+constexpr int kMaxStages = 8;
+__shared__ int32_t s_chunk_item[kMaxStages];
 
 __device__ __forceinline__ int blocks_in_item(const KParams& k, int64_t item) {
   const int c = static_cast<int>(item / k.n_tile_groups);
@@ -528,9 +537,33 @@ __device__ __forceinline__ int blocks_in_item(const KParams& k, int64_t item) {
   return min(b0 + k.chain, k.n_blocks) - b0;
 }
 
-// Thread 0: the next chunk of the CTA's item sequence into ring slot `slot`.
+// Thread 0: the next chunk of the CTA's items into ring slot `slot`.  The
+// first item of a CTA is its block index; later items are claimed one at a
+// time from the launch's counter when their first chunk is issued (dynamic
+// schedule: CTAs that finish early take more), or taken round-robin without
+// a counter.  Past the last item the slot gets the sentinel -1 and its full
+// barrier completes without a copy, so every warp's wait ends.
 __device__ __forceinline__ void issue_next(const KParams& k, const Pipe& pp, int slot) {
   ProdState& ps = s_prod;
+  if (ps.blk == 0 && ps.chunk == 0) {
+    int64_t item;
+    if (!ps.started) {
+      item = blockIdx.x;
+      ps.started = 1;
+    } else if (k.item_counter) {
+      item = static_cast<int64_t>(gridDim.x) + atomicAdd(k.item_counter, 1);
+    } else {
+      item = ps.item + gridDim.x;
+    }
+    ps.item = item;
+    if (item >= k.n_items) {
+      s_chunk_item[slot] = -1;
+      ps.done = 1;
+      mbar_arrive(pp.full + 8u * slot);
+      return;
+    }
+  }
+  s_chunk_item[slot] = static_cast<int32_t>(ps.item);
   const int c = static_cast<int>(ps.item / k.n_tile_groups);
   const int b = c * k.chain + ps.blk;
   const uint32_t bytes = static_cast<uint32_t>(pp.chunk_rows) * 512u;
@@ -542,10 +575,7 @@ __device__ __forceinline__ void issue_next(const KParams& k, const Pipe& pp, int
   ++ps.issued;
   if (++ps.chunk == pp.chunks_per_block) {
     ps.chunk = 0;
-    if (++ps.blk == blocks_in_item(k, ps.item)) {
-      ps.blk = 0;
-      ps.item += gridDim.x;
-    }
+    if (++ps.blk == blocks_in_item(k, ps.item)) ps.blk = 0;
   }
 }
 
@@ -955,7 +985,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(pp.empty + 8u * slot);
-      if (threadIdx.x == 0 && s_prod.issued < s_prod.total) {
+      if (threadIdx.x == 0 && !s_prod.done) {
         // The slot just released is the next one to refill.
         if (!mbar_wait(pp.empty + 8u * slot, parity)) {
           atomicExch(k.flag, kErrTimeoutEmpty);
@@ -1111,21 +1141,32 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
       mbar_init(pp.empty + 8u * s, WARPS);
     }
     abort_flag = 0;
-    int32_t total = 0;
-    for (int64_t it = blockIdx.x; it < k.n_items; it += gridDim.x)
-      total += blocks_in_item(k, it) * pp.chunks_per_block;
     s_prod.issued = 0;
-    s_prod.total = total;
-    s_prod.item = blockIdx.x;
     s_prod.blk = 0;
     s_prod.chunk = 0;
+    s_prod.item = 0;
+    s_prod.started = 0;
+    s_prod.done = 0;
     fence_mbar_init();
-    for (int s = 0; s < k.stages && s_prod.issued < s_prod.total; ++s) issue_next(k, pp, s);
+    for (int s = 0; s < k.stages && !s_prod.done; ++s) issue_next(k, pp, s);
   }
   __syncthreads();
 
   bool ok = true;
-  for (int64_t item = blockIdx.x; item < k.n_items && ok; item += gridDim.x) {
+  while (ok) {
+    // the next item: the index thread 0 wrote with the chunk it staged first
+    {
+      const int slot = static_cast<int>(pp.kc % pp.stages);
+      const uint32_t parity = static_cast<uint32_t>((pp.kc / pp.stages) & 1);
+      if (!__all_sync(0xffffffffu, mbar_wait(pp.full + 8u * slot, parity))) {
+        if (lane == 0) atomicExch(k.flag, kErrTimeoutFull);
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+    }
+    const int64_t item = s_chunk_item[pp.kc % pp.stages];
+    if (item < 0) break;
     const int c = static_cast<int>(item / k.n_tile_groups);
     const int tg = static_cast<int>(item % k.n_tile_groups);
     const int t = tg * WARPS + warp;
@@ -1271,9 +1312,12 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
                        const Tile* tiles, const ProfileDev* profs, const double* rho,
                        int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                        double* partial, int64_t n_points, int* d_flag, int64_t* launches,
-                       double* loops_out, const GuardBufs* guard, int* grid_out = nullptr) {
+                       double* loops_out, const GuardBufs* guard, int* grid_out = nullptr,
+                       int* item_counter = nullptr) {
   WilsonPlan plan = plan_in;
+  if (plan.stages > kMaxStages) return cudaErrorInvalidConfiguration;
   KParams kp{};
+  kp.item_counter = item_counter;
   kp.loops_out = loops_out;
   kp.blocks = e.blocks; kp.n_blocks = e.n_blocks; kp.ppl = e.ppl; kp.n_loops = e.n_loops;
   kp.tiles = tiles; kp.n_tiles = plan.n_tiles; kp.profs = profs; kp.rho = rho;
@@ -1295,6 +1339,10 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
     const int64_t g = static_cast<int64_t>(sms) * occ;                               \
     const int grid = static_cast<int>(g < plan.n_items ? g : plan.n_items);          \
     if (grid_out) { *grid_out = grid; return cudaSuccess; }                          \
+    if (item_counter) {                                                              \
+      const cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(int), s);         \
+      if (e != cudaSuccess) return e;                                                \
+    }                                                                                \
     ++*launches;                                                                     \
     return launch_t<A, P_, W_, M_>(s, kp, grid, smem);                               \
   }
@@ -1352,9 +1400,9 @@ cudaError_t launch_wilson(cudaStream_t s, const WilsonPlan& plan, const Ensemble
                           const Tile* tiles, const ProfileDev* profs, const double* rho,
                           int32_t n_groups, int32_t loops_per_group, wln_prec prec,
                           double* partial, int64_t n_points, int* d_flag, int64_t* launches,
-                          const GuardBufs* guard) {
+                          const GuardBufs* guard, int* item_counter) {
   return launch_any(s, plan, e, tiles, profs, rho, n_groups, loops_per_group, prec, partial,
-                    n_points, d_flag, launches, nullptr, guard);
+                    n_points, d_flag, launches, nullptr, guard, nullptr, item_counter);
 }
 
 int wilson_grid(const WilsonPlan& plan, const Ensemble& e, wln_prec prec) {
@@ -1368,10 +1416,11 @@ int wilson_grid(const WilsonPlan& plan, const Ensemble& e, wln_prec prec) {
 
 cudaError_t launch_wilson_loops(cudaStream_t s, const WilsonPlan& plan, const Ensemble& e,
                                 const Tile* tiles, const ProfileDev* profs, const double* rho,
-                                wln_prec prec, double* out, int* d_flag, int64_t* launches) {
+                                wln_prec prec, double* out, int* d_flag, int64_t* launches,
+                                int* item_counter) {
   // groups play no part; lpg = n_loops keeps the group arithmetic in range
   return launch_any(s, plan, e, tiles, profs, rho, 1, e.n_loops, prec, nullptr, 0, d_flag,
-                    launches, out, nullptr);
+                    launches, out, nullptr, nullptr, item_counter);
 }
 
 cudaError_t launch_selftest_wait(cudaStream_t s, int* d_flag, uint64_t limit_ns) {
