@@ -509,6 +509,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="replay the seed-7 Poisson request stream against the serving ensemble")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=6,
+                    help="requests of the bounded serving block in the default line (0: none)")
     ap.add_argument("--rate-scales", default="sat",
                     help="comma list: 'sat' (2000 req/s) and/or fractions of measured capacity")
     ap.add_argument("--correlation", action="store_true",
@@ -720,6 +722,8 @@ def main():
                             # Wilson kernel rates, FP32 compensated over FP64
                             "fp32_over_fp64_rate": (wl.loop_points / (wilson_ms / 1e3)) / (n_lp / f64_s)}
         ens.free()
+    if ws == 1 and args.serve_requests > 0 and args.workload == "paper":
+        line["serve"] = serve_block(ctx, args.prec, args.serve_requests)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl, ctx)
         pc = precision_corners(wl, ctx)
@@ -1127,22 +1131,15 @@ def run_sweep(args):
     print(json.dumps(line))
 
 
-def run_serve(args):
-    """Continuous batching: replay the seed-7 Poisson stream (2000 req/s) of
-    single-profile queries against the serving ensemble (32768 x 4096); each
-    request's latency runs from its arrival to its results on the host."""
-    import torch
-    from paper_1407_7486_gb300 import build, wln
-    build.build()
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(0)
-    ctx = wln.Context(0, stream)
-    cfg = I.serving_ensemble()
-    ens = ctx.gen_loops(cfg["seed"], cfg["n_loops"], cfg["ppl"])
-    reqs = I.request_stream(args.requests)
+def _serve_replay(ctx, ens, cfg, reqs, scales, prec):
+    """Replay `reqs` through a continuous-batching server at each arrival-rate
+    scale ('sat': the stream's own 2000 req/s; a number: that fraction of the
+    capacity measured by the saturated run).  Latency runs from a request's
+    arrival to its results on the host.  Returns (runs, capacity req/s)."""
+    from paper_1407_7486_gb300 import wln
     runs = []
     capacity = None
-    for scale in args.rate_scales.split(","):
+    for scale in scales:
         if scale == "sat":
             times = [r.arrival_s for r in reqs]
             label = "2000 req/s (saturated)"
@@ -1152,7 +1149,7 @@ def run_serve(args):
             rate = float(scale) * capacity
             times = list(np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(reqs))))
             label = f"{scale} x capacity = {rate:.3f} req/s"
-        sv = wln.Server(ctx, ens, cfg["n_groups"], prec=args.prec, arena_bytes=16 << 30,
+        sv = wln.Server(ctx, ens, cfg["n_groups"], prec=prec, arena_bytes=16 << 30,
                         tile_groups_per_step=128)
         t0 = time.perf_counter()
         pending = list(range(len(reqs)))
@@ -1185,10 +1182,68 @@ def run_serve(args):
         thr = lp / makespan
         if scale == "sat":
             capacity = len(reqs) / makespan
-        runs.append({"rate": label, "p50_ms": float(np.percentile(lat, 50)),
+        runs.append({"rate": label, "requests": len(reqs),
+                     "p50_ms": float(np.percentile(lat, 50)),
                      "p99_ms": float(np.percentile(lat, 99)), "loop_point_evals_per_s": thr,
                      "makespan_s": makespan, "steps": sv.info()["steps"], "clocks": clk.summary()})
         sv.free()
+    return runs, capacity
+
+
+def _serve_oracle_check(ctx, ens, cfg, req, prec):
+    """One request through the server, its sums against the FP64 oracle on
+    sampled (point, group) pairs."""
+    from paper_1407_7486_gb300 import wln
+    sv = wln.Server(ctx, ens, cfg["n_groups"], prec=prec, arena_bytes=16 << 30,
+                    tile_groups_per_step=128)
+    rid = sv.submit(req.profile, req.rho, req.T)
+    for _ in range(100000):
+        sv.step()
+        state, res = sv.poll(rid)
+        if state == sv.DONE:
+            break
+    y32, _ = ctx.loops_copy(ens)
+    out = sampled_oracle_error(y32, [req.profile], [req.rho], [req.T], res[0], cfg["n_groups"])
+    sv.release(rid)
+    sv.free()
+    return out
+
+
+def serve_block(ctx, prec: str, n_requests: int):
+    """The bounded serving measurement carried by the default line: the
+    serving ensemble (32768 loops x 4096 points, 32 groups), the first
+    n_requests of the seed-7 Poisson stream, saturated and replayed at half the
+    measured capacity; p50/p99 latency of the half-capacity replay."""
+    cfg = I.serving_ensemble()
+    ens = ctx.gen_loops(cfg["seed"], cfg["n_loops"], cfg["ppl"])
+    reqs = I.request_stream(n_requests)
+    runs, capacity = _serve_replay(ctx, ens, cfg, reqs, ["sat", "0.5"], prec)
+    half = runs[-1]
+    block = {"workload": f"serving: {cfg['n_loops']} loops x {cfg['ppl']} ppl, G={cfg['n_groups']}, "
+                         f"first {len(reqs)} requests of the seed-7 Poisson stream (mean 2000 req/s)",
+             "p50_ms": half["p50_ms"], "p99_ms": half["p99_ms"], "rate": half["rate"],
+             "loop_point_evals_per_s": half["loop_point_evals_per_s"],
+             "capacity_req_per_s": capacity, "saturated": runs[0],
+             "gpu_error_vs_oracle_sampled": dict(_serve_oracle_check(ctx, ens, cfg, reqs[0], prec),
+                                                 request=0)}
+    ens.free()
+    return block
+
+
+def run_serve(args):
+    """Continuous batching: replay the seed-7 Poisson stream (2000 req/s) of
+    single-profile queries against the serving ensemble (32768 x 4096); each
+    request's latency runs from its arrival to its results on the host."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    cfg = I.serving_ensemble()
+    ens = ctx.gen_loops(cfg["seed"], cfg["n_loops"], cfg["ppl"])
+    reqs = I.request_stream(args.requests)
+    runs, capacity = _serve_replay(ctx, ens, cfg, reqs, args.rate_scales.split(","), args.prec)
     line = _common_line("serve p50/p99 latency (ms) and loop-point evals/s", runs[0]["loop_point_evals_per_s"],
                         "loop-point evals/s", len(reqs), 0, None, "f32",
                         {"workload": f"serving: {cfg['n_loops']} loops x {cfg['ppl']} ppl, G={cfg['n_groups']}, "
@@ -1196,22 +1251,8 @@ def run_serve(args):
                          "arena": "16 GiB", "tile_groups_per_step": 128})
     line["serve"] = runs
     line["capacity_req_per_s"] = capacity
-    # one request through the server, its results against the FP64 oracle
-    sv = wln.Server(ctx, ens, cfg["n_groups"], prec=args.prec, arena_bytes=16 << 30,
-                    tile_groups_per_step=128)
-    r0 = reqs[0]
-    rid = sv.submit(r0.profile, r0.rho, r0.T)
-    for _ in range(100000):
-        sv.step()
-        state, res = sv.poll(rid)
-        if state == sv.DONE:
-            break
-    y32, _ = ctx.loops_copy(ens)
     line["gpu_error_vs_oracle_sampled"] = dict(
-        sampled_oracle_error(y32, [r0.profile], [r0.rho], [r0.T], res[0], cfg["n_groups"]),
-        request=0)
-    sv.release(rid)
-    sv.free()
+        _serve_oracle_check(ctx, ens, cfg, reqs[0], args.prec), request=0)
     ens.free(); ctx.close()
     print(json.dumps(line))
 
