@@ -521,6 +521,9 @@ def main():
                     help="with --levels: the nested loops (all, even, 0 mod 4 points)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-guard", action="store_true",
+                    help="turn the precision guard off (a comparison: the FP32 path then misses "
+                         "the 1e-6 bar at strong spins)")
     args = ap.parse_args()
     wl = _workload(args.workload)
 
@@ -551,6 +554,8 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
     ctx = wln.Context(dev, stream)
+    if args.no_guard:
+        ctx.set_precision_guard(False)
     # weak scaling: rank r holds loops [r N_l, (r+1) N_l) of one ensemble (the
     # Philox counter is the global loop index), so N ranks evaluate N N_l loops
     seed, loop0 = wl.seed, rank * wl.n_loops
