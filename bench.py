@@ -64,17 +64,29 @@ N_ALG_FP64 = 18 + 17 + 11 / 2
 # tan(theta) = 0.05 it takes int dt/Q = r (1 - t^2/3 + t^4/5), r = 1/(Q0 + B),
 # t^2 = D r^2, instead of sqrt(D) (1), the quotient (1), the degree-7
 # polynomial (8 + 1) and theta/sqrt(D), and 1/D instead of (1/sqrt(D))^2 (1):
-# 9 fewer again.
+# 9 fewer again; below tan(theta) = 0.18 five terms of the same series, two
+# FMAs more than three: 7 fewer than the low form.
 N_ALG_LOW_SAVED = 6
+N_ALG_MID_SAVED = 7
 N_ALG_TINY_SAVED = 9
+# FP32 operations per segment of the precision guard's double-float walk
+# (csrc/wln_guard.cu, counted with two-sum 6, fast two-sum 3, sum 11, accurate
+# sum 20, product 7, product by a float 6, reciprocal 6, reciprocal square
+# root 16, negation 0): position 17 + 6, differences 22, C, B, X, D 25 each,
+# Q1 36, 1/Q1 6, 1/sqrt(D) 16, the arguments of the angle 18, the angle 153
+# (fold 21, table-driven arctangent 106, unfolding 26), int dt/Q 7, the phase
+# term and its sum 27, the spin bracket 61 and its sum 34: 503, plus 4 MUFU.
+N_ALG_DF = 503
 
 
 def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float):
     """Fractions of the flux-tube segment evaluations of one pass that the
-    kernel walks with the low form of the arctangent, and with its short
-    series: the same float32 tests per (tile of P radii at one T, block of 32
-    loops) that the kernel makes from the block's longest segment and largest
-    |y| (accounting only).  Returns (low, short), short a part of low."""
+    kernel walks with the pi/4 form of the arctangent or better, with the
+    five-term series or better, and with the three-term series: the same
+    float32 tests per (tile of P radii at one T, block of 32 loops) that the
+    kernel makes from the block's longest segment and largest |y|
+    (accounting only).  Returns (low, mid, short), each a part of the one
+    before."""
     f = np.float32
     n_loops = y32.shape[0]
     n_blocks = (n_loops + 31) // 32
@@ -85,7 +97,7 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
     dm = np.concatenate([d, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
     rm = np.concatenate([r, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
     in_block = np.minimum(32, n_loops - 32 * np.arange(n_blocks)).astype(np.float64)
-    low = tiny = tot = 0.0
+    low = mid = tiny = tot = 0.0
     for prof, rho, T in zip(profiles, rhos, Ts):
         if prof.kind != I.PROFILE_FLUX_TUBE:
             continue
@@ -101,13 +113,21 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
             rhs = np.sqrt(f(prof.lam * prof.lam) + gap * gap)
             w = nval[:, None] * in_block[None, :]
             low += float(((lhs <= f(0.9) * rhs) * w).sum())
+            mid += float(((lhs <= f(0.3) * rhs) * w).sum())
             tiny += float(((lhs <= f(0.09) * rhs) * w).sum())
             tot += float(w.sum())
-    return (low / tot, tiny / tot) if tot else (0.0, 0.0)
+    return (low / tot, mid / tot, tiny / tot) if tot else (0.0, 0.0, 0.0)
 
 
-def _n_alg(base: float, fr) -> float:
-    return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_TINY_SAVED * fr[1]
+def _n_alg(base: float, fr, mid_form: bool = True) -> float:
+    """Operations per (segment, radius): the general form's count less what
+    each cheaper form saves (6 on the pi/4 form; 7 more on the five-term
+    series, 9 more on the three-term one).  Passes without the five-term
+    form walk its blocks with the pi/4 form."""
+    if mid_form:
+        return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_MID_SAVED * fr[1] - \
+            (N_ALG_TINY_SAVED - N_ALG_MID_SAVED) * fr[2]
+    return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_TINY_SAVED * fr[2]
 
 
 def _workload(name: str) -> I.Workload:
@@ -629,14 +649,18 @@ def main():
     peak_ops = sm_count() * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 ops/s
     seg = wl.segment_evals
     n_alg = N_ALG_FP32
-    f_low = (0.0, 0.0)
+    f_low = (0.0, 0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 4, 1.0)
         n_alg = _n_alg(N_ALG_FP32, f_low)
-    achieved = n_alg * seg / (wilson_ms / 1e3) / 1e12
+    # the Wilson stage (float pass, double-float recomputation, fixup) does
+    # the float walk's work on every segment and the double-float walk's on
+    # the segments of the loops the guard recomputes
+    df_ops = N_ALG_DF * guard["escalated_loops"] / args.steps * wl.ppl if args.prec == "fp32" else 0.0
+    achieved = (n_alg * seg + df_ops) / (wilson_ms / 1e3) / 1e12
     traffic = _ncu_traffic(f"wilson_kernel_{args.workload}")
     line = {
         "metric": METRIC, "value": value, "unit": "loop-point evals/s", "n_gpus": ws,
@@ -654,10 +678,14 @@ def main():
                      "kernel_ms": wilson_ms,
                      "segment_evals_per_s": seg / (wilson_ms / 1e3),
                      "n_alg_fp32_per_segment": n_alg, "n_alg_mufu_per_segment": N_ALG_MUFU,
-                     "low_angle_fraction": f_low[0], "short_series_fraction": f_low[1],
+                     "guard_double_float_ops": df_ops,
+                     "low_angle_fraction": f_low[0], "mid_series_fraction": f_low[1],
+                     "short_series_fraction": f_low[2],
                      "n_alg_basis": f"{N_ALG_FP32:g} per (segment, point), "
                                     f"{N_ALG_LOW_SAVED} fewer on the low-angle form, "
-                                    f"{N_ALG_TINY_SAVED} fewer again on its short series",
+                                    f"{N_ALG_MID_SAVED} or {N_ALG_TINY_SAVED} fewer again on its "
+                                    f"five- or three-term series; plus {N_ALG_DF} per segment "
+                                    f"of each loop the precision guard recomputes in double-float",
                      # context only: the same launch counted as if every segment
                      # took the general form (the rate of segment evaluations in
                      # units of the general formula's operations)
@@ -820,7 +848,8 @@ def run_batched(args, wl: I.Workload):
         ach = n_alg * wl.segment_evals / (ms / 1e3) / 1e12
         line["roofline"].update({"achieved": ach, "frac": ach / line["roofline"]["peak"],
                                  "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
-                                 "short_series_fraction": f_low[1]})
+                                 "mid_series_fraction": f_low[1],
+                                 "short_series_fraction": f_low[2]})
     line["gpu_error_vs_oracle_sampled"] = sampled_oracle_error(
         y32, wl.profiles, wl.rho, wl.T, S2, wl.n_groups)
     line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
@@ -891,16 +920,16 @@ def run_levels(args, wl: I.Workload):
     # paper's levels: circle N/2 + square N/4 + triangle N/4 = N segments per
     # loop and point; nested levels: N + N/2 + N/4
     seg = wl.segment_evals * (1.75 if args.nested else 1.0)
-    n_alg, f_low = N_ALG_FP32_LEVELS, (0.0, 0.0)
+    n_alg, f_low = N_ALG_FP32_LEVELS, (0.0, 0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         # sub-loop segments join points up to 4 apart
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 3, 4.0)
-        if args.nested:     # the nested pass takes the low form but not the short series
-            f_low = (f_low[0], 0.0)
-        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low)
+        if args.nested:     # the nested pass takes the low form but not the series
+            f_low = (f_low[0], 0.0, 0.0)
+        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low, mid_form=False)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation"
                         + (", nested loops)" if args.nested else ")"),
@@ -917,7 +946,7 @@ def run_levels(args, wl: I.Workload):
                         "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
-                        "short_series_fraction": f_low[1],
+                        "mid_series_fraction": f_low[1], "short_series_fraction": f_low[2],
                         "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": wl.loop_points / e2e_s, "unit": "loop-point evals/s",
@@ -1045,7 +1074,7 @@ def run_correlation(args, wl: I.Workload):
                         "kernel": "wilson_kernel<F32Comp,4,4,loops>", "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
-                        "short_series_fraction": f_low[1],
+                        "mid_series_fraction": f_low[1], "short_series_fraction": f_low[2],
                         "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"}
     line["e2e"] = {"value": lp / e2e_s, "unit": "loop-point evals/s", "h2d_bytes_per_step":

@@ -551,10 +551,11 @@ wln_status wln_set_tuning(wln_ctx* ctx, int32_t points_per_lane, int32_t warps, 
  * discretisation levels), theta <= atan(u / (1 - u)):
  *   level 1: blocks with u <= 0.45 (theta <= pi/4) skip the arctangent's
  *            range fold and octant unfolding -- the same angle bit for bit;
- *   level 2: blocks with u <= 0.045 (tan theta < 0.05) take int dt/Q =
- *            theta / sqrt(D) from three terms of the series of atan(t)/t
- *            (relative remainder below 2.2e-9, so results move by float
- *            rounding only).
+ *   level 2: blocks with u <= 0.15 (tan theta < 0.18) take int dt/Q =
+ *            theta / sqrt(D) from five terms of the series of atan(t)/t,
+ *            and blocks with u <= 0.045 (tan theta < 0.05) from three
+ *            (relative remainders below 3.3e-9, so results move by float
+ *            rounding only; the level passes keep the three-term form).
  * Later launches on this context use forms up to `level`: 0 = the general
  * form everywhere, 1, or 2 (the default).  Any other value: WLN_EINVAL.
  */

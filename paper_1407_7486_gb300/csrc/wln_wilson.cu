@@ -34,13 +34,15 @@
 // segment of the block at the warp's tile (T, rho, lambda).  For u <= 0.45
 // (theta <= pi/4) the warp walks the block with the arctangent's low form,
 // without the range fold and the octant unfolding (6 of the 17 operations of
-// theta; the same bits); for u <= 0.045 (tan(theta) < 0.05) it takes
-// int dt/Q = theta / sqrt(D) from three terms of the series of atan(t)/t,
-// without 1/sqrt(D) (the spin then takes 1/D; the result moves by rounding
-// only).  The choice is per block and the same on every
-// lane, so the walk has no branch per segment: the row loop exists once per
-// form (twice for the nested levels, whose long loop pays more for a third
-// copy in instruction fetch than the series saves).
+// theta; the same bits); for u <= 0.15 (tan(theta) < 0.18) it takes
+// int dt/Q = theta / sqrt(D) from five terms of the series of atan(t)/t,
+// and for u <= 0.045 (tan(theta) < 0.05) from three, without 1/sqrt(D) (the
+// spin then takes 1/D; the result moves by rounding only).  The choice is
+// per block and the same on every lane, so the walk has no branch per
+// segment: the row loop exists once per form (three times for the paper's
+// levels, without the five-term series, and twice for the nested levels,
+// whose long loops pay more for further copies in instruction fetch than
+// the series save).
 //
 // Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
 // the same pass can instead walk the three interleaved sub-loops of every
@@ -171,17 +173,29 @@ __device__ __forceinline__ float atan2_low(float y, float x) {
 
 // The angle when 0 < y <= 0.05 x: the Taylor series t - t^3/3 + t^5/5 of
 // atan t, whose remainder (below t^7/7) is under 2.2e-9 of atan t there.
-// (The walk's short-series form uses the same series for theta / sqrt(D)
-// directly; this one serves walks that do not carry Q.)
+// (The walk's short-series forms use the same series for theta / sqrt(D)
+// directly; these serve walks that do not carry Q.)
 __device__ __forceinline__ float atan2_tiny(float y, float x) {
   const float t = y * rcp_approx(x);
   const float s = t * t;
   return fmaf(t * s, fmaf(s, 0.2f, -0.333333343f), t);
 }
 
-// at2_form<1>: the angle when every segment of a block is known to subtend
-// at most pi/4 at the field axis; at2_form<2>: at most atan(0.05) (kLowAngle:
-// the flavour has these cheaper forms); at2_form<0> is the general angle.
+// The angle when 0 < y <= 0.18 x: t (1 - t^2/3 + t^4/5 - t^6/7 + t^8/9),
+// remainder below t^11/11, under 3.3e-9 of atan t there.
+__device__ __forceinline__ float atan2_mid(float y, float x) {
+  const float t = y * rcp_approx(x);
+  const float s = t * t;
+  float q = fmaf(s, 0.111111112f, -0.142857149f);
+  q = fmaf(s, q, 0.2f);
+  q = fmaf(s, q, -0.333333343f);
+  return fmaf(t * s, q, t);
+}
+
+// Forms of the angle, by the largest angle a block's segments may subtend at
+// the field axis: at2_form<0> the general angle, <1> at most pi/4, <2>
+// tan(theta) < 0.18, <3> tan(theta) < 0.05 (kLowAngle: the flavour has the
+// cheaper forms).
 struct F32Comp {
   using F = float;
   static constexpr bool kCompensated = true;
@@ -190,7 +204,10 @@ struct F32Comp {
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   template <int FORM>
   __device__ static float at2_form(float y, float x) {
-    return FORM == 2 ? atan2_tiny(y, x) : (FORM == 1 ? atan2_low(y, x) : atan2_pos(y, x));
+    return FORM == 3   ? atan2_tiny(y, x)
+           : FORM == 2 ? atan2_mid(y, x)
+           : FORM == 1 ? atan2_low(y, x)
+                       : atan2_pos(y, x);
   }
 };
 struct F32Naive {
@@ -201,7 +218,10 @@ struct F32Naive {
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   template <int FORM>
   __device__ static float at2_form(float y, float x) {
-    return FORM == 2 ? atan2_tiny(y, x) : (FORM == 1 ? atan2_low(y, x) : atan2_pos(y, x));
+    return FORM == 3   ? atan2_tiny(y, x)
+           : FORM == 2 ? atan2_mid(y, x)
+           : FORM == 1 ? atan2_low(y, x)
+                       : atan2_pos(y, x);
   }
 };
 struct F64 {
@@ -270,17 +290,18 @@ struct KParams {
 // times the unit loop's (up to span of them for a sub-loop), and a margin of
 // 0.9 keeps the float comparison of the two sides on the same side.  Every
 // lane computes the same answer from the same block statistics.
-// The same bound gives t = tan(theta) <= u / (1 - u), u = |d| / sqrt(Q0);
-// for u <= 0.045, t < 0.05 and three terms of the series of atan t suffice.
-// Returns the form of theta for the block: 2, 1 or 0 (general).  (In float:
-// the margins are far above its rounding.)
+// The same bound gives t = tan(theta) <= u / (1 - u), u = |d| / sqrt(Q0):
+// for u <= 0.15, t < 0.18 and five terms of the series of atan t suffice;
+// for u <= 0.045, t < 0.05 and three.  Returns the form of theta for the
+// block: 3 (t < 0.05), 2 (t < 0.18), 1 (theta <= pi/4) or 0 (general).  (In
+// float: the margins are far above its rounding.)
 struct LowAngle {
   float two_span_sT, sT, rho_min, l2;
   __device__ __forceinline__ int block(const KParams& k, int b) const {
     const float2 st = k.stats[b];
     const float gap = fmaxf(0.0f, rho_min - sT * st.y);
     const float lhs = two_span_sT * st.x, rhs = sqrtf(l2 + gap * gap);
-    return lhs <= 0.09f * rhs ? 2 : (lhs <= 0.9f * rhs ? 1 : 0);
+    return lhs <= 0.09f * rhs ? 3 : (lhs <= 0.3f * rhs ? 2 : (lhs <= 0.9f * rhs ? 1 : 0));
   }
 };
 
@@ -288,9 +309,10 @@ struct LowAngle {
 // carries Q at the current point so that theta = atan2(sqrt(D), Q0 + B)
 // (one multiply fewer per segment and radius, one register more per radius);
 // without it theta = atan2(C sqrt(D), D + B (B + C)).  step_<1> may be used
-// when every segment subtends at most pi/4 at the axis, step_<2> when at most
-// atan(0.05) (the caller has checked): theta then needs no octant unfolding,
-// and in the second case only three terms of its series.
+// when every segment subtends at most pi/4 at the axis, step_<2> when
+// tan(theta) < 0.18 and step_<3> when tan(theta) < 0.05 (the caller has
+// checked): theta then needs no octant unfolding, and in the last two cases
+// only five or three terms of its series.
 template <class A, int P, bool CQ = true>
 struct Walk {
   using F = typename A::F;
@@ -338,13 +360,23 @@ struct Walk {
       const F X = fma(rx[p], dy, -rydx);
       const F D = fma(X, X, l2C);
       const F BC = B + C;
-      if constexpr (FORM == 2 && CQ) {
-        // tan(theta) = t < 0.05 with t^2 = D r^2, r = 1/(Q0 + B): int dt/Q =
-        // theta / sqrt(D) = r atan(t) / t = r (1 - t^2/3 + t^4/5), without
-        // 1/sqrt(D); the spin takes 1/D instead.
+      if constexpr (FORM >= 2 && CQ) {
+        // tan(theta) = t with t^2 = D r^2, r = 1/(Q0 + B): int dt/Q =
+        // theta / sqrt(D) = r atan(t) / t, without 1/sqrt(D); the spin takes
+        // 1/D instead.  t < 0.05: r (1 - t^2/3 + t^4/5); t < 0.18: r (1 -
+        // t^2/3 + t^4/5 - t^6/7 + t^8/9) (remainders under 3.3e-9).
         const F r = A::rcp(q[p] + B);
         const F t2 = D * (r * r);
-        const F J1 = r * fma(t2, fma(t2, F(0.2), F(-0.333333343)), F(1));
+        F poly;
+        if constexpr (FORM == 3) {
+          poly = fma(t2, fma(t2, F(0.2), F(-0.333333343)), F(1));
+        } else {
+          poly = fma(t2, F(0.111111112), F(-0.142857149));
+          poly = fma(t2, poly, F(0.2));
+          poly = fma(t2, poly, F(-0.333333343));
+          poly = fma(t2, poly, F(1));
+        }
+        const F J1 = r * poly;
         ph[p].add(X * J1);
         const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
         sp[p].add(br * A::rcp(D));
@@ -883,7 +915,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
                       static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
                       static_cast<float>(prof.l2)};
-    return min(la.block(k, b), k.low_angle);
+    const int f = la.block(k, b);
+    return k.low_angle >= 2 ? f : min(f, k.low_angle);   // level 2: the series forms too
   };
   const int b0 = c * k.chain;
   const int b1 = min(b0 + k.chain, k.n_blocks);
@@ -939,7 +972,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             r = 1;
           }
           // the form of theta for this block is the same on every lane
-          if (form == 2) rows_plain<2>(w, rowp, r, pp.chunk_rows);
+          if (form == 3) rows_plain<3>(w, rowp, r, pp.chunk_rows);
+          else if (form == 2) rows_plain<2>(w, rowp, r, pp.chunk_rows);
           else if (form == 1) rows_plain<1>(w, rowp, r, pp.chunk_rows);
           else rows_plain<0>(w, rowp, r, pp.chunk_rows);
         } else if constexpr (NEST) {
@@ -978,8 +1012,10 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(v.z, v.w);
             r = 2;
           }
-          if (form == 2) rows_levels<2>(w, rowp, r, pp.chunk_rows);
-          else if (form == 1) rows_levels<1>(w, rowp, r, pp.chunk_rows);
+          // no copy for the middle series (instruction fetch): its blocks
+          // take the pi/4 form
+          if (form == 3) rows_levels<3>(w, rowp, r, pp.chunk_rows);
+          else if (form >= 1) rows_levels<1>(w, rowp, r, pp.chunk_rows);
           else rows_levels<0>(w, rowp, r, pp.chunk_rows);
         }
       }

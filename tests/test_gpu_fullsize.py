@@ -14,7 +14,10 @@ outputs one by one:
     spin is largest; smallest flux at the largest radius and shortest time),
     each group mean within its R15 bar (max(1e-6, 2^-21 P) scalar,
     max(1, cosh s) max(1e-6, 2^-21 (s + P)) spinor, averaged over the
-    group's loops), the oracle working on the same float points;
+    group's loops), the oracle working on the same float points; the same
+    samples and 24 more from the strongest spins (F = 50, the 8 longest
+    times, the 16 smallest radii), where the precision guard works, within
+    the plain bar: 1e-6 scalar, 1e-6 max(1, <cosh s>) spinor;
   * FP64 group sums on the benchmark's FP64 subset (one tube, every 8th
     radius, every 4th time), sampled the same way with 1e-12 and 2^-50;
   * properties that hold at any size, on every output: the group means of
@@ -108,6 +111,23 @@ def test_full_size_fp32_group_sums_sampled(full):
     samples.append((0, n_rho - 1, wl.n_groups - 1))                        # F = 1, rho = 8, T = 1e-3
     worst = _check_samples(S, y32, wl, samples, 1e-6, 2.0 ** -21)
     print("worst sample / bar", worst)
+    n_T = len(wl.T[last])
+    for _ in range(24):
+        it = n_T - 1 - int(rng.integers(8))
+        samples.append((last, it * n_rho + int(rng.integers(16)), int(rng.integers(wl.n_groups))))
+    lpg = wl.n_loops // wl.n_groups
+    worst_s = worst_f = 0.0
+    for q, p, g in samples:
+        base = sum(len(wl.rho[k]) * len(wl.T[k]) for k in range(q))
+        r, t = wl.rho[q][p % len(wl.rho[q])], wl.T[q][p // len(wl.rho[q])]
+        yg = y32[g * lpg:(g + 1) * lpg].astype(np.float64)
+        ref = oracle.group_sums(yg, wl.profiles[q], [r], [t], 1)[0, 0]
+        cosh = np.cosh(oracle.phase_spin(yg, wl.profiles[q], r, t)[1]).sum()
+        es = abs(S[base + p, g, 0] - ref[0]) / lpg
+        ef = abs(S[base + p, g, 1] - ref[1]) / max(cosh, lpg)
+        worst_s, worst_f = max(worst_s, es), max(worst_f, ef)
+        assert es <= 1e-6 and ef <= 1e-6, (q, p, g, es, ef)
+    print(f"plain bar: scalar {worst_s:.2e}, spinor / <cosh s> {worst_f:.2e}")
 
 
 def test_full_size_properties_on_every_output(full):

@@ -4,13 +4,16 @@ For a segment from r to r + d and Q(t) = lambda^2 + |r + t d|^2, the angle
 theta = atan2(sqrt(D), Q0 + B) (B = r.d, D = lambda^2 |d|^2 + (r x d)^2)
 obeys tan(theta) <= u / (1 - u) with u = |d| / sqrt(Q0): sqrt(D) <=
 sqrt(Q0) |d| (Lagrange) and Q0 + B >= Q0 - sqrt(Q0) |d|.  The kernel takes the
-low form (no octant unfolding) for 2u <= 0.9 and the short series for
-2u <= 0.09, with u bounded per block through |d| <= sqrt(T) |d|max and
-Q0 >= lambda^2 + (rho - sqrt(T) |y|max)_+^2.  Checked here:
+low form (no octant unfolding) for 2u <= 0.9, the five-term series for
+2u <= 0.3 and the three-term series for 2u <= 0.09, with u bounded per block
+through |d| <= sqrt(T) |d|max and Q0 >= lambda^2 + (rho - sqrt(T) |y|max)_+^2.
+Checked here:
   * the bound itself, by brute force over random and adversarial segments
     (short and long, near and across the axis, thin and wide tubes);
-  * that the two thresholds give theta <= pi/4 and tan(theta) < 0.05;
-  * the remainder of the series 1 - t^2/3 + t^4/5 of atan(t)/t below t^6/7;
+  * that the three thresholds give theta <= pi/4, tan(theta) < 0.18 and
+    tan(theta) < 0.05;
+  * the remainders of the series 1 - t^2/3 + t^4/5 (below t^6/7) and
+    1 - t^2/3 + t^4/5 - t^6/7 + t^8/9 (below t^10/11) of atan(t)/t;
   * the per-block reading of u on a real ensemble against every segment's u;
   * the bench's accounting of the forms at the extremes (all or nothing).
 """
@@ -51,9 +54,10 @@ def test_thresholds_give_the_forms():
     d = rng.normal(size=(n, 2))
     d *= (10.0 ** rng.uniform(-3, 0, size=(n, 1))) / np.linalg.norm(d, axis=1, keepdims=True)
     theta, u = _theta_u(r, d, 0.7)
-    low, short = 2 * u <= 0.9, 2 * u <= 0.09
-    assert low.any() and short.any() and (~low).any()
+    low, mid, short = 2 * u <= 0.9, 2 * u <= 0.3, 2 * u <= 0.09
+    assert low.any() and mid.any() and short.any() and (~low).any()
     assert np.all(theta[low] <= np.pi / 4)
+    assert np.all(np.tan(theta[mid]) < 0.18)
     assert np.all(np.tan(theta[short]) < 0.05)
 
 
@@ -64,6 +68,11 @@ def test_series_remainder():
     # (plus the double rounding of both sides, a few ulps of 1)
     assert np.all(np.abs(np.arctan(t) / t - series) <= t ** 6 / 7.0 + 1e-15)
     assert (0.05 ** 6) / 7.0 < 2.3e-9
+    t = np.linspace(1e-6, 0.18, 20001)
+    s2 = t * t
+    series5 = 1.0 - s2 / 3.0 + s2 ** 2 / 5.0 - s2 ** 3 / 7.0 + s2 ** 4 / 9.0
+    assert np.all(np.abs(np.arctan(t) / t - series5) <= t ** 10 / 11.0 + 1e-15)
+    assert (0.18 ** 10) / 11.0 < 3.3e-9
 
 
 def test_block_bound_covers_every_segment():
@@ -90,38 +99,50 @@ def test_accounting_extremes():
     y32 = oracle.gen_loops(4, 64, 128).astype(np.float32)
     prof = I.Profile(I.PROFILE_FLUX_TUBE, F=10.0, lam=1.0)
     rho = I.lin_grid(0.0, 3.0, 7)
-    low, short = bench.low_angle_fraction(y32, [prof], [rho], [np.array([1e-8])], 4, 1.0)
-    assert low == 1.0 and short == 1.0
-    low, short = bench.low_angle_fraction(y32, [prof], [np.zeros(1)], [np.array([1e4])], 4, 1.0)
-    assert low == 0.0 and short == 0.0
+    low, mid, short = bench.low_angle_fraction(y32, [prof], [rho], [np.array([1e-8])], 4, 1.0)
+    assert low == 1.0 and mid == 1.0 and short == 1.0
+    low, mid, short = bench.low_angle_fraction(y32, [prof], [np.zeros(1)], [np.array([1e4])], 4, 1.0)
+    assert low == 0.0 and mid == 0.0 and short == 0.0
     const = I.Profile(I.PROFILE_CONST_B, B=1.0)
-    assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0)
+    assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0, 0.0)
+    # the operation count: 6 fewer on the low form, 13 on the five-term series,
+    # 15 on the three-term one; without the five-term form its share takes 6
+    assert bench._n_alg(38.75, (1.0, 1.0, 1.0)) == 38.75 - 15
+    assert bench._n_alg(38.75, (1.0, 1.0, 0.0)) == 38.75 - 13
+    assert bench._n_alg(38.75, (1.0, 1.0, 0.0), mid_form=False) == 38.75 - 6
+    assert bench._n_alg(38.75, (1.0, 1.0, 1.0), mid_form=False) == 38.75 - 15
 
 
-def test_short_series_form_of_int_dt_over_q():
-    """The kernel's short-series form: int_0^1 dt/Q = theta / sqrt(D) =
-    r (1 - t^2/3 + t^4/5), r = 1/(Q0 + B), t^2 = D r^2, on segments with
-    2u <= 0.09 -- checked against the closed form and against a 400-point
-    Gauss-Legendre rule of the integral itself."""
+import pytest
+
+
+@pytest.mark.parametrize("u_max,terms,bound", [(0.045, 3, 2.3e-9), (0.15, 5, 3.3e-9)])
+def test_series_forms_of_int_dt_over_q(u_max, terms, bound):
+    """The kernel's series forms: int_0^1 dt/Q = theta / sqrt(D) =
+    r atan(t)/t, r = 1/(Q0 + B), t^2 = D r^2, from three terms of the series
+    on segments with 2u <= 0.09 and five on segments with 2u <= 0.3 -- checked
+    against the closed form and against a 400-point Gauss-Legendre rule of
+    the integral itself."""
     rng = np.random.default_rng(8)
     n = 20000
     lam = 0.8
     r = rng.normal(size=(n, 2)) * 3.0
     d = rng.normal(size=(n, 2))
     Q0 = lam * lam + np.sum(r * r, axis=1)
-    d *= (0.045 * np.sqrt(Q0) * rng.uniform(0.01, 1.0, size=n) / np.linalg.norm(d, axis=1))[:, None]
+    d *= (u_max * np.sqrt(Q0) * rng.uniform(0.01, 1.0, size=n) / np.linalg.norm(d, axis=1))[:, None]
     theta, u = _theta_u(r, d, lam)
-    assert np.all(2 * u <= 0.09 * (1 + 1e-12))
+    assert np.all(u <= u_max * (1 + 1e-12))
     B = np.sum(r * d, axis=1)
     X = r[:, 0] * d[:, 1] - r[:, 1] * d[:, 0]
     D = lam * lam * np.sum(d * d, axis=1) + X * X
     rr = 1.0 / (Q0 + B)
     t2 = D * rr * rr
-    series = rr * (1.0 - t2 / 3.0 + t2 * t2 / 5.0)
+    coef = [1.0, -1.0 / 3.0, 1.0 / 5.0, -1.0 / 7.0, 1.0 / 9.0][:terms]
+    series = rr * sum(c * t2 ** k for k, c in enumerate(coef))
     closed = theta / np.sqrt(D)
-    assert np.all(np.abs(series - closed) <= 2.3e-9 * closed + 1e-15 * closed)
+    assert np.all(np.abs(series - closed) <= bound * closed + 1e-15 * closed)
     x, w = np.polynomial.legendre.leggauss(400)
     tq = 0.5 * (x + 1.0)
     Q = lam * lam + np.sum((r[:, None, :] + tq[None, :, None] * d[:, None, :]) ** 2, axis=2)
     quad = 0.5 * np.sum(w[None, :] / Q, axis=1)
-    assert np.all(np.abs(series - quad) <= 2.3e-9 * quad + 1e-14 * quad)
+    assert np.all(np.abs(series - quad) <= bound * quad + 1e-14 * quad)
