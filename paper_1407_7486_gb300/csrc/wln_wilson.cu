@@ -325,6 +325,8 @@ struct Walk {
   F q[P], rq[P];     // Q and 1/Q at the current point
   Acc<F, A::kCompensated> ph[P], sp[P];
 
+  __device__ __forceinline__ void set_rho(int p, F v) { rho[p] = v; }
+
   __device__ __forceinline__ void start(F x0, F y0) {
     ux = x0; uy = y0;
     ry = s * y0;
@@ -422,6 +424,7 @@ struct WalkB {
   F ux, uy, ry;
   F rx[P];
   Acc<F, A::kCompensated> ph[P];
+  __device__ __forceinline__ void set_rho(int p, F v) { rho[p] = v; }
   __device__ __forceinline__ void start(F x0, F y0) {
     ux = x0; uy = y0; ry = s * y0;
 #pragma unroll
@@ -447,6 +450,188 @@ struct WalkB {
   __device__ __forceinline__ void raw(int p, double& ps, double& pc, double& ss,
                                       double& sc) const {
     ps = ph[p].s; pc = ph[p].c; ss = 1.0; sc = 0.0;
+  }
+};
+
+// ------------------------------------------------- paired FP32 arithmetic
+// The sm_100 family issues two FP32 operations of a float2 in one instruction
+// (fma, add, mul), each lane rounded exactly as the scalar _rn operation.
+// Neither subtraction nor negation exists in paired form; both are written
+// exactly: fma(a, -1, b) rounds as b - a, and negating one factor of a
+// product (or every input of an fma) negates the rounded result.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+template <class A>
+__device__ __forceinline__ float2 rcp2(float2 x) {
+  return make_float2(A::rcp(x.x), A::rcp(x.y));
+}
+template <class A>
+__device__ __forceinline__ float2 rsq2(float2 x) {
+  return make_float2(A::rsq(x.x), A::rsq(x.y));
+}
+
+// atan_unit, atan2_low and atan2_pos on a pair, bitwise equal per lane.
+__device__ __forceinline__ float2 atan_unit2(float2 t) {
+  const float2 s = mul2(t, t);
+  float2 q = fma2(bc2(0.002920693f), s, bc2(-0.01636793f));
+  q = fma2(q, s, bc2(0.043211866f));
+  q = fma2(q, s, bc2(-0.07552215f));
+  q = fma2(q, s, bc2(0.106660046f));
+  q = fma2(q, s, bc2(-0.14211056f));
+  q = fma2(q, s, bc2(0.19993773f));
+  q = fma2(q, s, bc2(-0.33333153f));
+  return fma2(mul2(t, s), q, t);
+}
+
+__device__ __forceinline__ float2 atan2_low2(float2 y, float2 x) {
+  return atan_unit2(mul2(y, make_float2(rcp_approx(x.x), rcp_approx(x.y))));
+}
+
+__device__ __forceinline__ float2 atan2_pos2(float2 y, float2 x) {
+  const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+  const float2 mn = make_float2(fminf(y.x, ax.x), fminf(y.y, ax.y));
+  const float2 mx = make_float2(fmaxf(y.x, ax.x), fmaxf(y.y, ax.y));
+  float2 r = atan_unit2(mul2(mn, make_float2(rcp_approx(mx.x), rcp_approx(mx.y))));
+  const float2 up = fma2(r, bc2(-1.0f), bc2(1.5707963267948966f));   // pi/2 - r
+  r = make_float2(y.x > ax.x ? up.x : r.x, y.y > ax.y ? up.y : r.y);
+  const float2 left = fma2(r, bc2(-1.0f), bc2(3.14159265358979323846f));   // pi - r
+  return make_float2(x.x < 0.0f ? left.x : r.x, x.y < 0.0f ? left.y : r.y);
+}
+
+// Acc on a pair; nc holds the compensation negated (so that every step is a
+// paired add or fma).
+template <bool kComp>
+struct Acc2 {
+  float2 s, nc, part;
+  __device__ __forceinline__ void zero() {
+    s = bc2(0.0f); nc = bc2(0.0f); part = bc2(0.0f);
+  }
+  __device__ __forceinline__ void add(float2 a, float2 b) { part = fma2(a, b, part); }
+  __device__ __forceinline__ void fold() {
+    if (kComp) {
+      const float2 y = add2(part, nc);                 // part - c
+      const float2 t = add2(s, y);
+      const float2 u = fma2(s, bc2(-1.0f), t);         // t - s
+      nc = fma2(u, bc2(-1.0f), y);                     // -((t - s) - y)
+      s = t;
+    } else {
+      s = add2(s, part);
+    }
+    part = bc2(0.0f);
+  }
+  __device__ __forceinline__ void lane(int i, double& sum, double& comp) const {
+    sum = i ? s.y : s.x;
+    comp = -(i ? nc.y : nc.x);
+  }
+};
+
+// The flux-tube walk of Walk<A, P, true> for the float flavours with the
+// radii of a lane in pairs: the same operations in the same order, bitwise
+// equal per radius, two radii per instruction.  The values every radius
+// shares (the segment, the scaled y) are formed once in scalar arithmetic and
+// broadcast to both lanes of a pair: a paired instruction takes two cycles of
+// the FMA pipe, which bounds this walk, so work the radii share stays scalar.
+template <class A, int P>
+struct Walk2 {
+  static_assert(P % 2 == 0, "radii in pairs");
+  static constexpr int H = P / 2;
+  using F = float;
+  F s, l2;
+  float2 rho[H];
+  F ux, uy, ry;               // the current point; ry = s y
+  float2 rx[H], q[H], rq[H];
+  Acc2<A::kCompensated> ph[H], sp[H];
+
+  __device__ __forceinline__ void set_rho(int p, F v) {
+    if (p & 1) rho[p >> 1].y = v;
+    else rho[p >> 1].x = v;
+  }
+
+  __device__ __forceinline__ void start(F x0, F y0) {
+    ux = x0; uy = y0;
+    ry = s * y0;
+    const float2 e0 = bc2(fmaf(ry, ry, l2));
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      rx[j] = fma2(bc2(s), bc2(x0), rho[j]);
+      q[j] = fma2(rx[j], rx[j], e0);
+      rq[j] = rcp2<A>(q[j]);
+      ph[j].zero();
+      sp[j].zero();
+    }
+  }
+
+  __device__ __forceinline__ void step(F x1, F y1) { step_<0>(x1, y1); }
+
+  template <int FORM>
+  __device__ __forceinline__ void step_(F x1, F y1) {
+    const F dxs = s * (x1 - ux), dys = s * (y1 - uy);
+    const F Cs = fmaf(dxs, dxs, dys * dys);
+    const F ry1 = s * y1;
+    const float2 M1 = bc2(-1.0f), S = bc2(s), X1 = bc2(x1);
+    const float2 dx = bc2(dxs), dy = bc2(dys), C = bc2(Cs), nC = bc2(-Cs);
+    const float2 l2C = bc2(l2 * Cs);
+    const float2 e1 = bc2(fmaf(ry1, ry1, l2));
+    const float2 rydy = bc2(ry * dys);
+    const float2 nrydx = bc2(-(ry * dxs));
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const float2 rx1 = fma2(S, X1, rho[j]);
+      const float2 q1 = fma2(rx1, rx1, e1);
+      const float2 rq1 = rcp2<A>(q1);
+      const float2 B = fma2(rx[j], dx, rydy);
+      const float2 X = fma2(rx[j], dy, nrydx);
+      const float2 D = fma2(X, X, l2C);
+      const float2 nBC = fma2(B, M1, nC);             // -(B + C)
+      const float2 xa = add2(q[j], B);                // Q0 + B
+      float2 J1, w;
+      if constexpr (FORM >= 2) {
+        // theta / sqrt(D) = r atan(t) / t, t^2 = D r^2, r = 1/(Q0 + B)
+        const float2 r = rcp2<A>(xa);
+        const float2 t2 = mul2(D, mul2(r, r));
+        float2 poly;
+        if constexpr (FORM == 3) {
+          poly = fma2(t2, fma2(t2, bc2(0.2f), bc2(-0.333333343f)), bc2(1.0f));
+        } else {
+          poly = fma2(t2, bc2(0.111111112f), bc2(-0.142857149f));
+          poly = fma2(t2, poly, bc2(0.2f));
+          poly = fma2(t2, poly, bc2(-0.333333343f));
+          poly = fma2(t2, poly, bc2(1.0f));
+        }
+        J1 = mul2(r, poly);
+        w = rcp2<A>(D);
+      } else {
+        const float2 rsD = rsq2<A>(D);
+        const float2 ya = mul2(D, rsD);
+        const float2 theta = FORM == 1 ? atan2_low2(ya, xa) : atan2_pos2(ya, xa);
+        J1 = mul2(theta, rsD);
+        w = mul2(rsD, rsD);
+      }
+      ph[j].add(X, J1);
+      // ((C + B)/Q1 - B/Q0 + C J1) / D with the quotients' difference as
+      // (D - B (B + C)) / (Q0 Q1)
+      const float2 br = fma2(mul2(fma2(B, nBC, D), rq[j]), rq1, mul2(C, J1));
+      sp[j].add(br, w);
+      rx[j] = rx1;
+      q[j] = q1;
+      rq[j] = rq1;
+    }
+    ux = x1; uy = y1; ry = ry1;
+  }
+
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int j = 0; j < H; ++j) { ph[j].fold(); sp[j].fold(); }
+  }
+
+  __device__ __forceinline__ void raw(int p, double& ps, double& pc, double& ss,
+                                      double& sc) const {
+    ph[p >> 1].lane(p & 1, ps, pc);
+    sp[p >> 1].lane(p & 1, ss, sc);
   }
 };
 
@@ -899,7 +1084,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const int i = p < tile.n_valid ? p : (tile.n_valid > 0 ? tile.n_valid - 1 : 0);
-      w[q].rho[p] = static_cast<F>(k.rho[tile.rho0 + i]);
+      w[q].set_rho(p, static_cast<F>(k.rho[tile.rho0 + i]));
     }
   }
   // the spin's scale T spin_per and the phase's turns per unit sum, as
@@ -1211,12 +1396,15 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
     const ProfileDev& prof = k.profs[tile.profile];
     // three walks per radius: Q fits in registers for up to 3 radii per lane
     constexpr bool CQ = !level_mode(MODE) || P <= 3;
+    // float group sums and per-loop values walk the radii in pairs
+    constexpr bool PAIRED = sizeof(typename A::F) == 4 && P % 2 == 0 && !level_mode(MODE);
+    using TubeWalk = std::conditional_t<PAIRED, Walk2<A, (PAIRED ? P : 2)>, Walk<A, P, CQ>>;
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane,
                                              t);
     else
-      ok = run_item<A, P, Walk<A, P, CQ>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag,
-                                                lane, t);
+      ok = run_item<A, P, TubeWalk, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane,
+                                          t);
   }
 
   if (!ok && threadIdx.x == 0) {
