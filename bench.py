@@ -46,29 +46,41 @@ def sm_count(dev: int = 0) -> int:
     return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 # Algorithmic FP32 operations per (segment, point) of the compensated walk,
 # counted from the formulas in csrc/wln_wilson.cu (an FMA, a min/max or a
-# select each count 1): 18 per radius for the geometry, the closed-form
-# integrals (theta = atan2(sqrt(D), Q0 + B)), the products and the two partial
-# sums; 17 for the arctangent (range fold 2, quotient 1, square 1, polynomial
-# 8, octant unfolding 4, plus t*s 1); 11 per segment shared by the lane's
-# P = 4 radii (11/4); and two Kahan folds of 4 operations every 8 segments (1).
-# The level pass holds P = 3 radii per lane: the shared part is 11/3.
-N_ALG_FP32 = 18 + 17 + 11 / 4 + 1
-N_ALG_FP32_LEVELS = 18 + 17 + 11 / 3 + 1
+# select each count 1; a product added into a sum is one FMA): 16 per radius
+# for the geometry (Q1 and its point 2, B, X, D 3, Q0 + B 1), the closed-form
+# integrals (theta = atan2(sqrt(D), Q0 + B): sqrt(D) 1, theta/sqrt(D) 1), the
+# spin bracket (B + C, D - B (B + C), the two reciprocal factors, C J1: 5),
+# 1/D 1 and the two sums 2; 17 for the arctangent (range fold 2, quotient 1,
+# square 1, polynomial 8, octant unfolding 4, plus t*s 1); 11 per segment
+# shared by the lane's P = 4 radii (11/4); and two Kahan folds of 4
+# operations every 8 segments (1).  The level pass holds P = 3 radii per
+# lane: the shared part is 11/3.
+N_ALG_FP32 = 16 + 17 + 11 / 4 + 1
+N_ALG_FP32_LEVELS = 16 + 17 + 11 / 3 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 # The FP64 comparison walk (2 radii per lane): the general form throughout,
 # the shared part over 2 radii, no compensated folds.
-N_ALG_FP64 = 18 + 17 + 11 / 2
+N_ALG_FP64 = 16 + 17 + 11 / 2
 # Where every segment of a block subtends at most pi/4 at the axis the kernel
 # takes the arctangent's low form, which needs neither the range fold (2) nor
-# the octant unfolding (4): 6 operations fewer per (segment, point); below
-# tan(theta) = 0.05 it takes int dt/Q = r (1 - t^2/3 + t^4/5), r = 1/(Q0 + B),
-# t^2 = D r^2, instead of sqrt(D) (1), the quotient (1), the degree-7
-# polynomial (8 + 1) and theta/sqrt(D), and 1/D instead of (1/sqrt(D))^2 (1):
-# 9 fewer again; below tan(theta) = 0.18 five terms of the same series, two
-# FMAs more than three: 7 fewer than the low form.
+# the octant unfolding (4): 6 operations fewer per (segment, point).  Below
+# tan(theta) = 0.18 it takes int dt/Q = r (1 - t^2/3 + t^4/5 - t^6/7 + t^8/9),
+# r = 1/(Q0 + B), t^2 = D r^2 (r^2 1, t^2 1, 4 FMAs, r times it 1) instead of
+# sqrt(D) (1), the quotient (1), the degree-7 polynomial (8 + 1) and
+# theta/sqrt(D) (1), and 1/D by a reciprocal instead of (1/sqrt(D))^2 (1): 7
+# fewer than the low form.  Below tan(theta) = 0.05 three terms of the series
+# (2 FMAs fewer), and the spin as int dt/Q^2 = C r^3 (1/3 - 2 t^2/5) +
+# 1/(Q0 Q1) (r^3 1, the bracket 1, two FMAs into the sum) in place of the
+# bracket and its sum (6, 1/D by no reciprocal at all), with C/3 and 2C/5
+# shared by the radii (2/P): 9 + 2 - 2/P fewer than the low form (MUFU: 2).
 N_ALG_LOW_SAVED = 6
 N_ALG_MID_SAVED = 7
-N_ALG_TINY_SAVED = 9
+
+
+def n_alg_tiny_saved(P: int) -> float:
+    """Operations the three-term form saves against the low form, per
+    (segment, radius), with P radii per lane sharing C/3 and 2C/5."""
+    return 9 + 2 - 2 / P
 # FP32 operations per segment of the precision guard's double-float walk
 # (csrc/wln_guard.cu, counted with two-sum 6, fast two-sum 3, sum 11, accurate
 # sum 20, product 7, product by a float 6, reciprocal 6, reciprocal square
@@ -119,15 +131,16 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
     return (low / tot, mid / tot, tiny / tot) if tot else (0.0, 0.0, 0.0)
 
 
-def _n_alg(base: float, fr, mid_form: bool = True) -> float:
+def _n_alg(base: float, fr, mid_form: bool = True, P: int = 4) -> float:
     """Operations per (segment, radius): the general form's count less what
     each cheaper form saves (6 on the pi/4 form; 7 more on the five-term
-    series, 9 more on the three-term one).  Passes without the five-term
-    form walk its blocks with the pi/4 form."""
+    series, 11 - 2/P more on the three-term one).  Passes without the
+    five-term form walk its blocks with the pi/4 form."""
+    tiny = n_alg_tiny_saved(P)
     if mid_form:
         return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_MID_SAVED * fr[1] - \
-            (N_ALG_TINY_SAVED - N_ALG_MID_SAVED) * fr[2]
-    return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_TINY_SAVED * fr[2]
+            (tiny - N_ALG_MID_SAVED) * fr[2]
+    return base - N_ALG_LOW_SAVED * fr[0] - tiny * fr[2]
 
 
 def _workload(name: str) -> I.Workload:
@@ -677,13 +690,14 @@ def main():
                      "kernel": "wilson_kernel<F32Comp,4,8>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
                      "kernel_ms": wilson_ms,
                      "segment_evals_per_s": seg / (wilson_ms / 1e3),
-                     "n_alg_fp32_per_segment": n_alg, "n_alg_mufu_per_segment": N_ALG_MUFU,
+                     "n_alg_fp32_per_segment": n_alg,
+                     "n_alg_mufu_per_segment": N_ALG_MUFU - f_low[2],
                      "guard_double_float_ops": df_ops,
                      "low_angle_fraction": f_low[0], "mid_series_fraction": f_low[1],
                      "short_series_fraction": f_low[2],
                      "n_alg_basis": f"{N_ALG_FP32:g} per (segment, point), "
                                     f"{N_ALG_LOW_SAVED} fewer on the low-angle form, "
-                                    f"{N_ALG_MID_SAVED} or {N_ALG_TINY_SAVED} fewer again on its "
+                                    f"{N_ALG_MID_SAVED} or {n_alg_tiny_saved(4):g} fewer again on its "
                                     f"five- or three-term series; plus {N_ALG_DF} per segment "
                                     f"of each loop the precision guard recomputes in double-float",
                      # context only: the same launch counted as if every segment
@@ -844,7 +858,7 @@ def run_batched(args, wl: I.Workload):
     y32, _ = ctx.loops_copy(ens)
     if args.prec == "fp32":
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, b.P, 1.0)
-        n_alg = _n_alg(N_ALG_FP32, f_low)
+        n_alg = _n_alg(N_ALG_FP32 + 11 / b.P - 11 / 4, f_low, P=b.P)
         ach = n_alg * wl.segment_evals / (ms / 1e3) / 1e12
         line["roofline"].update({"achieved": ach, "frac": ach / line["roofline"]["peak"],
                                  "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
@@ -929,7 +943,7 @@ def run_levels(args, wl: I.Workload):
         f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 3, 4.0)
         if args.nested:     # the nested pass takes the low form but not the series
             f_low = (f_low[0], 0.0, 0.0)
-        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low, mid_form=False)
+        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low, mid_form=False, P=3)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation"
                         + (", nested loops)" if args.nested else ")"),

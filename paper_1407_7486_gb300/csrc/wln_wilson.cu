@@ -243,6 +243,7 @@ struct Acc {
   F s, c, part;
   __device__ __forceinline__ void zero() { s = F(0); c = F(0); part = F(0); }
   __device__ __forceinline__ void add(F x) { part += x; }
+  __device__ __forceinline__ void add(F a, F b) { part = fma(a, b, part); }
   __device__ __forceinline__ void fold() {
     if (kComp) {
       const F y = part - c;
@@ -313,8 +314,22 @@ struct LowAngle {
 // tan(theta) < 0.18 and step_<3> when tan(theta) < 0.05 (the caller has
 // checked): theta then needs no octant unfolding, and in the last two cases
 // only five or three terms of its series.
+//
+// Spin unit: the spin sums hold 2 int dt/Q^2 per segment, except on blocks
+// walked with step_<3> when kSeriesSpin: there they hold int dt/Q^2 itself,
+// and the caller doubles the block's spin scale (exact in double).  On those
+// segments, with r = 1/(Q0 + B) and t^2 = D r^2 (t = tan(theta)):
+//   int dt/Q   = r f(t^2),                f(u) = atan(sqrt u)/sqrt u
+//                                               = sum_k (-u)^k / (2k + 1),
+//   int dt/Q^2 = -d/d(lambda^2) int dt/Q  (lambda^2 moves Q0 + B by 1 and D
+//              by C)  = r^2 [f - (C r - 2 t^2) f'] = 1/(Q0 Q1) + C r^3 h(t^2),
+//   h(u) = -f'(u) = 1/3 - 2u/5 + 3u^2/7 - ...,  using r^2/(1 + t^2) =
+//   1/(Q0 Q1) (Q0 Q1 = (Q0 + B)^2 + D).  Two terms of h leave a remainder
+//   under 3.6e-9 of int dt/Q^2 for t < 0.05 (C r < 0.0022 there); the spin
+//   then needs neither 1/D nor a difference of nearly equal quotients.
 template <class A, int P, bool CQ = true>
 struct Walk {
+  static constexpr bool kSeriesSpin = CQ;
   using F = typename A::F;
   F s, l2;           // sqrt(T), lambda^2
   F rho[P];
@@ -353,6 +368,9 @@ struct Walk {
     const F ry1 = s * y1;
     const F e1 = fma(ry1, ry1, l2);
     const F rydy = ry * dy, rydx = ry * dx;
+    // C h(t^2) = C/3 - (2C/5) t^2 on the three-term form (values the radii share)
+    F c3 = F(0), cn25 = F(0);
+    if constexpr (FORM == 3 && CQ) { c3 = C * F(0.333333343); cn25 = C * F(-0.4); }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const F rx1 = fma(s, x1, rho[p]);
@@ -368,7 +386,8 @@ struct Walk {
         // 1/D instead.  t < 0.05: r (1 - t^2/3 + t^4/5); t < 0.18: r (1 -
         // t^2/3 + t^4/5 - t^6/7 + t^8/9) (remainders under 3.3e-9).
         const F r = A::rcp(q[p] + B);
-        const F t2 = D * (r * r);
+        const F r2 = r * r;
+        const F t2 = D * r2;
         F poly;
         if constexpr (FORM == 3) {
           poly = fma(t2, fma(t2, F(0.2), F(-0.333333343)), F(1));
@@ -379,9 +398,15 @@ struct Walk {
           poly = fma(t2, poly, F(1));
         }
         const F J1 = r * poly;
-        ph[p].add(X * J1);
-        const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
-        sp[p].add(br * A::rcp(D));
+        ph[p].add(X, J1);
+        if constexpr (FORM == 3) {
+          // int dt/Q^2 = C r^3 (1/3 - 2 t^2/5) + 1/(Q0 Q1)  (unit: see above)
+          sp[p].add(r2 * r, fma(t2, cn25, c3));
+          sp[p].add(rq[p], rq1);
+        } else {
+          const F br = fma(fma(-B, BC, D) * rq[p], rq1, C * J1);
+          sp[p].add(br * A::rcp(D));
+        }
       } else {
         const F rsD = A::rsq(D);
         // atan2(C sqrt(D), D + B (B + C)) with the common factor C removed:
@@ -418,6 +443,7 @@ struct Walk {
 // Constant field: only the area is needed, half the sum of X = r x d.
 template <class A, int P>
 struct WalkB {
+  static constexpr bool kSeriesSpin = false;
   using F = typename A::F;
   F s, l2;
   F rho[P];
@@ -537,6 +563,7 @@ struct Acc2 {
 // the FMA pipe, which bounds this walk, so work the radii share stays scalar.
 template <class A, int P>
 struct Walk2 {
+  static constexpr bool kSeriesSpin = true;   // as Walk<A, P, true>
   static_assert(P % 2 == 0, "radii in pairs");
   static constexpr int H = P / 2;
   using F = float;
@@ -578,6 +605,8 @@ struct Walk2 {
     const float2 e1 = bc2(fmaf(ry1, ry1, l2));
     const float2 rydy = bc2(ry * dys);
     const float2 nrydx = bc2(-(ry * dxs));
+    float2 c3 = bc2(0.0f), cn25 = bc2(0.0f);
+    if constexpr (FORM == 3) { c3 = bc2(Cs * 0.333333343f); cn25 = bc2(Cs * -0.4f); }
 #pragma unroll
     for (int j = 0; j < H; ++j) {
       const float2 rx1 = fma2(S, X1, rho[j]);
@@ -586,36 +615,43 @@ struct Walk2 {
       const float2 B = fma2(rx[j], dx, rydy);
       const float2 X = fma2(rx[j], dy, nrydx);
       const float2 D = fma2(X, X, l2C);
-      const float2 nBC = fma2(B, M1, nC);             // -(B + C)
       const float2 xa = add2(q[j], B);                // Q0 + B
-      float2 J1, w;
-      if constexpr (FORM >= 2) {
-        // theta / sqrt(D) = r atan(t) / t, t^2 = D r^2, r = 1/(Q0 + B)
+      if constexpr (FORM == 3) {
+        // theta / sqrt(D) = r atan(t) / t and int dt/Q^2 = C r^3 (1/3 -
+        // 2 t^2/5) + 1/(Q0 Q1), t^2 = D r^2, r = 1/(Q0 + B) (as in Walk)
         const float2 r = rcp2<A>(xa);
-        const float2 t2 = mul2(D, mul2(r, r));
-        float2 poly;
-        if constexpr (FORM == 3) {
-          poly = fma2(t2, fma2(t2, bc2(0.2f), bc2(-0.333333343f)), bc2(1.0f));
-        } else {
-          poly = fma2(t2, bc2(0.111111112f), bc2(-0.142857149f));
+        const float2 r2 = mul2(r, r);
+        const float2 t2 = mul2(D, r2);
+        const float2 poly = fma2(t2, fma2(t2, bc2(0.2f), bc2(-0.333333343f)), bc2(1.0f));
+        ph[j].add(X, mul2(r, poly));
+        sp[j].add(mul2(r2, r), fma2(t2, cn25, c3));
+        sp[j].add(rq[j], rq1);
+      } else {
+        float2 J1, w;
+        if constexpr (FORM == 2) {
+          // theta / sqrt(D) = r atan(t) / t, t^2 = D r^2, r = 1/(Q0 + B)
+          const float2 r = rcp2<A>(xa);
+          const float2 t2 = mul2(D, mul2(r, r));
+          float2 poly = fma2(t2, bc2(0.111111112f), bc2(-0.142857149f));
           poly = fma2(t2, poly, bc2(0.2f));
           poly = fma2(t2, poly, bc2(-0.333333343f));
           poly = fma2(t2, poly, bc2(1.0f));
+          J1 = mul2(r, poly);
+          w = rcp2<A>(D);
+        } else {
+          const float2 rsD = rsq2<A>(D);
+          const float2 ya = mul2(D, rsD);
+          const float2 theta = FORM == 1 ? atan2_low2(ya, xa) : atan2_pos2(ya, xa);
+          J1 = mul2(theta, rsD);
+          w = mul2(rsD, rsD);
         }
-        J1 = mul2(r, poly);
-        w = rcp2<A>(D);
-      } else {
-        const float2 rsD = rsq2<A>(D);
-        const float2 ya = mul2(D, rsD);
-        const float2 theta = FORM == 1 ? atan2_low2(ya, xa) : atan2_pos2(ya, xa);
-        J1 = mul2(theta, rsD);
-        w = mul2(rsD, rsD);
+        ph[j].add(X, J1);
+        // ((C + B)/Q1 - B/Q0 + C J1) / D with the quotients' difference as
+        // (D - B (B + C)) / (Q0 Q1)
+        const float2 nBC = fma2(B, M1, nC);             // -(B + C)
+        const float2 br = fma2(mul2(fma2(B, nBC, D), rq[j]), rq1, mul2(C, J1));
+        sp[j].add(br, w);
       }
-      ph[j].add(X, J1);
-      // ((C + B)/Q1 - B/Q0 + C J1) / D with the quotients' difference as
-      // (D - B (B + C)) / (Q0 Q1)
-      const float2 br = fma2(mul2(fma2(B, nBC, D), rq[j]), rq1, mul2(C, J1));
-      sp[j].add(br, w);
       rx[j] = rx1;
       q[j] = q1;
       rq[j] = rq1;
@@ -1131,6 +1167,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
     const int form = block_form(b);
+    // the block's spin sums hold int dt/Q^2 itself, not twice it, where its
+    // segments take the three-term series (the nested walks do not)
+    const bool half_spin = WalkT::kSeriesSpin && !NEST && form == 3;
     // first point of each walk, for the closing segments
     float fx[NW], fy[NW];
 #pragma unroll
@@ -1153,7 +1192,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             const float4 v = rowp[0];
             fx[0] = v.x; fy[0] = v.y;
             w[0].start(v.x, v.y);
-            w[0].step(v.z, v.w);
+            if (half_spin) w[0].template step_<3>(v.z, v.w);
+            else w[0].step(v.z, v.w);
             r = 1;
           }
           // the form of theta for this block is the same on every lane
@@ -1193,7 +1233,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             fx[0] = a.x; fy[0] = a.y; fx[1] = a.z; fy[1] = a.w; fx[2] = v.z; fy[2] = v.w;
             w[0].start(a.x, a.y);
             w[1].start(a.z, a.w);
-            w[0].step(v.x, v.y);
+            if (half_spin) w[0].template step_<3>(v.x, v.y);
+            else w[0].step(v.x, v.y);
             w[2].start(v.z, v.w);
             r = 2;
           }
@@ -1221,9 +1262,13 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     if (!active) continue;
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
-      w[q].step(fx[q], fy[q]);  // closing segment back to the walk's first point
+      // closing segment back to the walk's first point
+      if (half_spin) w[q].template step_<3>(fx[q], fy[q]);
+      else w[q].step(fx[q], fy[q]);
       w[q].fold();
     }
+    // the spin's scale for this block's sums (doubling is exact)
+    auto st_b = [&]() { return half_spin ? 2.0 * st_d() : st_d(); };
     if constexpr (PL) {
       if (valid) {
 #pragma unroll
@@ -1231,8 +1276,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
           if (p < tile.n_valid) {
             double ps, pc, ss, sc, t[kComps];
             w[0].raw(p, ps, pc, ss, sc);
-            wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_d()), prof.turns_per,
-                            st_d(), t);
+            wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_b()), prof.turns_per,
+                            st_b(), t);
             // evict-first store: the results stream past L2 without pushing
             // out the loop chain the CTAs are sweeping
             __stcs(reinterpret_cast<double2*>(k.loops_out) +
@@ -1261,8 +1306,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
           double ps, pc, ss, sc, t[K];
           float sabs = 0.0f;
           w[0].raw(p, ps, pc, ss, sc);
-          wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_d()), prof.turns_per,
-                          st_d(), t, &sabs);
+          wilson_terms<A>(ps, pc, ss, sc, split(prof.turns_per), split(st_b()), prof.turns_per,
+                          st_b(), t, &sabs);
 #pragma unroll
           for (int q = 0; q < K; ++q)
             if (mine) acc[(p * K + q) * 33 + lane] += t[q];
@@ -1288,10 +1333,11 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
           // full loop's T/N (a constant field's spin is B T on every loop);
           // the nested walks of N, N/2 and N/4 points count 1, 2 and 4 times.
           const bool tube = prof.kind != WLN_PROFILE_CONST_B;
+          const double hs = half_spin ? 2.0 : 1.0;
           double po, so, pq, sq, pt, stt;
-          walk_sums(w[0], p, tube ? (NEST ? 1.0 : 2.0) : 1.0, po, so);
-          walk_sums(w[1], p, tube ? (NEST ? 2.0 : 4.0) : 1.0, pq, sq);
-          walk_sums(w[2], p, tube ? 4.0 : 1.0, pt, stt);
+          walk_sums(w[0], p, tube ? (NEST ? 1.0 : 2.0 * hs) : 1.0, po, so);
+          walk_sums(w[1], p, tube ? (NEST ? 2.0 : 4.0 * hs) : 1.0, pq, sq);
+          walk_sums(w[2], p, tube ? 4.0 * hs : 1.0, pt, stt);
           // Paper's levels: W_N = e^{i (circ/2 + sq/4 + tri/4)}, W_N/2 = e^{i circ},
           // W_N/4 = e^{i (sq + tri)/2}, the spins combined the same way.  Nested
           // levels: each walk is its own level.  One copy of the W arithmetic

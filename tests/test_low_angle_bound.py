@@ -14,10 +14,13 @@ Checked here:
     tan(theta) < 0.05;
   * the remainders of the series 1 - t^2/3 + t^4/5 (below t^6/7) and
     1 - t^2/3 + t^4/5 - t^6/7 + t^8/9 (below t^10/11) of atan(t)/t;
+  * the three-term form's spin integral int dt/Q^2 = 1/(Q0 Q1) +
+    C r^3 (1/3 - 2 t^2/5), against the closed form and a quadrature;
   * the per-block reading of u on a real ensemble against every segment's u;
   * the bench's accounting of the forms at the extremes (all or nothing).
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_1407_7486_gb300 import inputs as I
@@ -106,14 +109,15 @@ def test_accounting_extremes():
     const = I.Profile(I.PROFILE_CONST_B, B=1.0)
     assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0, 0.0)
     # the operation count: 6 fewer on the low form, 13 on the five-term series,
-    # 15 on the three-term one; without the five-term form its share takes 6
-    assert bench._n_alg(38.75, (1.0, 1.0, 1.0)) == 38.75 - 15
-    assert bench._n_alg(38.75, (1.0, 1.0, 0.0)) == 38.75 - 13
-    assert bench._n_alg(38.75, (1.0, 1.0, 0.0), mid_form=False) == 38.75 - 6
-    assert bench._n_alg(38.75, (1.0, 1.0, 1.0), mid_form=False) == 38.75 - 15
-
-
-import pytest
+    # 6 + 9 + 2 - 2/P on the three-term one (its spin series, C/3 and 2C/5
+    # shared by P radii); without the five-term form its share takes 6
+    base = bench.N_ALG_FP32
+    assert base == 16 + 17 + 11 / 4 + 1
+    assert bench._n_alg(base, (1.0, 1.0, 1.0)) == base - 16.5
+    assert bench._n_alg(base, (1.0, 1.0, 0.0)) == base - 13
+    assert bench._n_alg(base, (1.0, 1.0, 0.0), mid_form=False) == base - 6
+    assert bench._n_alg(base, (1.0, 1.0, 1.0), mid_form=False) == base - 16.5
+    assert bench._n_alg(base, (1.0, 1.0, 1.0), mid_form=False, P=3) == pytest.approx(base - (17 - 2 / 3))
 
 
 @pytest.mark.parametrize("u_max,terms,bound", [(0.045, 3, 2.3e-9), (0.15, 5, 3.3e-9)])
@@ -146,3 +150,41 @@ def test_series_forms_of_int_dt_over_q(u_max, terms, bound):
     Q = lam * lam + np.sum((r[:, None, :] + tq[None, :, None] * d[:, None, :]) ** 2, axis=2)
     quad = 0.5 * np.sum(w[None, :] / Q, axis=1)
     assert np.all(np.abs(series - quad) <= bound * quad + 1e-14 * quad)
+
+
+def test_series_form_of_int_dt_over_q2():
+    """The three-term form's spin integral: int_0^1 dt/Q^2 = -d/d(lambda^2)
+    int_0^1 dt/Q.  Shifting lambda^2 by e moves Q0 + B by e and D by C e, so
+    with int dt/Q = r f(t^2), f(u) = atan(sqrt u)/sqrt u, it is
+    r^2 [f - (C r - 2 t^2) f'] = 1/(Q0 Q1) + C r^3 h(t^2), h = -f' =
+    1/3 - 2u/5 + 3u^2/7 - ...  (r^2/(1 + t^2) = 1/(Q0 Q1)).  Two terms of h,
+    on segments with 2u <= 0.09, against the closed form
+    [(C + B)/Q1 - B/Q0 + C int dt/Q] / (2D) and a 400-point Gauss-Legendre
+    rule of the integral; the remainder bound is 3.6e-9 relative."""
+    rng = np.random.default_rng(9)
+    n = 20000
+    for lam in (0.1, 0.8, 3.0):
+        r = rng.normal(size=(n, 2)) * 3.0
+        d = rng.normal(size=(n, 2))
+        Q0 = lam * lam + np.sum(r * r, axis=1)
+        d *= (0.045 * np.sqrt(Q0) * rng.uniform(0.3, 1.0, size=n) /
+              np.linalg.norm(d, axis=1))[:, None]
+        theta, u = _theta_u(r, d, lam)
+        B = np.sum(r * d, axis=1)
+        C = np.sum(d * d, axis=1)
+        X = r[:, 0] * d[:, 1] - r[:, 1] * d[:, 0]
+        D = lam * lam * C + X * X
+        Q1 = Q0 + 2 * B + C
+        rr = 1.0 / (Q0 + B)
+        t2 = D * rr * rr
+        series = 1.0 / (Q0 * Q1) + C * rr ** 3 * (1.0 / 3.0 - 0.4 * t2)
+        x, w = np.polynomial.legendre.leggauss(400)
+        tq = 0.5 * (x + 1.0)
+        Q = lam * lam + np.sum((r[:, None, :] + tq[None, :, None] * d[:, None, :]) ** 2, axis=2)
+        quad = 0.5 * np.sum(w[None, :] / Q ** 2, axis=1)
+        assert np.all(np.abs(series - quad) <= 3.6e-9 * quad + 1e-14 * quad)
+        # the closed form, where it keeps its digits (it cancels for short segments)
+        closed = ((C + B) / Q1 - B / Q0 + C * theta / np.sqrt(D)) / (2 * D)
+        ok = C / Q0 > 1e-4
+        assert ok.sum() > n // 4
+        assert np.all(np.abs(series - closed)[ok] <= 1e-8 * closed[ok])
