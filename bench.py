@@ -53,10 +53,9 @@ def sm_count(dev: int = 0) -> int:
 # 1/D 1 and the two sums 2; 17 for the arctangent (range fold 2, quotient 1,
 # square 1, polynomial 8, octant unfolding 4, plus t*s 1); 11 per segment
 # shared by the lane's P = 4 radii (11/4); and two Kahan folds of 4
-# operations every 8 segments (1).  The level pass holds P = 3 radii per
-# lane: the shared part is 11/3.
+# operations every 8 segments (1).  The level passes hold P = 4 radii per
+# lane too, and a segment of a sub-loop costs the same as one of the loop.
 N_ALG_FP32 = 16 + 17 + 11 / 4 + 1
-N_ALG_FP32_LEVELS = 16 + 17 + 11 / 3 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
 # The FP64 comparison walk (2 radii per lane): the general form throughout,
 # the shared part over 2 radii, no compensated folds.
@@ -131,16 +130,12 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
     return (low / tot, mid / tot, tiny / tot) if tot else (0.0, 0.0, 0.0)
 
 
-def _n_alg(base: float, fr, mid_form: bool = True, P: int = 4) -> float:
+def _n_alg(base: float, fr, P: int = 4) -> float:
     """Operations per (segment, radius): the general form's count less what
     each cheaper form saves (6 on the pi/4 form; 7 more on the five-term
-    series, 11 - 2/P more on the three-term one).  Passes without the
-    five-term form walk its blocks with the pi/4 form."""
-    tiny = n_alg_tiny_saved(P)
-    if mid_form:
-        return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_MID_SAVED * fr[1] - \
-            (tiny - N_ALG_MID_SAVED) * fr[2]
-    return base - N_ALG_LOW_SAVED * fr[0] - tiny * fr[2]
+    series, 11 - 2/P more on the three-term one)."""
+    return base - N_ALG_LOW_SAVED * fr[0] - N_ALG_MID_SAVED * fr[1] - \
+        (n_alg_tiny_saved(P) - N_ALG_MID_SAVED) * fr[2]
 
 
 def _workload(name: str) -> I.Workload:
@@ -934,16 +929,14 @@ def run_levels(args, wl: I.Workload):
     # paper's levels: circle N/2 + square N/4 + triangle N/4 = N segments per
     # loop and point; nested levels: N + N/2 + N/4
     seg = wl.segment_evals * (1.75 if args.nested else 1.0)
-    n_alg, f_low = N_ALG_FP32_LEVELS, (0.0, 0.0, 0.0)
+    n_alg, f_low = N_ALG_FP32, (0.0, 0.0, 0.0)
     if args.prec == "fp32":
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
         # sub-loop segments join points up to 4 apart
-        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 3, 4.0)
-        if args.nested:     # the nested pass takes the low form but not the series
-            f_low = (f_low[0], 0.0, 0.0)
-        n_alg = _n_alg(N_ALG_FP32_LEVELS, f_low, mid_form=False, P=3)
+        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 4, 4.0)
+        n_alg = _n_alg(N_ALG_FP32, f_low)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (discretisation levels N, N/2, N/4 + extrapolation"
                         + (", nested loops)" if args.nested else ")"),

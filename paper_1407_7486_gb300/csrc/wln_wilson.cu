@@ -39,10 +39,7 @@
 // and for u <= 0.045 (tan(theta) < 0.05) from three, without 1/sqrt(D) (the
 // spin then takes 1/D; the result moves by rounding only).  The choice is
 // per block and the same on every lane, so the walk has no branch per
-// segment: the row loop exists once per form (three times for the paper's
-// levels, without the five-term series, and twice for the nested levels,
-// whose long loops pay more for further copies in instruction fetch than
-// the series save).
+// segment: the row loop exists once per form, in every mode.
 //
 // Discretisation levels (Sec. "Estimating the Discretization Uncertainties"):
 // the same pass can instead walk the three interleaved sub-loops of every
@@ -1168,8 +1165,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const bool valid = loop < k.n_loops;
     const int form = block_form(b);
     // the block's spin sums hold int dt/Q^2 itself, not twice it, where its
-    // segments take the three-term series (the nested walks do not)
-    const bool half_spin = WalkT::kSeriesSpin && !NEST && form == 3;
+    // segments take the three-term series
+    const bool half_spin = WalkT::kSeriesSpin && form == 3;
     // first point of each walk, for the closing segments
     float fx[NW], fy[NW];
 #pragma unroll
@@ -1211,17 +1208,24 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 #pragma unroll
             for (int q = 0; q < NW; ++q) { fx[q] = a.x; fy[q] = a.y; }
             w[0].start(a.x, a.y);
-            w[0].step(a.z, a.w);
-            w[0].step(v.x, v.y);
-            w[0].step(v.z, v.w);
             w[1].start(a.x, a.y);
-            w[1].step(v.x, v.y);
             w[2].start(a.x, a.y);
+            if (half_spin) {
+              w[0].template step_<3>(a.z, a.w);
+              w[0].template step_<3>(v.x, v.y);
+              w[0].template step_<3>(v.z, v.w);
+              w[1].template step_<3>(v.x, v.y);
+            } else {
+              w[0].step(a.z, a.w);
+              w[0].step(v.x, v.y);
+              w[0].step(v.z, v.w);
+              w[1].step(v.x, v.y);
+            }
             r = 2;
           }
-          // two copies only: a third of this long loop costs more in
-          // instruction fetch than the short series saves
-          if (form >= 1) rows_nested<1>(w, rowp, r, pp.chunk_rows);
+          if (form == 3) rows_nested<3>(w, rowp, r, pp.chunk_rows);
+          else if (form == 2) rows_nested<2>(w, rowp, r, pp.chunk_rows);
+          else if (form == 1) rows_nested<1>(w, rowp, r, pp.chunk_rows);
           else rows_nested<0>(w, rowp, r, pp.chunk_rows);
         } else {
           // Rows come in pairs (chunk_rows is even): row r even holds points
@@ -1238,10 +1242,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             w[2].start(v.z, v.w);
             r = 2;
           }
-          // no copy for the middle series (instruction fetch): its blocks
-          // take the pi/4 form
           if (form == 3) rows_levels<3>(w, rowp, r, pp.chunk_rows);
-          else if (form >= 1) rows_levels<1>(w, rowp, r, pp.chunk_rows);
+          else if (form == 2) rows_levels<2>(w, rowp, r, pp.chunk_rows);
+          else if (form == 1) rows_levels<1>(w, rowp, r, pp.chunk_rows);
           else rows_levels<0>(w, rowp, r, pp.chunk_rows);
         }
       }
@@ -1335,8 +1338,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
           const bool tube = prof.kind != WLN_PROFILE_CONST_B;
           const double hs = half_spin ? 2.0 : 1.0;
           double po, so, pq, sq, pt, stt;
-          walk_sums(w[0], p, tube ? (NEST ? 1.0 : 2.0 * hs) : 1.0, po, so);
-          walk_sums(w[1], p, tube ? (NEST ? 2.0 : 4.0 * hs) : 1.0, pq, sq);
+          walk_sums(w[0], p, tube ? (NEST ? 1.0 : 2.0) * hs : 1.0, po, so);
+          walk_sums(w[1], p, tube ? (NEST ? 2.0 : 4.0) * hs : 1.0, pq, sq);
           walk_sums(w[2], p, tube ? 4.0 * hs : 1.0, pt, stt);
           // Paper's levels: W_N = e^{i (circ/2 + sq/4 + tri/4)}, W_N/2 = e^{i circ},
           // W_N/4 = e^{i (sq + tri)/2}, the spins combined the same way.  Nested
@@ -1377,7 +1380,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
 // warps with up to 168; the other shapes 16 warps with up to 128.  Measured
 // on the paper workload: 4 radii x 4 warps x 3 CTAs 664 ms, 8 radii x 8 warps
 // x 1 CTA 659 ms, 4 radii x 8 warps x 2 CTAs 682 ms (spilling); the level
-// pass 3 radii x 4 warps x 2 CTAs 757 ms, 4 x 8 x 1 774 ms.
+// pass with the scalar walk 3 radii x 4 warps x 2 CTAs 757 ms, 4 x 8 x 1
+// 774 ms, with the radii in pairs 4 x 4 x 2 541 ms.
 constexpr int min_ctas(int P, int warps, int mode) {
   return (level_mode(mode) || P >= 8) ? 256 / (warps * 32)
                                          : (P == 4 && warps == 4) ? 3 : 512 / (warps * 32);
@@ -1440,10 +1444,10 @@ __global__ void __launch_bounds__(WARPS * 32, min_ctas(P, WARPS, MODE)) wilson_k
     const Tile& tile = k.tiles[t < k.n_tiles ? t : 0];
     const bool active = t < k.n_tiles && tile.n_valid > 0;   // n_valid 0: padding
     const ProfileDev& prof = k.profs[tile.profile];
-    // three walks per radius: Q fits in registers for up to 3 radii per lane
+    // three walks per radius: the scalar walk carries Q for up to 3 radii
     constexpr bool CQ = !level_mode(MODE) || P <= 3;
-    // float group sums and per-loop values walk the radii in pairs
-    constexpr bool PAIRED = sizeof(typename A::F) == 4 && P % 2 == 0 && !level_mode(MODE);
+    // the float flavours walk the radii in pairs, in every mode
+    constexpr bool PAIRED = sizeof(typename A::F) == 4 && P % 2 == 0;
     using TubeWalk = std::conditional_t<PAIRED, Walk2<A, (PAIRED ? P : 2)>, Walk<A, P, CQ>>;
     if (prof.kind == WLN_PROFILE_CONST_B)
       ok = run_item<A, P, WalkB<A, P>, MODE>(k, pp, acc, c, tile, prof, active, &abort_flag, lane,
@@ -1528,7 +1532,7 @@ size_t smem_bytes(const WilsonPlan& p, int ppl) {
 // walks per radius (4 radii per lane, FP64 1) and ignore the tuning of the
 // plain pass.
 int plan_points_per_lane(const wln_ctx* ctx, wln_prec prec, int mode) {
-  if (level_mode(mode)) return prec == WLN_PREC_FP64 ? 1 : 3;
+  if (level_mode(mode)) return prec == WLN_PREC_FP64 ? 1 : 4;
   if (mode == kModeLoops) return prec == WLN_PREC_FP64 ? 2 : 4;
   if (prec == WLN_PREC_FP64) return 2;
   return ctx->tune_P ? ctx->tune_P : 4;
@@ -1545,7 +1549,7 @@ WilsonPlan make_plan(const wln_ctx* ctx, const Ensemble& e, int n_tiles, wln_pre
   // Group sums: 4 radii x 8 warps, 2 CTAs per SM, 64-row chunks, 2 stages
   // (537 ms on the paper workload against 560 ms for 4 x 4 warps, 3 CTAs per
   // SM, 32 rows, 3 stages, once the low-angle forms made the walk lighter).
-  // Per-loop values keep (4, 4); the levels (3, 4), 2 CTAs per SM.
+  // Per-loop values keep (4, 4); the levels (4, 4), 2 CTAs per SM.
   const bool wide = !fixed && p.P == 4;
   const int def_warps = (level_mode(mode) || (p.P == 4 && !wide)) ? 4 : 8;
   p.warps = f64 ? 4 : ((!fixed && ctx->tune_warps) ? ctx->tune_warps : def_warps);
@@ -1619,16 +1623,16 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
 #define WLN_CASE(A, P_, W_) WLN_CASE_L(A, P_, W_, kModeSums)
   if (plan.mode == kModeLevels) {
     switch (prec) {
-      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 3, 4, kModeLevels) break;
-      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 3, 4, kModeLevels) break;
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 4, kModeLevels) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 4, kModeLevels) break;
       case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, kModeLevels) break;
     }
     return cudaErrorInvalidConfiguration;
   }
   if (plan.mode == kModeNested) {
     switch (prec) {
-      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 3, 4, kModeNested) break;
-      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 3, 4, kModeNested) break;
+      case WLN_PREC_FP32_COMP: WLN_CASE_L(F32Comp, 4, 4, kModeNested) break;
+      case WLN_PREC_FP32_NAIVE: WLN_CASE_L(F32Naive, 4, 4, kModeNested) break;
       case WLN_PREC_FP64: WLN_CASE_L(F64, 1, 4, kModeNested) break;
     }
     return cudaErrorInvalidConfiguration;

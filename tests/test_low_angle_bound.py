@@ -110,14 +110,13 @@ def test_accounting_extremes():
     assert bench.low_angle_fraction(y32, [const], [np.zeros(1)], [np.ones(1)], 4, 1.0) == (0.0, 0.0, 0.0)
     # the operation count: 6 fewer on the low form, 13 on the five-term series,
     # 6 + 9 + 2 - 2/P on the three-term one (its spin series, C/3 and 2C/5
-    # shared by P radii); without the five-term form its share takes 6
+    # shared by P radii)
     base = bench.N_ALG_FP32
     assert base == 16 + 17 + 11 / 4 + 1
     assert bench._n_alg(base, (1.0, 1.0, 1.0)) == base - 16.5
     assert bench._n_alg(base, (1.0, 1.0, 0.0)) == base - 13
-    assert bench._n_alg(base, (1.0, 1.0, 0.0), mid_form=False) == base - 6
-    assert bench._n_alg(base, (1.0, 1.0, 1.0), mid_form=False) == base - 16.5
-    assert bench._n_alg(base, (1.0, 1.0, 1.0), mid_form=False, P=3) == pytest.approx(base - (17 - 2 / 3))
+    assert bench._n_alg(base, (1.0, 0.0, 0.0)) == base - 6
+    assert bench._n_alg(base, (1.0, 1.0, 1.0), P=2) == pytest.approx(base - 16)
 
 
 @pytest.mark.parametrize("u_max,terms,bound", [(0.045, 3, 2.3e-9), (0.15, 5, 3.3e-9)])
