@@ -223,9 +223,14 @@ wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t
  * components stay float.  A group with more than 64 such loops per radius
  * keeps the rest in float (counted in wln_precision_guard_stats).  The
  * corrections are applied in a fixed order, so results stay independent of
- * the batch and of scheduling.  If the queue of loops to recompute fills
- * (more than n_points * n_loops / 512 of them, at least 65536) the call
- * returns WLN_ENOMEM, at the next synchronising call for a device output.
+ * the batch and of scheduling.  The queue of loops to recompute starts with
+ * 8 entries per (point, group) whose spin can reach 2 at all (T eB at the
+ * closest approach to the axis that the ensemble's loops allow), at least
+ * 65536; the call waits for the float pass to read how many loops it
+ * selected, and if they exceed the queue it runs the pass again with the
+ * queue sized to that number (the selection is deterministic).  A queue that
+ * still overflows leaves those loops in float and makes the call (for a device
+ * output, the next synchronising call) return WLN_ENOMEM.
  */
 wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
                           const wln_profile* profiles, int32_t n_profiles,
@@ -285,7 +290,9 @@ wln_status wln_precision_guard_stats(wln_ctx* ctx, int64_t* escalated_loops, int
  * bounded device wait: with a host output the call waits for the stream and
  * returns WLN_ETIMEOUT (and clears the device flag, so later calls start
  * clean); with a device output the flag is read by the next synchronising
- * call, as for wln_wilson_avg.
+ * call, as for wln_wilson_avg.  The precision guard's queue lives in the same
+ * array, sized as wln_wilson_avg first sizes it; it cannot grow, so a pass
+ * that selects more loops than it holds returns WLN_ENOMEM the same way.
  */
 wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* ens,
                                   const wln_profile* profiles, int32_t n_profiles,
@@ -573,8 +580,11 @@ wln_status wln_set_low_angle(wln_ctx* ctx, int32_t level);
  * are evenly spaced and its times geometric) the per-group effective action
  * of the spinor and the scalar loop.  use_graph != 0 records the pass into a
  * CUDA graph on the first call and replays the graph afterwards (the context
- * stream must not be the legacy default stream).  The ensemble must outlive
- * the batch.
+ * stream must not be the legacy default stream).  With the precision guard,
+ * the batch's first run is a direct one that waits for its float pass and, if
+ * the guard selected more loops than its queue holds, regrows the queue and
+ * runs the float pass again (as wln_wilson_avg does); the graph is recorded
+ * by the next use_graph call.  The ensemble must outlive the batch.
  * wln_batch_results copies the results out (each pointer may be NULL; host or
  * device): group_sums double[n_points][G][WLN_K]; stats double[4][n_points]
  * = mean and SEM of W_scal - 1, mean and SEM of W_ferm - 1; gamma
@@ -616,8 +626,11 @@ wln_status wln_batch_free(wln_ctx* ctx, wln_batch* batch);
  * 3 done, 4 cancelled) and, when done, copies the results (layouts as
  * wln_batch_results, n_profiles = 1; any pointer may be NULL; host memory).
  * wln_server_release drops a done or cancelled request's host results.
- * wln_server_step waits only when two steps are already in flight.  The server
- * is not thread-safe: drive it from one thread.
+ * wln_server_step waits only when two steps are already in flight.  Before a
+ * step is launched, its precision-guard queue is sized for every loop its
+ * points could select (64 per (point, group) whose spin can reach 2), grown
+ * when a step needs more than its slot holds.  The server is not thread-safe:
+ * drive it from one thread.
  */
 typedef struct wln_server wln_server;
 wln_status wln_server_create(wln_ctx* ctx, const wln_ensemble* ens, int32_t n_groups,

@@ -82,6 +82,10 @@ wln_status check_flag(wln_ctx* ctx) {
   if (h != 0) {
     cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
     cudaStreamSynchronize(ctx->stream);
+    if (h == kErrGuardQueue)
+      return fail(ctx, WLN_ENOMEM,
+                  "the precision guard's queue was full: some loops it selected kept float "
+                  "precision (see wln_precision_guard_stats)");
     return fail(ctx, WLN_ETIMEOUT,
                 h == kErrTimeoutFull    ? "a staged-copy wait ran out (device)"
                 : h == kErrTimeoutEmpty ? "a buffer-release wait ran out (device)"
@@ -157,6 +161,15 @@ wln_status finish_ensemble(wln_ctx* ctx, wln_ensemble* en, int* d_deg, wln_ensem
     wln_free_ensemble(ctx, en);
     return fail(ctx, WLN_EINVAL, "two consecutive loop points coincide (zero-length segment)");
   }
+  // the largest |y| of any loop, kept on the host for the precision guard's
+  // bound on which points can reach its spin floor
+  std::vector<float2> st(static_cast<size_t>(en->e.n_blocks));
+  err = cudaMemcpy(st.data(), en->e.stats, st.size() * sizeof(float2), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) {
+    wln_free_ensemble(ctx, en);
+    return cuda_fail(ctx, err, "ensemble statistics");
+  }
+  for (const float2& s : st) en->e.ymax = std::fmax(en->e.ymax, s.y);
   *out = en;
   return WLN_OK;
 }
@@ -628,87 +641,108 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   const int P = plan_points_per_lane(ctx, prec, mode);
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl, P, bt);
   if (bt.n_points > (int64_t(1) << 31) - 1) return fail(ctx, WLN_EINVAL, "too many points");
-  const bool use_guard =
-      guard_applies(ctx, prec, mode, ens->e.n_loops, n_groups, profiles, n_profiles);
+  // the precision guard runs where some point's spin can reach its floor; its
+  // queue first gets kGuardPerPair entries per such (point, group)
+  const int64_t guard_pts =
+      guard_applies(ctx, prec, mode, ens->e.n_loops, n_groups, profiles, n_profiles)
+          ? guard_points(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e)
+          : 0;
+  const bool use_guard = guard_pts > 0;
   const int bpg = guard_layout_bpg(prec, mode, ens->e.n_loops, n_groups);
   const WilsonPlan plan =
       make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, mode, bpg);
+  int64_t gcap = use_guard ? guard_capacity(guard_pts, n_groups, kGuardPerPair) : 0;
 
-  // Device layout of this call: work list | profiles | radii | partials |
-  // (precision guard: per-warp records, queue, counters) | (host output)
-  Carve cv;
-  const size_t o_tiles = cv.take<Tile>(bt.tiles.size());
-  const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
-  const size_t o_rho = cv.take<double>(bt.rho.size());
-  const size_t upload = cv.off;
-  const size_t n_partial =
-      per_loop ? 0 : static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
-  const size_t o_part = cv.take<double>(n_partial);
-  GuardBufs gb;
-  size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
-  int64_t gcap = 0;
-  if (use_guard) {
-    gb.on = 1;
-    gb.bpg = bpg;
-    gb.warp_bytes = guard_warp_bytes(bpg, plan.P);
-    gcap = guard_capacity(bt.n_points, ens->e.n_loops);
-    o_gscr = cv.take<char>(static_cast<size_t>(wilson_grid(plan, ens->e, prec)) * plan.warps *
-                           gb.warp_bytes);
-    o_gq = cv.take<char>(guard_queue_bytes(gcap));
-    o_gcnt = cv.take<int>(4);
-  }
-  const size_t n_out = per_loop ? static_cast<size_t>(bt.n_points) * ens->e.n_loops * 2
-                                : static_cast<size_t>(bt.n_points) * n_groups * K;
-  Out out = plan_out(cv, group_sums, n_out);
-  if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) return st;
-  if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
-  bind_out(out, ctx->scratch.ptr);
-
-  char* h = static_cast<char*>(ctx->pinned);
-  std::memcpy(h + o_tiles, bt.tiles.data(), bt.tiles.size() * sizeof(Tile));
-  std::memcpy(h + o_profs, bt.profs.data(), bt.profs.size() * sizeof(ProfileDev));
-  std::memcpy(h + o_rho, bt.rho.data(), bt.rho.size() * sizeof(double));
-  char* d = static_cast<char*>(ctx->scratch.ptr);
-  cudaError_t err = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ctx->stream);
-  if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "upload work list");
-
-  int64_t launches = 0;
-  if (per_loop) {
-    err = launch_wilson_loops(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
-                              at<ProfileDev>(d, o_profs), at<double>(d, o_rho), prec,
-                              static_cast<double*>(out.dev), ctx->d_flag, &launches, ctx->d_items);
-    ctx->launches += launches;
-    if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
-  } else {
-    const int32_t lpg = ens->e.n_loops / n_groups;
+  // A launch whose guard selected more loops than the queue holds is run again
+  // with the queue sized to exactly what it selected (the selection depends
+  // only on the float walk, so the second launch selects the same loops).
+  for (int attempt = 0;; ++attempt) {
+    // Device layout of this call: work list | profiles | radii | partials |
+    // (precision guard: per-warp records, queue, counters) | (host output)
+    Carve cv;
+    const size_t o_tiles = cv.take<Tile>(bt.tiles.size());
+    const size_t o_profs = cv.take<ProfileDev>(bt.profs.size());
+    const size_t o_rho = cv.take<double>(bt.rho.size());
+    const size_t upload = cv.off;
+    const size_t n_partial =
+        per_loop ? 0 : static_cast<size_t>(plan.n_chains + n_groups) * bt.n_points * K;
+    const size_t o_part = cv.take<double>(n_partial);
+    GuardBufs gb;
+    size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
     if (use_guard) {
-      guard_bind(gb, d + o_gscr, d + o_gq, gcap, at<int>(d, o_gcnt));
-      guard_attach(gb, ctx);
-      err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), ctx->stream);
-      if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard counters");
+      gb.on = 1;
+      gb.bpg = bpg;
+      gb.warp_bytes = guard_warp_bytes(bpg, plan.P);
+      o_gscr = cv.take<char>(static_cast<size_t>(wilson_grid(plan, ens->e, prec)) * plan.warps *
+                             gb.warp_bytes);
+      o_gq = cv.take<char>(guard_queue_bytes(gcap));
+      o_gcnt = cv.take<int>(4);
     }
-    err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
-                        at<ProfileDev>(d, o_profs), at<double>(d, o_rho), n_groups, lpg, prec,
-                        at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches,
-                        use_guard ? &gb : nullptr, ctx->d_items);
-    if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
-    if (use_guard) {
-      err = launch_guard(ctx->stream, gb, ens->e, at<Tile>(d, o_tiles), at<ProfileDev>(d, o_profs),
-                         at<double>(d, o_rho), at<double>(d, o_part), ctx->num_sms, &launches);
-      if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard");
+    const size_t n_out = per_loop ? static_cast<size_t>(bt.n_points) * ens->e.n_loops * 2
+                                  : static_cast<size_t>(bt.n_points) * n_groups * K;
+    Out out = plan_out(cv, group_sums, n_out);
+    if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) return st;
+    if ((st = ensure_pinned(ctx, upload)) != WLN_OK) return st;
+    bind_out(out, ctx->scratch.ptr);
+
+    char* h = static_cast<char*>(ctx->pinned);
+    std::memcpy(h + o_tiles, bt.tiles.data(), bt.tiles.size() * sizeof(Tile));
+    std::memcpy(h + o_profs, bt.profs.data(), bt.profs.size() * sizeof(ProfileDev));
+    std::memcpy(h + o_rho, bt.rho.data(), bt.rho.size() * sizeof(double));
+    char* d = static_cast<char*>(ctx->scratch.ptr);
+    cudaError_t err = cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ctx->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(ctx->staging_done, ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "upload work list");
+
+    int64_t launches = 0;
+    if (per_loop) {
+      err = launch_wilson_loops(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
+                                at<ProfileDev>(d, o_profs), at<double>(d, o_rho), prec,
+                                static_cast<double*>(out.dev), ctx->d_flag, &launches, ctx->d_items);
+      ctx->launches += launches;
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+    } else {
+      const int32_t lpg = ens->e.n_loops / n_groups;
+      if (use_guard) {
+        guard_bind(gb, d + o_gscr, d + o_gq, gcap, at<int>(d, o_gcnt));
+        guard_attach(gb, ctx);
+        err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), ctx->stream);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard counters");
+      }
+      err = launch_wilson(ctx->stream, plan, ens->e, at<Tile>(d, o_tiles),
+                          at<ProfileDev>(d, o_profs), at<double>(d, o_rho), n_groups, lpg, prec,
+                          at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches,
+                          use_guard ? &gb : nullptr, ctx->d_items);
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
+      if (use_guard) {
+        // the loops the float pass selected (the call waits for it here)
+        int selected = 0;
+        err = cudaMemcpyAsync(&selected, gb.counters, sizeof(int), cudaMemcpyDeviceToHost,
+                              ctx->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard queue");
+        if (selected > gcap && attempt == 0) {
+          ctx->launches += launches;
+          gcap = selected;
+          continue;
+        }
+        err = launch_guard(ctx->stream, gb, ens->e, at<Tile>(d, o_tiles),
+                           at<ProfileDev>(d, o_profs), at<double>(d, o_rho), at<double>(d, o_part),
+                           ctx->num_sms, &launches);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "precision guard");
+      }
+      err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
+                                   n_groups, lpg, static_cast<double*>(out.dev));
+      ++launches;
+      ctx->launches += launches;
+      if (err != cudaSuccess) return cuda_fail(ctx, err, "group reduction");
     }
-    err = launch_reduce_partials(ctx->stream, plan, ens->e, at<double>(d, o_part), bt.n_points,
-                                 n_groups, lpg, static_cast<double*>(out.dev));
-    ++launches;
-    ctx->launches += launches;
-    if (err != cudaSuccess) return cuda_fail(ctx, err, "group reduction");
+    if (out.host) {
+      if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy results");
+      return check_flag(ctx);
+    }
+    return WLN_OK;
   }
-  if (out.host) {
-    if ((err = copy_back(out, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, err, "copy results");
-    return check_flag(ctx);
-  }
-  return WLN_OK;
 }
 
 }  // namespace

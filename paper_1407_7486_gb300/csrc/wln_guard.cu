@@ -27,6 +27,8 @@
 // the float approximation.  The arctangent reduces its argument with a table
 // of atan(j/16) and sums five terms of the Taylor series.  Intrinsics with
 // explicit rounding keep the compiler from fusing the transformations.
+#include <cmath>
+
 #include "wln_internal.cuh"
 
 namespace wln {
@@ -266,7 +268,9 @@ __global__ void __launch_bounds__(128) guard_walk_kernel(GuardBufs g, const floa
 }
 
 // Adds each slot's corrections, in queue order, to the spinor components of
-// its partial sum; then counts the launch into the context totals.
+// its partial sum; then counts the launch into the context totals, and raises
+// the context's error flag if the queue could not hold every selected loop
+// (those selections kept float precision).
 __global__ void guard_fixup_kernel(GuardBufs g, double* partial) {
   const int64_t n = g.counters[1];
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -288,6 +292,8 @@ __global__ void guard_fixup_kernel(GuardBufs g, double* partial) {
     atomicAdd(&g.totals[2], static_cast<unsigned long long>(g.counters[3]));
     atomicAdd(&g.totals[3], 1ull);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && g.flag && g.counters[2] > 0)
+    atomicExch(g.flag, kErrGuardQueue);
 }
 
 }  // namespace
@@ -319,10 +325,32 @@ void guard_bind(GuardBufs& g, void* scratch, void* queue, int64_t cap, int* coun
 void guard_attach(GuardBufs& g, const wln_ctx* ctx) {
   g.all = ctx->guard == 2;
   g.totals = ctx->d_guard_totals;
+  g.flag = ctx->d_flag;
 }
 
-int64_t guard_capacity(int64_t n_points, int32_t n_loops) {
-  const int64_t c = n_points * static_cast<int64_t>(n_loops) / 512;
+bool guard_point_reaches(const wln_profile& pr, double rho, double T, const Ensemble& e) {
+  if (pr.kind != WLN_PROFILE_FLUX_TUBE) return false;
+  const double pi = 3.14159265358979323846;
+  const double l2 = pr.lambda * pr.lambda;
+  const double gap = std::fmax(0.0, rho - std::sqrt(T) * 1.01 * static_cast<double>(e.ymax));
+  const double den = l2 + gap * gap;
+  return T * 2.0 * std::fabs(pr.F) / (2.0 * pi) * l2 / (den * den) >= 0.9 * kGuardFloor;
+}
+
+int64_t guard_points(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                     const int32_t* rho_off, const double* T, const int32_t* T_off,
+                     const Ensemble& e) {
+  int64_t n = 0;
+  for (int q = 0; q < n_profiles; ++q)
+    for (int32_t it = T_off[q]; it < T_off[q + 1]; ++it)
+      for (int32_t ir = rho_off[q]; ir < rho_off[q + 1]; ++ir)
+        n += guard_point_reaches(profiles[q], rho_cm[ir], T[it], e);
+  return n;
+}
+
+int64_t guard_capacity(int64_t n_points, int32_t n_groups, int per_pair) {
+  if (n_points <= 0) return 0;
+  const int64_t c = n_points * n_groups * static_cast<int64_t>(per_pair);
   return c < 65536 ? 65536 : c;
 }
 

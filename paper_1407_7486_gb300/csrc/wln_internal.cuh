@@ -43,10 +43,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// Device error flag values (bounded waits that ran out).
+// Device error flag values: bounded waits that ran out, and a precision-guard
+// queue that could not hold every loop its launch selected.
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
 constexpr int kErrTimeoutSelfTest = 3;
+constexpr int kErrGuardQueue = 4;
 
 struct Ensemble {
   int64_t loop0 = 0;          // global index of the first loop (Philox counter word 1)
@@ -58,6 +60,7 @@ struct Ensemble {
   float2* stats = nullptr;    // [n_blocks]: longest segment, largest |y| of the block's loops
   float* maxlen = nullptr;    // [n_blocks]: longest loop (sum of its segment lengths), in
                               // the same allocation as stats
+  float ymax = 0.0f;          // host copy of the largest |y| of any loop (host-side bounds)
 };
 
 // Per-profile constants used by the Wilson kernels.
@@ -125,6 +128,9 @@ struct GuardSlot {
   int32_t n;
 };
 constexpr int kGuardSel = 64;   // loops a warp may select per (group, radius)
+constexpr float kGuardFloor = 2.0f;   // blocks whose largest spin stays below are not recorded
+constexpr int kGuardPerPair = 8;      // queue entries provided per (point, group) that can
+                                      // reach the floor, before a launch shows its need
 struct GuardBufs {
   int on = 0;
   int all = 0;                  // select every recorded loop (a check of the double-float walk)
@@ -138,6 +144,7 @@ struct GuardBufs {
   int64_t cap = 0;              // items (and slots) the queue holds
   int* counters = nullptr;      // this launch: items, slots, overflows, saturated selections
   unsigned long long* totals = nullptr;   // the context's running totals (wln_precision_guard_stats)
+  int* flag = nullptr;          // the context's device error flag (kErrGuardQueue on overflow)
 };
 
 struct Scratch {
@@ -242,7 +249,17 @@ int guard_layout_bpg(wln_prec prec, int mode, int32_t n_loops, int32_t n_groups)
 bool guard_applies(const wln_ctx* ctx, wln_prec prec, int mode, int32_t n_loops,
                    int32_t n_groups, const wln_profile* profiles, int32_t n_profiles);
 size_t guard_warp_bytes(int bpg, int P);
-int64_t guard_capacity(int64_t n_points, int32_t n_loops);
+// Points whose spin can reach kGuardFloor at all: spin <= T eB(gap), eB(r) =
+// 2 calF lambda^2 / (lambda^2 + r^2)^2 the tube's field, gap = max(0, rho -
+// sqrt(T) ymax) the closest any loop comes to the axis (a 1% margin on ymax
+// and 10% on the floor).  Only these can put loops in the guard's queue.
+bool guard_point_reaches(const wln_profile& pr, double rho, double T, const Ensemble& e);
+int64_t guard_points(const wln_profile* profiles, int32_t n_profiles, const double* rho_cm,
+                     const int32_t* rho_off, const double* T, const int32_t* T_off,
+                     const Ensemble& e);
+// Queue entries for n_points such points: per_pair per (point, group), at
+// least 65536; 0 when no point can reach the floor.
+int64_t guard_capacity(int64_t n_points, int32_t n_groups, int per_pair);
 size_t guard_queue_bytes(int64_t cap);
 void guard_bind(GuardBufs& g, void* scratch, void* queue, int64_t cap, int* counters);
 // The context's mode and running totals into g.

@@ -142,8 +142,11 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
   if (n_tiles > (int64_t(1) << 30) || n_points > (int64_t(1) << 30))
     return fail(ctx, WLN_EINVAL, "too many points");
   const int32_t n_rho = rho_off[n_profiles], n_T = T_off[n_profiles];
-  const bool use_guard =
-      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles);
+  const int64_t guard_pts =
+      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles)
+          ? guard_points(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e)
+          : 0;
+  const bool use_guard = guard_pts > 0;
   const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
   const WilsonPlan plan =
       make_plan(ctx, ens->e, static_cast<int>(n_tiles), prec, kModeSums, bpg);
@@ -174,7 +177,7 @@ extern "C" wln_status wln_wilson_avg_noalloc(wln_ctx* ctx, const wln_ensemble* e
     gb.on = 1;
     gb.bpg = bpg;
     gb.warp_bytes = guard_warp_bytes(bpg, plan.P);
-    gcap = guard_capacity(n_points, ens->e.n_loops);
+    gcap = guard_capacity(guard_pts, n_groups, kGuardPerPair);
     o_gscr = take(static_cast<size_t>(wilson_grid(plan, ens->e, prec)) * plan.warps *
                   gb.warp_bytes);
     o_gq = take(guard_queue_bytes(gcap));

@@ -50,22 +50,29 @@ struct wln_batch {
   cudaGraphExec_t graph = nullptr;
   int64_t kernels_per_run = 0;
   GuardBufs guard;            // precision guard (FP32 compensated, whole-block groups)
+  void* guard_queue = nullptr;   // its queue (regrown to the first run's need, if larger)
+  bool guard_checked = false;    // the first run has shown the queue holds what it selects
   int num_sms = 0;
   int* items = nullptr;       // the Wilson launch's item counter (the creating context's)
 };
 
 namespace {
 
-cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* launches) {
+// The float pass (with the guard's selection) of a batch run.
+cudaError_t enqueue_wilson(wln_batch* b, cudaStream_t s, int* flag, int64_t* launches) {
   cudaError_t err = cudaSuccess;
   if (b->guard.on) err = cudaMemsetAsync(b->guard.counters, 0, 4 * sizeof(int), s);
   if (err != cudaSuccess) return err;
-  err = launch_wilson(s, b->plan, b->ens->e, b->tiles, b->profs, b->rho, b->n_groups, b->lpg,
-                      b->prec, b->partial, b->n_points, flag, launches,
-                      b->guard.on ? &b->guard : nullptr, b->items);
-  if (err != cudaSuccess) return err;
-  err = launch_guard(s, b->guard, b->ens->e, b->tiles, b->profs, b->rho, b->partial, b->num_sms,
-                     launches);
+  return launch_wilson(s, b->plan, b->ens->e, b->tiles, b->profs, b->rho, b->n_groups, b->lpg,
+                       b->prec, b->partial, b->n_points, flag, launches,
+                       b->guard.on ? &b->guard : nullptr, b->items);
+}
+
+// The rest of a batch run: the guard's recomputation, the reduction, the
+// statistics and the effective action.
+cudaError_t enqueue_rest(wln_batch* b, cudaStream_t s, int64_t* launches) {
+  cudaError_t err = launch_guard(s, b->guard, b->ens->e, b->tiles, b->profs, b->rho, b->partial,
+                                 b->num_sms, launches);
   if (err != cudaSuccess) return err;
   err = launch_reduce_partials(s, b->plan, b->ens->e, b->partial, b->n_points, b->n_groups,
                                b->lpg, b->sums);
@@ -85,6 +92,21 @@ cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* laun
   return launch_effective_action(s, b->quad, b->n_profiles, b->rho, b->T, b->sums, b->n_groups,
                                  b->lpg, 0, b->gg + gstride, b->gamma + 2 * b->n_profiles,
                                  launches);
+}
+
+cudaError_t enqueue_batch(wln_batch* b, cudaStream_t s, int* flag, int64_t* launches) {
+  cudaError_t err = enqueue_wilson(b, s, flag, launches);
+  return err != cudaSuccess ? err : enqueue_rest(b, s, launches);
+}
+
+// A (re)allocated guard queue of cap entries, bound to the batch's guard.
+cudaError_t bind_guard_queue(wln_batch* b, int64_t cap) {
+  if (b->guard_queue) cudaFree(b->guard_queue);
+  b->guard_queue = nullptr;
+  cudaError_t err = cudaMalloc(&b->guard_queue, guard_queue_bytes(cap));
+  if (err != cudaSuccess) return err;
+  guard_bind(b->guard, b->guard.scratch, b->guard_queue, cap, b->guard.counters);
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -144,8 +166,11 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   build_batch(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e.ppl,
               plan_points_per_lane(ctx, prec), bt);
   b->n_points = bt.n_points;
-  const bool use_guard =
-      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles);
+  const int64_t guard_pts =
+      guard_applies(ctx, prec, kModeSums, ens->e.n_loops, n_groups, profiles, n_profiles)
+          ? guard_points(profiles, n_profiles, rho_cm, rho_off, T, T_off, ens->e)
+          : 0;
+  const bool use_guard = guard_pts > 0;
   const int bpg = guard_layout_bpg(prec, kModeSums, ens->e.n_loops, n_groups);
   b->plan = make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, kModeSums, bpg);
   b->num_sms = ctx->num_sms;
@@ -168,16 +193,15 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   const size_t o_stats = take(sizeof(double) * kStats * static_cast<size_t>(b->n_points));
   const size_t o_gg = take(sizeof(double) * 2 * static_cast<size_t>(n_profiles) * n_groups);
   const size_t o_gamma = take(sizeof(double) * 4 * static_cast<size_t>(n_profiles));
-  size_t o_gscr = 0, o_gq = 0, o_gcnt = 0;
+  size_t o_gscr = 0, o_gcnt = 0;
   int64_t gcap = 0;
   if (use_guard) {
     b->guard.on = 1;
     b->guard.bpg = bpg;
     b->guard.warp_bytes = guard_warp_bytes(bpg, b->plan.P);
-    gcap = guard_capacity(b->n_points, ens->e.n_loops);
+    gcap = guard_capacity(guard_pts, n_groups, kGuardPerPair);
     o_gscr = take(static_cast<size_t>(wilson_grid(b->plan, ens->e, prec)) * b->plan.warps *
                   b->guard.warp_bytes);
-    o_gq = take(guard_queue_bytes(gcap));
     o_gcnt = take(4 * sizeof(int));
   }
   cudaError_t err = cudaMalloc(&b->mem, off);
@@ -197,8 +221,15 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   b->gg = reinterpret_cast<double*>(d + o_gg);
   b->gamma = reinterpret_cast<double*>(d + o_gamma);
   if (use_guard) {
-    guard_bind(b->guard, d + o_gscr, d + o_gq, gcap, reinterpret_cast<int*>(d + o_gcnt));
+    b->guard.scratch = d + o_gscr;
+    b->guard.counters = reinterpret_cast<int*>(d + o_gcnt);
     guard_attach(b->guard, ctx);   // mode and statistics of the creating context
+    err = bind_guard_queue(b, gcap);
+    if (err != cudaSuccess) {
+      cudaFree(b->mem);
+      delete b;
+      return cuda_fail(ctx, err, "cudaMalloc batch guard queue");
+    }
   }
   std::vector<char> h(upload, 0);
   std::memcpy(h.data() + o_tiles, bt.tiles.data(), sizeof(Tile) * bt.tiles.size());
@@ -208,6 +239,7 @@ wln_status wln_batch_create(wln_ctx* ctx, const wln_ensemble* ens, const wln_pro
   if (b->has_action) std::memcpy(h.data() + o_quad, qp.data(), sizeof(QuadProfile) * n_profiles);
   err = cudaMemcpy(d, h.data(), upload, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
+    if (b->guard_queue) cudaFree(b->guard_queue);
     cudaFree(b->mem);
     delete b;
     return cuda_fail(ctx, err, "upload batch");
@@ -220,6 +252,28 @@ wln_status wln_batch_run(wln_ctx* ctx, wln_batch* b, int32_t use_graph) {
   if (!ctx || !b) return fail(ctx, WLN_EINVAL, "null argument");
   if (b->device != ctx->device) return fail(ctx, WLN_EINVAL, "batch lives on another device");
   DeviceGuard guard(ctx->device);
+  if (b->guard.on && !b->guard_checked) {
+    // The first run goes direct and waits for its float pass: if the guard
+    // selected more loops than its queue holds, the queue is regrown to that
+    // number and the float pass runs again.  A batch's inputs are fixed, so
+    // later runs (and their graph) select the same loops.
+    int64_t launches = 0;
+    cudaError_t err = enqueue_wilson(b, ctx->stream, ctx->d_flag, &launches);
+    int selected = 0;
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(&selected, b->guard.counters, sizeof(int), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+    if (err == cudaSuccess && selected > b->guard.cap) {
+      err = bind_guard_queue(b, selected);
+      if (err == cudaSuccess) err = enqueue_wilson(b, ctx->stream, ctx->d_flag, &launches);
+    }
+    if (err == cudaSuccess) err = enqueue_rest(b, ctx->stream, &launches);
+    ctx->launches += launches;
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "batch run");
+    b->guard_checked = true;
+    return WLN_OK;
+  }
   if (!use_graph) {
     int64_t launches = 0;
     cudaError_t err = enqueue_batch(b, ctx->stream, ctx->d_flag, &launches);
@@ -292,6 +346,7 @@ wln_status wln_batch_free(wln_ctx* ctx, wln_batch* b) {
   DeviceGuard guard(b->device);
   if (ctx) cudaStreamSynchronize(ctx->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->guard_queue) cudaFree(b->guard_queue);
   if (b->mem) cudaFree(b->mem);
   delete b;
   return WLN_OK;
@@ -389,9 +444,12 @@ struct wln_server {
   int cur = 0;
   int64_t steps = 0;
   // precision guard: per-warp records shared by the steps (they run in stream
-  // order), a queue and counters per step slot
+  // order), a queue and counters per step slot; a slot's queue is sized before
+  // each step for everything its points could select (kGuardSel loops per
+  // (point, group) that can reach the spin floor), grown when a step needs more
   GuardBufs guard[2];
   char* d_guard = nullptr;
+  void* guard_queue[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -565,8 +623,27 @@ wln_status launch_step(wln_server* sv, int slot) {
   plan.n_tile_groups = static_cast<int>(pick.size());
   plan.n_items = static_cast<int64_t>(plan.n_chains) * plan.n_tile_groups;
   int64_t launches = 0;
-  const GuardBufs& gb = sv->guard[slot];
-  if (err == cudaSuccess && gb.on) err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), s);
+  GuardBufs& gb = sv->guard[slot];
+  if (err == cudaSuccess && gb.on) {
+    int64_t reach = 0;
+    for (auto& [id, tg] : pick) {
+      const Request& r = sv->reqs[id];
+      for (int j = 0; j < sv->warps; ++j) {
+        const Tile& tl = r.tiles[static_cast<size_t>(tg) * sv->warps + j];
+        for (int p = 0; p < tl.n_valid; ++p)
+          reach += guard_point_reaches(r.prof, r.rho[tl.rho0 + p], tl.T, sv->ens->e);
+      }
+    }
+    const int64_t need = guard_capacity(reach, sv->G, kGuardSel);
+    if (need > gb.cap) {
+      // this slot's previous step has retired, so its queue is idle
+      if (sv->guard_queue[slot]) cudaFree(sv->guard_queue[slot]);
+      sv->guard_queue[slot] = nullptr;
+      err = cudaMalloc(&sv->guard_queue[slot], guard_queue_bytes(need));
+      if (err == cudaSuccess) guard_bind(gb, gb.scratch, sv->guard_queue[slot], need, gb.counters);
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(gb.counters, 0, 4 * sizeof(int), s);
+  }
   if (err == cudaSuccess)
     err = launch_wilson(s, plan, sv->ens->e, reinterpret_cast<Tile*>(d + o_tiles),
                         reinterpret_cast<ProfileDev*>(d + o_profs),
@@ -632,17 +709,15 @@ wln_status wln_server_create(wln_ctx* ctx, const wln_ensemble* ens, int32_t n_gr
   if (err == cudaSuccess && use_guard) {
     const size_t scr = align256(static_cast<size_t>(wilson_grid(sv->base, ens->e, prec)) *
                                 sv->base.warps * guard_warp_bytes(bpg, sv->P));
-    const int64_t cap = guard_capacity(static_cast<int64_t>(tile_groups_per_step) * sv->warps *
-                                           sv->P, ens->e.n_loops);
-    const size_t q = align256(guard_queue_bytes(cap)), cnt = 256;
-    err = cudaMalloc(reinterpret_cast<void**>(&sv->d_guard), scr + 2 * (q + cnt));
+    const size_t cnt = 256;
+    err = cudaMalloc(reinterpret_cast<void**>(&sv->d_guard), scr + 2 * cnt);
     for (int i = 0; i < 2 && err == cudaSuccess; ++i) {
       GuardBufs& g = sv->guard[i];
       g.on = 1;
       g.bpg = bpg;
       g.warp_bytes = guard_warp_bytes(bpg, sv->P);
-      guard_bind(g, sv->d_guard, sv->d_guard + scr + i * (q + cnt), cap,
-                 reinterpret_cast<int*>(sv->d_guard + scr + i * (q + cnt) + q));
+      // the queue comes with the first step that needs one
+      guard_bind(g, sv->d_guard, nullptr, 0, reinterpret_cast<int*>(sv->d_guard + scr + i * cnt));
       guard_attach(g, ctx);
     }
   }
@@ -814,6 +889,8 @@ wln_status wln_server_free(wln_server* sv) {
     if (sv->d_step[i]) cudaFree(sv->d_step[i]);
   }
   if (sv->d_guard) cudaFree(sv->d_guard);
+  for (void* q : sv->guard_queue)
+    if (q) cudaFree(q);
   for (int i = 0; i < 2; ++i) {
     if (sv->h_step[i]) cudaFreeHost(sv->h_step[i]);
     if (sv->step_done[i]) cudaEventDestroy(sv->step_done[i]);

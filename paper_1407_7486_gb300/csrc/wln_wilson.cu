@@ -921,7 +921,6 @@ __device__ __forceinline__ void rows_levels(WalkT* w, const float4* rowp, int r,
 // rho/(lambda^2 + rho^2) over the block's reach, 1/(2 lambda) if the block
 // comes within lambda of the axis.  Loops below kGuardFloor have cosh(spin)
 // < 3.77 and are not recorded; the model counts them in bulk.
-constexpr float kGuardFloor = 2.0f;
 constexpr float kCoshFloor = 3.76219569f;   // cosh(2)
 constexpr float kGuardBeta = 5e-8f;
 constexpr float kGuardCph = 2e-7f;

@@ -134,3 +134,50 @@ def test_guard_is_deterministic_in_every_path(ctx):
     assert np.all(np.abs(res[0][:, :, 1] - ref[:, :, 1]) <= 1e-12 * np.maximum(cs, lpg))
     sv.free()
     ens.free()
+
+
+def _strong_grid():
+    # 1024 loops of 256 points in 16 groups of 2 blocks, a strong tube on
+    # 16 x 16 points where every block reaches spin 2: with every recorded loop
+    # recomputed (mode "all"), a pass selects all 64 loops of every (point,
+    # group), 262144 in all, four times the 65536 entries the queue starts with
+    return (I.Profile(0, F=50.0, lam=1.0), I.lin_grid(0.0, 1.0, 16), I.log_grid(2.0, 20.0, 16), 16)
+
+
+def test_queue_grows_to_what_the_float_pass_selects(ctx):
+    """A pass whose guard selects more loops than the queue first holds runs
+    again with the queue sized to them: no selection is dropped, the
+    double-float results match the oracle, and a batch does the same on its
+    first run (its later graph replays give the same bits)."""
+    prof, rho, T, G = _strong_grid()
+    y32, ens = _ens(ctx, 43, 1024, 256)
+    y = y32.astype(np.float64)
+    lpg = 1024 // G
+    ctx.set_precision_guard("all")
+    try:
+        ctx.precision_guard_stats(reset=True)
+        S = ctx.wilson_avg(ens, [prof], [rho], [T], G, prec="fp32", where="host")
+        st = ctx.precision_guard_stats(reset=True)
+        bt = wln.Batch(ctx, ens, [prof], [rho], [T], G, prec="fp32")
+        bt.run(graph=True)
+        first = bt.results()[0]
+        bt.run(graph=True)
+        bt.run(graph=True)
+        replay = bt.results()[0]
+        st_b = ctx.precision_guard_stats(reset=True)
+        bt.free()
+    finally:
+        ctx.set_precision_guard(True)
+    n_sel = len(rho) * len(T) * G * 64
+    assert st["overflows"] == 0 and st["escalated_loops"] == n_sel, st
+    assert st_b["overflows"] == 0 and st_b["escalated_loops"] == 3 * n_sel, st_b
+    assert np.array_equal(first, S) and np.array_equal(replay, S)
+    ref = oracle.group_sums(y, prof, rho, T, G)
+    cosh = np.zeros((len(T) * len(rho), G))
+    for b, t in enumerate(T):
+        for a, r in enumerate(rho):
+            _, sp = oracle.phase_spin(y, prof, r, t)
+            cosh[b * len(rho) + a] = np.cosh(sp).reshape(G, -1).sum(axis=1)
+    err = np.abs(S[:, :, 1] - ref[:, :, 1]) / np.maximum(cosh, lpg)
+    assert err.max() <= 1e-10
+    ens.free()

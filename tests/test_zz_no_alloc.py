@@ -92,3 +92,26 @@ def test_noalloc_rejects_problems_beyond_its_array(ctx):
         ctx.wilson_avg_noalloc(ens, *big, prec="fp32")
     assert "MiB" in str(e.value)
     ens.free()
+
+
+def test_noalloc_reports_a_full_guard_queue(ctx):
+    # The fixed array cannot grow the precision guard's queue.  With every
+    # recorded loop recomputed (guard mode "all"), a strong tube on 16 x 16
+    # points selects 64 loops per (point, group), 131072 in all, twice the
+    # 65536 entries the queue holds: the call returns WLN_ENOMEM instead of
+    # leaving loops in float silently, the flag is cleared, and the next call
+    # (guard in its normal mode) matches wln_wilson_avg.
+    prof = I.Profile(0, F=50.0, lam=1.0)
+    args = ([prof], [I.lin_grid(0.0, 1.0, 16)], [I.log_grid(2.0, 20.0, 16)], 8)
+    ens = ctx.gen_loops(25, 1024, 256)
+    ctx.set_precision_guard("all")
+    try:
+        with pytest.raises(wln.WlnError) as e:
+            ctx.wilson_avg_noalloc(ens, *args, prec="fp32", where="host")
+        assert e.value.status == wln.WLN_ENOMEM and "queue" in str(e.value)
+    finally:
+        ctx.set_precision_guard(True)
+    ref = ctx.wilson_avg(ens, *args, prec="fp32", where="host")
+    got = ctx.wilson_avg_noalloc(ens, *args, prec="fp32", where="host")
+    assert np.array_equal(got, ref)
+    ens.free()
