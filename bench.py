@@ -462,6 +462,17 @@ def precision_corners(wl: I.Workload, gpu_ctx, n_groups: int = 2):
                       f"T in {{T_mid, T_max}}", "rows": out}
 
 
+def _guard_line(guard: dict, steps: int, loop_points: int) -> dict:
+    """Loops the precision guard recomputed in double-float per step (and as a
+    fraction of the step's loop-point evaluations), (group, radius)
+    selections it left in float because 64 loops would not bring its estimate
+    under the budget, and selections dropped because its queue was full."""
+    return {"escalated_loops_per_step": guard["escalated_loops"] / steps,
+            "fraction_of_loop_points": guard["escalated_loops"] / steps / loop_points,
+            "saturated_per_step": guard["saturated"] / steps,
+            "overflows": guard["overflows"]}
+
+
 def sampled_oracle_error(y32, profiles, rhos, Ts, S, n_groups: int, n_samples: int = 16,
                          seed: int = 3):
     """Error of group sums S (points ordered profile, T, rho) against the FP64
@@ -707,13 +718,8 @@ def main():
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
-        # loops the precision guard recomputed in double-float (per step), as a
-        # fraction of the step's loop-point evaluations
-        "precision_guard": {
-            "escalated_loops_per_step": guard["escalated_loops"] / args.steps,
-            "fraction_of_loop_points": guard["escalated_loops"] / args.steps / loop_points,
-            "saturated_per_step": guard["saturated"] / args.steps,
-            "overflows": guard["overflows"]} if args.prec == "fp32" else None,
+        "precision_guard": _guard_line(guard, args.steps, loop_points)
+        if args.prec == "fp32" else None,
     }
     if wl.meta.get("quad"):
         # the step's physics: spinor effective action per flux tube, mean +- group
@@ -808,10 +814,12 @@ def run_batched(args, wl: I.Workload):
     with torch.cuda.stream(stream):
         tuned = autotune.tune(ctx, ens, wl.profiles, wl.rho, wl.T, wl.n_groups, use_cache=False)
         b = wln.Batch(ctx, ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
+        b.run(graph=False)      # the first run sizes the precision guard's queue
         for _ in range(args.warmup):
-            b.run(graph=True)
+            b.run(graph=True)   # the first records the graph
         stream.synchronize()
         n0 = ctx.launch_count
+        ctx.precision_guard_stats(reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(0) as clk:
             e0.record(stream)
@@ -819,6 +827,7 @@ def run_batched(args, wl: I.Workload):
                 b.run(graph=True)
             e1.record(stream)
             stream.synchronize()
+    guard = ctx.precision_guard_stats(reset=True)
     ms = e0.elapsed_time(e1) / args.steps
     S, st, g = b.results()
     peaks, peak_kind = _peaks()
@@ -837,6 +846,7 @@ def run_batched(args, wl: I.Workload):
                         "kernel_ms": ms, "note": "whole graph pass timed (Wilson > 99%)"}
     line["gpu_launches"] = int(ctx.launch_count - n0)
     line["clocks"] = clk.summary()
+    line["precision_guard"] = _guard_line(guard, args.steps, wl.loop_points)
     # end to end through the public API: build the batch from the host grids
     # (work list upload), one graph pass, results read back to the host
     with torch.cuda.stream(stream):
@@ -1192,6 +1202,7 @@ def _serve_replay(ctx, ens, cfg, reqs, scales, prec):
             label = f"{scale} x capacity = {rate:.3f} req/s"
         sv = wln.Server(ctx, ens, cfg["n_groups"], prec=prec, arena_bytes=16 << 30,
                         tile_groups_per_step=128)
+        ctx.precision_guard_stats(reset=True)
         t0 = time.perf_counter()
         pending = list(range(len(reqs)))
         ids, done_at = {}, {}
@@ -1223,10 +1234,14 @@ def _serve_replay(ctx, ens, cfg, reqs, scales, prec):
         thr = lp / makespan
         if scale == "sat":
             capacity = len(reqs) / makespan
+        guard = ctx.precision_guard_stats(reset=True)
         runs.append({"rate": label, "requests": len(reqs),
                      "p50_ms": float(np.percentile(lat, 50)),
                      "p99_ms": float(np.percentile(lat, 99)), "loop_point_evals_per_s": thr,
-                     "makespan_s": makespan, "steps": sv.info()["steps"], "clocks": clk.summary()})
+                     "makespan_s": makespan, "steps": sv.info()["steps"], "clocks": clk.summary(),
+                     "precision_guard": {"escalated_loops": guard["escalated_loops"],
+                                         "saturated": guard["saturated"],
+                                         "overflows": guard["overflows"]}})
         sv.free()
     return runs, capacity
 
