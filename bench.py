@@ -57,9 +57,14 @@ def sm_count(dev: int = 0) -> int:
 # lane too, and a segment of a sub-loop costs the same as one of the loop.
 N_ALG_FP32 = 16 + 17 + 11 / 4 + 1
 N_ALG_MUFU = 3      # 1/Q, 1/sqrt(D), and the reciprocal inside the arctangent
-# The FP64 comparison walk (2 radii per lane): the general form throughout,
-# the shared part over 2 radii, no compensated folds.
+# The FP64 comparison walk (2 radii per lane): the general form, the shared
+# part over 2 radii, no compensated folds.  On blocks with tan(theta) < 0.05
+# it takes series long enough for double precision: int dt/Q = r f(t^2) with
+# six terms (r^2, t^2, 5 FMAs, r times it) and int dt/Q^2 = 1/(Q0 Q1) +
+# C r^3 h(t^2) with five terms of h (r^3, C r^3, 4 FMAs), the two sums: 23
+# per radius instead of 33, 10 fewer.
 N_ALG_FP64 = 16 + 17 + 11 / 2
+N_ALG_FP64_TINY_SAVED = 10
 # Where every segment of a block subtends at most pi/4 at the axis the kernel
 # takes the arctangent's low form, which needs neither the range fold (2) nor
 # the octant unfolding (4): 6 operations fewer per (segment, point).  Below
@@ -363,13 +368,18 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     rho = wl.rho[q][::stride]
     T = wl.T[q][::stride]
     lpg = wl.n_loops // wl.n_groups
+    # the oracle works on the GPU ensemble's own float loops (its generator's
+    # float copy can differ by one rounding at boundary cases, which would show
+    # as an error of the Wilson path)
+    ens = gpu_ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+    y_all, _ = gpu_ctx.loops_copy(ens)
     # calibrate on one group at every sampled point (enough (point, group) pairs for all threads)
-    y = oracle.gen_loops(wl.seed, lpg, wl.ppl).astype(np.float32).astype(np.float64)
+    y = y_all[:lpg].astype(np.float64)
     t0 = time.perf_counter()
     oracle.group_sums(y, prof, rho, T, 1, threads=threads)
     per_group = max(time.perf_counter() - t0, 1e-6)
     n_groups = int(max(1, min(wl.n_groups, budget_s / per_group)))
-    y = oracle.gen_loops(wl.seed, n_groups * lpg, wl.ppl).astype(np.float32).astype(np.float64)
+    y = y_all[:n_groups * lpg].astype(np.float64)
     t0 = time.perf_counter()
     ref = oracle.group_sums(y, prof, rho, T, n_groups, threads=threads)
     dt = time.perf_counter() - t0
@@ -383,7 +393,6 @@ def cpu_baseline(wl: I.Workload, gpu_ctx, prec_tol=1e-6, budget_s: float = 15.0)
     # GPU result on the same sample (same loops: the first n_groups groups of the ensemble)
     err = {}
     cs = _cosh_group_sums(y, prof, rho, T, n_groups)
-    ens = gpu_ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
     for prec in ("fp32", "fp64"):
         S = gpu_ctx.wilson_avg(ens, [prof], [rho], [T], wl.n_groups, prec=prec, where="host")
         S = S[:, :n_groups]
@@ -753,18 +762,22 @@ def main():
         stream.synchronize()
         n_lp = wl.n_loops * len(sub_rho[0]) * len(sub_T[0])
         f64_s = a.elapsed_time(b) / 1e3
-        # the same algorithmic count as the float walk's general form, in FP64
-        # operations, against the FP64 pipe (the library's atan2, division and
-        # square root take more operations than counted, which shows as a
-        # lower fraction)
+        # the float walk's count in FP64 operations, with the share of segment
+        # evaluations on the double-precision series form, against the FP64
+        # pipe (the library's atan2, division and square root take more
+        # operations than counted, which shows as a lower fraction)
+        y64f, _ = ctx.loops_copy(ens)
+        f3 = low_angle_fraction(y64f, [wl.profiles[q]], sub_rho, sub_T, 2, 1.0)[2]
+        n_alg_64 = N_ALG_FP64 - N_ALG_FP64_TINY_SAVED * f3
         f64_peak = sm_count() * FP64_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-        f64_ach = N_ALG_FP64 * n_lp * wl.ppl / f64_s / 1e12
+        f64_ach = n_alg_64 * n_lp * wl.ppl / f64_s / 1e12
         line["fp64_gpu"] = {"value": n_lp / f64_s, "unit": "loop-point evals/s",
                             "sample": f"F={wl.profiles[q].F}, {len(sub_rho[0])} rho x "
                                       f"{len(sub_T[0])} T, all loops, Wilson kernel only",
                             "roofline": {"bound": "fp64", "achieved": f64_ach, "peak": f64_peak,
                                          "unit": "T FP64 op/s", "frac": f64_ach / f64_peak,
-                                         "n_alg_fp64_per_segment": N_ALG_FP64,
+                                         "n_alg_fp64_per_segment": n_alg_64,
+                                         "series_fraction": f3,
                                          "peak_basis": f"{sm_count()} SMs x {FP64_LANES_PER_SM} "
                                                        f"FP64 lanes x {sm_mhz:.0f} MHz"},
                             # Wilson kernel rates, FP32 compensated over FP64
@@ -978,12 +991,14 @@ def run_levels(args, wl: I.Workload):
     if not args.no_cpu_baseline:
         q = 1 if len(wl.profiles) > 1 else 0
         prof, rho, T = wl.profiles[q], wl.rho[q][::4], wl.T[q][::4]
-        y = oracle.gen_loops(wl.seed, wl.n_loops, wl.ppl).astype(np.float32).astype(np.float64)
+        # the oracle on the GPU ensemble's own float loops
+        ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+        y32, _ = ctx.loops_copy(ens)
+        y = y32.astype(np.float64)
         t0 = time.perf_counter()
         lev = ost.nested_level_sums if args.nested else ost.level_sums
         ref = lev(oracle, y, prof, rho, T, wl.n_groups, threads=oracle.max_threads())
         dt = time.perf_counter() - t0
-        ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         G = ctx.wilson_levels(ens, [prof], [rho], [T], wl.n_groups, prec=args.prec, where="host",
                               nested=args.nested)
         ens.free()

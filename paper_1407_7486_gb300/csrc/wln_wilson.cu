@@ -197,6 +197,7 @@ struct F32Comp {
   using F = float;
   static constexpr bool kCompensated = true;
   static constexpr bool kLowAngle = true;
+  static constexpr bool kFiveTerm = true;   // the tan(theta) < 0.18 series form
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   template <int FORM>
@@ -211,6 +212,7 @@ struct F32Naive {
   using F = float;
   static constexpr bool kCompensated = false;
   static constexpr bool kLowAngle = true;
+  static constexpr bool kFiveTerm = true;
   __device__ static float rcp(float x) { return rcp_approx(x); }
   __device__ static float rsq(float x) { return rsqrt_approx(x); }
   template <int FORM>
@@ -221,10 +223,15 @@ struct F32Naive {
                        : atan2_pos(y, x);
   }
 };
+// The FP64 flavour takes the three-term form's place with series long enough
+// for double precision (below): on blocks with tan(theta) < 0.05 it needs
+// neither the arctangent nor 1/sqrt(D); elsewhere the library's atan2 (its
+// pi/4 form is the general one).
 struct F64 {
   using F = double;
   static constexpr bool kCompensated = false;
-  static constexpr bool kLowAngle = false;
+  static constexpr bool kLowAngle = true;
+  static constexpr bool kFiveTerm = false;
   __device__ static double rcp(double x) { return 1.0 / x; }
   __device__ static double rsq(double x) { return rsqrt(x); }
   template <int FORM>
@@ -367,7 +374,10 @@ struct Walk {
     const F rydy = ry * dy, rydx = ry * dx;
     // C h(t^2) = C/3 - (2C/5) t^2 on the three-term form (values the radii share)
     F c3 = F(0), cn25 = F(0);
-    if constexpr (FORM == 3 && CQ) { c3 = C * F(0.333333343); cn25 = C * F(-0.4); }
+    if constexpr (FORM == 3 && CQ && sizeof(F) == 4) {
+      c3 = C * F(0.333333343);
+      cn25 = C * F(-0.4);
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const F rx1 = fma(s, x1, rho[p]);
@@ -386,7 +396,14 @@ struct Walk {
         const F r2 = r * r;
         const F t2 = D * r2;
         F poly;
-        if constexpr (FORM == 3) {
+        if constexpr (FORM == 3 && sizeof(F) == 8) {
+          // double: six terms, remainder below t^12/13 < 2e-17
+          poly = fma(t2, -1.0 / 11.0, 1.0 / 9.0);
+          poly = fma(t2, poly, -1.0 / 7.0);
+          poly = fma(t2, poly, 0.2);
+          poly = fma(t2, poly, -1.0 / 3.0);
+          poly = fma(t2, poly, 1.0);
+        } else if constexpr (FORM == 3) {
           poly = fma(t2, fma(t2, F(0.2), F(-0.333333343)), F(1));
         } else {
           poly = fma(t2, F(0.111111112), F(-0.142857149));
@@ -396,7 +413,15 @@ struct Walk {
         }
         const F J1 = r * poly;
         ph[p].add(X, J1);
-        if constexpr (FORM == 3) {
+        if constexpr (FORM == 3 && sizeof(F) == 8) {
+          // double: h to five terms (remainder below C r (6/13) t^10, 1e-16)
+          F h = fma(t2, 5.0 / 11.0, -4.0 / 9.0);
+          h = fma(t2, h, 3.0 / 7.0);
+          h = fma(t2, h, -0.4);
+          h = fma(t2, h, 1.0 / 3.0);
+          sp[p].add(C * (r2 * r), h);
+          sp[p].add(rq[p], rq1);
+        } else if constexpr (FORM == 3) {
           // int dt/Q^2 = C r^3 (1/3 - 2 t^2/5) + 1/(Q0 Q1)  (unit: see above)
           sp[p].add(r2 * r, fma(t2, cn25, c3));
           sp[p].add(rq[p], rq1);
@@ -1132,7 +1157,8 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
                       static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
                       static_cast<float>(prof.l2)};
-    const int f = la.block(k, b);
+    int f = la.block(k, b);
+    if (!A::kFiveTerm && f == 2) f = 1;
     return k.low_angle >= 2 ? f : min(f, k.low_angle);   // level 2: the series forms too
   };
   const int b0 = c * k.chain;
