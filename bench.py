@@ -972,7 +972,7 @@ def run_levels(args, wl: I.Workload):
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
                         "traffic": _ncu_traffic(("wilson_nested_" if args.nested else "wilson_levels_")
                                                 + args.workload),
-                        "kernel": "wilson_kernel<F32Comp,3,4,%s>" % ("nested" if args.nested else "levels"),
+                        "kernel": "wilson_kernel<F32Comp,4,4,%s>" % ("nested" if args.nested else "levels"),
                         "kernel_ms": kern_ms,
                         "segment_evals_per_s": seg / (kern_ms / 1e3),
                         "n_alg_fp32_per_segment": n_alg, "low_angle_fraction": f_low[0],
