@@ -657,10 +657,13 @@ def main():
     t0 = time.perf_counter()
     e2e_steps = args.steps
     h2d = d2h = 0
+    step_ms = []
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
+            ts = time.perf_counter()
             outs, h2d, d2h = run_step(ctx, wl, seed, args.prec, where="host", cov=True,
                                       loop0=loop0, bufs=bufs)
+            step_ms.append((time.perf_counter() - ts) * 1e3)
     stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _max_over_ranks(e2e_s, ws)
@@ -724,7 +727,8 @@ def main():
                      "peak_basis": f"{sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{sm_mhz:.0f} MHz ({peak_kind} max SM clock)"},
         "e2e": {"value": loop_points * ws / e2e_s, "unit": "loop-point evals/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "step_ms": [round(v, 1) for v in step_ms]},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "precision_guard": _guard_line(guard, args.steps, loop_points)

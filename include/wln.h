@@ -223,14 +223,16 @@ wln_status wln_philox_stream(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t
  * components stay float.  A group with more than 64 such loops per radius
  * keeps the rest in float (counted in wln_precision_guard_stats).  The
  * corrections are applied in a fixed order, so results stay independent of
- * the batch and of scheduling.  The queue of loops to recompute starts with
- * 8 entries per (point, group) whose spin can reach 2 at all (T eB at the
- * closest approach to the axis that the ensemble's loops allow), at least
- * 65536; the call waits for the float pass to read how many loops it
- * selected, and if they exceed the queue it runs the pass again with the
- * queue sized to that number (the selection is deterministic).  A queue that
- * still overflows leaves those loops in float and makes the call (for a device
- * output, the next synchronising call) return WLN_ENOMEM.
+ * the batch and of scheduling.  The queue of loops to recompute holds 64
+ * entries per (point, group) whose spin can reach 2 at all (T eB at the
+ * closest approach to the axis that the ensemble's loops allow), everything
+ * a pass can select, when that is at most 2^22 entries.  Beyond that it
+ * starts with 8 per such (point, group); the call then waits for the float
+ * pass to read how many loops it selected, and if they exceed the queue it
+ * runs the pass again with the queue sized to that number (the selection is
+ * deterministic).  A queue that still overflows leaves those loops in float
+ * and makes the call (for a device output, the next synchronising call)
+ * return WLN_ENOMEM.
  */
 wln_status wln_wilson_avg(wln_ctx* ctx, const wln_ensemble* ens,
                           const wln_profile* profiles, int32_t n_profiles,

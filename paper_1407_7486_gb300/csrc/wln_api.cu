@@ -150,8 +150,15 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
 }
 
 wln_status finish_ensemble(wln_ctx* ctx, wln_ensemble* en, int* d_deg, wln_ensemble** out) {
+  // the degeneracy flag, and the block statistics for the largest |y| of any
+  // loop (kept on the host for the precision guard's bound on which points
+  // can reach its spin floor), read back with one wait
   int deg = 0;
+  std::vector<float2> st(static_cast<size_t>(en->e.n_blocks));
   cudaError_t err = cudaMemcpyAsync(&deg, d_deg, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(st.data(), en->e.stats, st.size() * sizeof(float2),
+                          cudaMemcpyDeviceToHost, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
@@ -160,14 +167,6 @@ wln_status finish_ensemble(wln_ctx* ctx, wln_ensemble* en, int* d_deg, wln_ensem
   if (deg) {
     wln_free_ensemble(ctx, en);
     return fail(ctx, WLN_EINVAL, "two consecutive loop points coincide (zero-length segment)");
-  }
-  // the largest |y| of any loop, kept on the host for the precision guard's
-  // bound on which points can reach its spin floor
-  std::vector<float2> st(static_cast<size_t>(en->e.n_blocks));
-  err = cudaMemcpy(st.data(), en->e.stats, st.size() * sizeof(float2), cudaMemcpyDeviceToHost);
-  if (err != cudaSuccess) {
-    wln_free_ensemble(ctx, en);
-    return cuda_fail(ctx, err, "ensemble statistics");
   }
   for (const float2& s : st) en->e.ymax = std::fmax(en->e.ymax, s.y);
   *out = en;
@@ -651,11 +650,15 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
   const int bpg = guard_layout_bpg(prec, mode, ens->e.n_loops, n_groups);
   const WilsonPlan plan =
       make_plan(ctx, ens->e, static_cast<int>(bt.tiles.size()), prec, mode, bpg);
-  int64_t gcap = use_guard ? guard_capacity(guard_pts, n_groups, kGuardPerPair) : 0;
-
-  // A launch whose guard selected more loops than the queue holds is run again
-  // with the queue sized to exactly what it selected (the selection depends
-  // only on the float walk, so the second launch selects the same loops).
+  // A queue of kGuardSel entries per such (point, group) holds anything a
+  // pass can select; up to 2^22 entries (192 MiB) the call takes that and need
+  // not wait.  Otherwise a launch whose guard selected more loops than the
+  // queue holds is run again with the queue sized to exactly what it
+  // selected (the selection depends only on the float walk, so the second
+  // launch selects the same loops).
+  const int64_t worst = use_guard ? guard_capacity(guard_pts, n_groups, kGuardSel) : 0;
+  int64_t gcap = worst <= (int64_t(1) << 22) ? worst
+                                              : guard_capacity(guard_pts, n_groups, kGuardPerPair);
   for (int attempt = 0;; ++attempt) {
     // Device layout of this call: work list | profiles | radii | partials |
     // (precision guard: per-warp records, queue, counters) | (host output)
@@ -714,7 +717,7 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
                           at<double>(d, o_part), bt.n_points, ctx->d_flag, &launches,
                           use_guard ? &gb : nullptr, ctx->d_items);
       if (err != cudaSuccess) return cuda_fail(ctx, err, "Wilson kernel");
-      if (use_guard) {
+      if (use_guard && gcap < worst) {
         // the loops the float pass selected (the call waits for it here)
         int selected = 0;
         err = cudaMemcpyAsync(&selected, gb.counters, sizeof(int), cudaMemcpyDeviceToHost,
@@ -726,6 +729,8 @@ wln_status wilson_pass(wln_ctx* ctx, const wln_ensemble* ens, const wln_profile*
           gcap = selected;
           continue;
         }
+      }
+      if (use_guard) {
         err = launch_guard(ctx->stream, gb, ens->e, at<Tile>(d, o_tiles),
                            at<ProfileDev>(d, o_profs), at<double>(d, o_rho), at<double>(d, o_part),
                            ctx->num_sms, &launches);

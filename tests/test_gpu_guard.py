@@ -138,17 +138,20 @@ def test_guard_is_deterministic_in_every_path(ctx):
 
 def _strong_grid():
     # 1024 loops of 256 points in 16 groups of 2 blocks, a strong tube on
-    # 16 x 16 points where every block reaches spin 2: with every recorded loop
+    # 64 T x 80 rho where every block reaches spin 2: with every recorded loop
     # recomputed (mode "all"), a pass selects all 64 loops of every (point,
-    # group), 262144 in all, four times the 65536 entries the queue starts with
-    return (I.Profile(0, F=50.0, lam=1.0), I.lin_grid(0.0, 1.0, 16), I.log_grid(2.0, 20.0, 16), 16)
+    # group), 5,242,880 in all.  That is above the 2^22 entries a call takes
+    # up front, so the queue starts at 8 per (point, group), 655,360, and the
+    # float pass's count has to regrow it
+    return (I.Profile(0, F=50.0, lam=1.0), I.lin_grid(0.0, 1.0, 80), I.log_grid(2.0, 20.0, 64), 16)
 
 
 def test_queue_grows_to_what_the_float_pass_selects(ctx):
     """A pass whose guard selects more loops than the queue first holds runs
     again with the queue sized to them: no selection is dropped, the
-    double-float results match the oracle, and a batch does the same on its
-    first run (its later graph replays give the same bits)."""
+    double-float results match the oracle (on sampled points), and a batch
+    does the same on its first run (its later graph replays give the same
+    bits)."""
     prof, rho, T, G = _strong_grid()
     y32, ens = _ens(ctx, 43, 1024, 256)
     y = y32.astype(np.float64)
@@ -172,12 +175,13 @@ def test_queue_grows_to_what_the_float_pass_selects(ctx):
     assert st["overflows"] == 0 and st["escalated_loops"] == n_sel, st
     assert st_b["overflows"] == 0 and st_b["escalated_loops"] == 3 * n_sel, st_b
     assert np.array_equal(first, S) and np.array_equal(replay, S)
-    ref = oracle.group_sums(y, prof, rho, T, G)
-    cosh = np.zeros((len(T) * len(rho), G))
-    for b, t in enumerate(T):
-        for a, r in enumerate(rho):
-            _, sp = oracle.phase_spin(y, prof, r, t)
-            cosh[b * len(rho) + a] = np.cosh(sp).reshape(G, -1).sum(axis=1)
-    err = np.abs(S[:, :, 1] - ref[:, :, 1]) / np.maximum(cosh, lpg)
-    assert err.max() <= 1e-10
+    rng = np.random.default_rng(44)
+    worst = 0.0
+    for p in rng.choice(len(rho) * len(T), 32, replace=False):
+        r, t = rho[p % len(rho)], T[p // len(rho)]
+        ref = oracle.group_sums(y, prof, [r], [t], G)[0]
+        _, sp = oracle.phase_spin(y, prof, r, t)
+        cosh = np.cosh(sp).reshape(G, -1).sum(axis=1)
+        worst = max(worst, float((np.abs(S[p, :, 1] - ref[:, 1]) / np.maximum(cosh, lpg)).max()))
+    assert worst <= 1e-10, worst
     ens.free()
