@@ -71,3 +71,48 @@ def test_strongest_points(ctx, case):
         print(f"F={F} lam={lam} {prec}: scalar {scal:.2e}, spinor / <cosh s> {ferm:.2e}")
         assert scal <= bar and ferm <= bar, (prec, scal, ferm)
     ens.free()
+
+
+# Wide strong tubes on the serving ensemble (32768 loops x 4096 points, 1024
+# loops per group): every loop of a group carries a similar large spin, so the
+# guard's model often finds 64 recomputed loops too few and leaves the group
+# in float (a "saturated" selection); the float walk itself must then hold the
+# plain bar.
+WIDE = [(100.0, 3.0), (100.0, 2.0), (60.0, 1.5), (100.0, 1.0)]
+
+
+@pytest.fixture(scope="module")
+def serving_ensemble(ctx):
+    cfg = I.serving_ensemble()
+    ens = ctx.gen_loops(cfg["seed"], cfg["n_loops"], cfg["ppl"])
+    y32, _ = ctx.loops_copy(ens)
+    yield ens, y32, cfg["n_groups"]
+    ens.free()
+
+
+@pytest.mark.parametrize("case", range(len(WIDE)))
+def test_wide_tubes_at_1024_loops_per_group(ctx, serving_ensemble, case):
+    ens, y32, G = serving_ensemble
+    F, lam = WIDE[case]
+    prof = I.Profile(0, F=F, lam=lam)
+    rho = np.array([0.0, 0.5, 1.0, 2.0]) * lam
+    T = np.array([2.0, 5.0, 10.0])
+    lpg = y32.shape[0] // G
+    ctx.precision_guard_stats(reset=True)
+    S = ctx.wilson_avg(ens, [prof], [rho], [T], G, prec="fp32", where="host")
+    st = ctx.precision_guard_stats(reset=True)
+    assert st["overflows"] == 0
+    worst_s = worst_f = 0.0
+    for b, t in enumerate(T):
+        for a, r in enumerate(rho):
+            p = b * len(rho) + a
+            for g in range(0, G, 4):
+                yg = y32[g * lpg:(g + 1) * lpg].astype(np.float64)
+                ref = oracle.group_sums(yg, prof, [r], [t], 1)[0, 0]
+                _, sp = oracle.phase_spin(yg, prof, r, t)
+                cs = float(np.cosh(sp).sum())
+                worst_s = max(worst_s, abs(S[p, g, 0] - ref[0]) / lpg)
+                worst_f = max(worst_f, abs(S[p, g, 1] - ref[1]) / max(cs, lpg))
+    print(f"F={F} lam={lam}: {st['saturated']} saturated selections; scalar {worst_s:.2e}, "
+          f"spinor / <cosh s> {worst_f:.2e}")
+    assert worst_s <= 1e-6 and worst_f <= 1e-6
