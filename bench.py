@@ -44,6 +44,37 @@ def sm_count(dev: int = 0) -> int:
     """Streaming multiprocessors of the device (cudaDevAttrMultiProcessorCount)."""
     import torch
     return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def l2_bytes(dev: int = 0) -> int:
+    """The device's L2 size (cudaDevAttrL2CacheSize)."""
+    import torch
+    return int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 128 << 20)
+
+
+class L2Flush:
+    """Between timed iterations whose inputs fit in L2: write a buffer of
+    twice the L2's size, outside the iteration's own events, so that every
+    iteration starts from DRAM."""
+
+    def __init__(self, dev: int, stream):
+        import torch
+        self.stream = stream
+        self.buf = torch.empty(2 * l2_bytes(dev), dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def __call__(self):
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.buf.fill_(1)
+
+
+def l2_note(ens_bytes: int, flushed: bool, how: str, dev: int = 0) -> str:
+    """The config's statement of how timed iterations meet L2."""
+    mb = ens_bytes / 1e6
+    if flushed:
+        return (f"inputs < L2 (loop ensemble {mb:.1f} MB, {how}): L2 flushed between timed "
+                f"iterations ({2 * l2_bytes(dev) / 1e6:.0f} MB written outside their events)")
+    return f"inputs > L2 (loop ensemble {mb:.0f} MB, {how})"
 # Algorithmic FP32 operations per (segment, point) of the compensated walk,
 # counted from the formulas in csrc/wln_wilson.cu (an FMA, a min/max or a
 # select each count 1; a product added into a sum is one FMA): 16 per radius
@@ -614,17 +645,25 @@ def main():
             run_step(ctx, wl, seed, args.prec, loop0=loop0)
     stream.synchronize()
 
-    # device-resident timed region
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # device-resident timed region; an ensemble that fits in L2 gets a flush
+    # before every step, outside the step's events
+    ens_bytes = wl.n_loops * wl.ppl * 8
+    flush = L2Flush(dev, stream) if ens_bytes < l2_bytes(dev) else None
+    st = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     wk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     launches0 = ctx.launch_count
     ctx.precision_guard_stats(reset=True)
     _barrier(ws)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev) as clk, torch.cuda.stream(stream):
         e0.record(stream)
         for i in range(args.steps):
+            if flush:
+                flush()
+            st[i][0].record(stream)
             ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
             wk[i][0].record(stream)
             S = ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=args.prec)
@@ -638,13 +677,15 @@ def main():
                 off += n
             _action(ctx, wl, S, lpg)
             ens.free()
+            st[i][1].record(stream)
         e1.record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
     _barrier(ws)
     launches = ctx.launch_count - launches0
     guard = ctx.precision_guard_stats(reset=True)
-    ms = e0.elapsed_time(e1) / args.steps
+    # the whole timed region, or with flushes the steps' own events
+    ms = (sum(a.elapsed_time(b) for a, b in st) if flush else e0.elapsed_time(e1)) / args.steps
     ms = _max_over_ranks(ms, ws)
     wilson_ms = statistics.mean(a.elapsed_time(b) for a, b in wk)
     loop_points = wl.loop_points
@@ -702,7 +743,7 @@ def main():
                    "n_points": wl.n_points, "n_groups": wl.n_groups,
                    "precision": "fp32 compensated" if args.prec == "fp32" else "fp64",
                    "covariance": "full, spinor, per profile",
-                   "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"},
+                   "l2": l2_note(ens_bytes, flush is not None, "regenerated every step", dev)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                      "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "wilson_kernel<F32Comp,4,8>" if args.prec == "fp32" else "wilson_kernel<F64,2,4>",
@@ -856,6 +897,7 @@ def run_batched(args, wl: I.Workload):
                         args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
                         {"workload": wl.name, "n_points": wl.n_points, "n_profiles": len(wl.profiles),
                          "graph": "one CUDA graph per pass (Wilson, reduction, statistics, action)",
+                         "l2": l2_note(wl.n_loops * wl.ppl * 8, False, "resident"),
                          "tiles": {"P": b.P, "chain_blocks": b.chain, "rows": tuned["rows"],
                                    "stages": tuned["stages"], "tuner": tuned["source"]}})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
@@ -971,7 +1013,7 @@ def run_levels(args, wl: I.Workload):
                         args.warmup, ms, "f32" if args.prec == "fp32" else "f64",
                         {"workload": wl.name, "n_loops": wl.n_loops, "ppl": wl.ppl,
                          "n_points": wl.n_points, "n_groups": wl.n_groups,
-                         "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
+                         "l2": l2_note(wl.n_loops * wl.ppl * 8, False, "regenerated every step")})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
                         "traffic": _ncu_traffic(("wilson_nested_" if args.nested else "wilson_levels_")
@@ -1103,7 +1145,7 @@ def run_correlation(args, wl: I.Workload):
                         {"workload": f"{wl.name}; one tube (F={prof[0].F}), per-loop values "
                                      f"{W.numel() * 8 / 1e9:.1f} GB", "n_loops": wl.n_loops,
                          "ppl": wl.ppl, "n_points": n_points, "n_groups": wl.n_groups,
-                         "l2": "inputs > L2 (loop ensemble 168 MB regenerated every step)"})
+                         "l2": l2_note(wl.n_loops * wl.ppl * 8, False, "regenerated every step")})
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                         "unit": "T FP32 op/s", "frac": achieved / peak_ops,
                         "traffic": _ncu_traffic(f"wilson_loops_{args.workload}"),
@@ -1142,10 +1184,13 @@ def run_sweep(args):
     stream = torch.cuda.Stream(0)
     ctx = wln.Context(0, stream)
     rows = []
+    flush = L2Flush(0, stream)
     n0 = ctx.launch_count
     with ClockSampler(0) as clk, torch.cuda.stream(stream):
         for ppl in (256, 1024, 4096, 16384):
             wl = I.sweep(ppl)
+            ens_bytes = wl.n_loops * ppl * 8
+            flushed = ens_bytes < l2_bytes(0)
             lpg = wl.n_loops // wl.n_groups
             ens = ctx.gen_loops(wl.seed, wl.n_loops, ppl)
             y32, _ = ctx.loops_copy(ens)
@@ -1159,13 +1204,16 @@ def run_sweep(args):
             for prec in ("fp64", "fp32", "fp32_naive"):
                 reps = 1 if prec == "fp64" else 3
                 ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(reps):
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(reps)]
+                for a, b in ev:
+                    if flushed:
+                        flush()
+                    a.record(stream)
                     ctx.wilson_avg(ens, wl.profiles, wl.rho, wl.T, wl.n_groups, prec=prec)
-                b.record(stream)
+                    b.record(stream)
                 stream.synchronize()
-                ms = a.elapsed_time(b) / reps
+                ms = sum(a.elapsed_time(b) for a, b in ev) / reps
                 e_s = e_f = e_c = 0.0
                 by_prof = []
                 for prof, r_s, t_s, ref, cs in subs:
@@ -1179,6 +1227,7 @@ def run_sweep(args):
                     by_prof.append(_ferm_scaled_err(S, ref, cs, lpg)[0])
                     e_c = max(e_c, by_prof[-1])
                 rows.append({"ppl": ppl, "prec": prec, "ms": ms,
+                             "l2": l2_note(ens_bytes, flushed, "resident"),
                              "ferm_max_rel_to_cosh": e_c,
                              "ferm_rel_to_cosh_by_profile": by_prof,
                              "loop_point_evals_per_s": wl.loop_points / (ms / 1e3),
@@ -1323,7 +1372,8 @@ def run_serve(args):
                         "loop-point evals/s", len(reqs), 0, None, "f32",
                         {"workload": f"serving: {cfg['n_loops']} loops x {cfg['ppl']} ppl, G={cfg['n_groups']}, "
                                      f"first {len(reqs)} requests of the seed-7 Poisson stream",
-                         "arena": "16 GiB", "tile_groups_per_step": 128})
+                         "arena": "16 GiB", "tile_groups_per_step": 128,
+                         "l2": l2_note(cfg["n_loops"] * cfg["ppl"] * 8, False, "resident")})
     line["serve"] = runs
     line["capacity_req_per_s"] = capacity
     line["gpu_error_vs_oracle_sampled"] = dict(

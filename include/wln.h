@@ -138,6 +138,10 @@ wln_status wln_selftest_wait(wln_ctx* ctx, int32_t timeout_ms);
  * Then, in double precision: xi <- xi - mean(xi) (closure), y_k = sum_{j<k}
  * xi_j, y <- y - mean(y) (common centre of mass, d-loop step 5).  The points
  * are stored as float on the device.  keep_fp64 != 0 also keeps a double copy.
+ * The raw increments are held in the context's scratch between drawing and
+ * closing: 16 bytes per point plus chunk sums (a sixteenth of that from
+ * ppl = 256 on), in slices of blocks of at most 1 GiB; WLN_ENOMEM if it
+ * cannot grow.
  * Rules: ppl a power of two, 4 <= ppl <= 16384; 1 <= n_loops <= 2^24.
  * The call synchronises.  It returns WLN_EINVAL if two consecutive stored
  * points coincide (a zero-length segment), which has negligible probability.

@@ -474,11 +474,15 @@ wln_status wln_gen_loops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_l
   wln_ensemble* en = nullptr;
   if ((st = alloc_ensemble(ctx, n_loops, ppl, keep_fp64 != 0, &en)) != WLN_OK) return st;
   en->e.loop0 = loop0;
-  if ((st = ensure_scratch(ctx, sizeof(int))) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
-  int* d_deg = static_cast<int*>(ctx->scratch.ptr);
+  Carve cv;
+  const size_t o_deg = cv.take<int>(1);
+  const size_t o_work = cv.take<char>(gen_loops_work_bytes(en->e.n_blocks, ppl));
+  if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
+  int* d_deg = at<int>(ctx->scratch.ptr, o_deg);
   cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
-  if (err == cudaSuccess) err = launch_gen_loops(ctx->stream, seed, en->e, d_deg);
-  ctx->launches += 3;
+  if (err == cudaSuccess)
+    err = launch_gen_loops(ctx->stream, seed, en->e, at<char>(ctx->scratch.ptr, o_work), d_deg);
+  ctx->launches += gen_loops_launches(en->e.n_blocks, ppl);
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "launch loop generation");

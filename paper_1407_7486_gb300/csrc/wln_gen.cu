@@ -45,26 +45,33 @@ __global__ void philox_stream_kernel(uint64_t seed, int64_t loop0, int32_t n_loo
                          static_cast<uint32_t>(seed >> 32));
 }
 
-// One CTA per block of 32 loops: lane = loop, warp w = chunk w of the points.
-// Pass 1 sums the raw increments xi_k and k * xi_k per chunk; a scan over
-// the chunks gives each chunk's starting partial sum S_{k0}.  With
-// mu = mean(xi), the closed positions are p_k = S_k - k mu
-// (S_k = sum_{j<k} xi_j), and their mean is
-// (1/N) sum_j xi_j (N - 1 - j) - mu (N - 1)/2.  Pass 2 regenerates the
-// chunk's increments and writes y_k = p_k - mean(p).
-template <int WG>
-__global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int64_t loop0,
-                                                            int32_t ppl, float4* blocks,
-                                                            double* xy64, int32_t n_loops) {
-  __shared__ double part[WG][32][4];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int32_t local = static_cast<int32_t>(blockIdx.x * 32u + lane);
-  const uint32_t loop = static_cast<uint32_t>(loop0 + local);   // Philox counter word 1
-  const int M = ppl / WG;           // points per chunk (even)
-  const int k0 = w * M;
+// Loop generation in two kernels over a slice of blocks (32 loops each,
+// lane = loop).  gen_increments_kernel: one warp per (block, chunk of M
+// points) draws the chunk's raw increments xi_k once, keeps them in `xi`
+// ([block][point][lane], double2) and writes the chunk's sums of xi_k and
+// k xi_k to `part` ([block][chunk][4][lane]).  Its many short warps spread
+// the double-precision Box-Muller work evenly over the SMs.
+// gen_close_kernel: one CTA per block, warp w taking points
+// [w N / WG, (w + 1) N / WG).  The warp adds up its chunks' sums, and a scan
+// over the warps gives its starting partial sum S_{k0}.  With mu = mean(xi)
+// the closed positions are p_k = S_k - k mu (S_k = sum_{j<k} xi_j), and their
+// mean is (1/N) sum_j xi_j (N - 1 - j) - mu (N - 1)/2.  The warp writes
+// y_k = p_k - mean(p) for its points from the stored increments.
+__global__ void __launch_bounds__(32 * kGenWarps) gen_increments_kernel(
+    uint64_t seed, int64_t loop0, int32_t ppl, int32_t b0, int32_t n_items, int32_t M,
+    double2* xi, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int item = static_cast<int>(blockIdx.x) * kGenWarps + static_cast<int>(threadIdx.x >> 5);
+  if (item >= n_items) return;
+  const int C = ppl / M;
+  const int bl = item / C;
+  const int k0 = (item - bl * C) * M;
+  // Philox counter word 1: the loop's global index
+  const uint32_t loop =
+      static_cast<uint32_t>(loop0 + (static_cast<int64_t>(b0) + bl) * 32 + lane);
   const double scale = sqrt(2.0 / ppl);
-
   double sx = 0.0, sy = 0.0, wx = 0.0, wy = 0.0;
+  double2* out = xi + (static_cast<size_t>(bl) * ppl + k0) * 32 + lane;
   for (int k = k0; k < k0 + M; k += 2) {
     double x0, y0, x1, y1;
     increments(seed, loop, k >> 1, scale, x0, y0, x1, y1);
@@ -72,15 +79,40 @@ __global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int64
     wx += k * x0; wy += k * y0;
     sx += x1; sy += y1;
     wx += (k + 1) * x1; wy += (k + 1) * y1;
+    out[0] = make_double2(x0, y0);
+    out[32] = make_double2(x1, y1);
+    out += 64;
   }
-  part[w][lane][0] = sx; part[w][lane][1] = sy;
-  part[w][lane][2] = wx; part[w][lane][3] = wy;
+  double* pp = part + static_cast<size_t>(item) * 128 + lane;
+  pp[0] = sx; pp[32] = sy; pp[64] = wx; pp[96] = wy;
+}
+
+template <int WG>
+__global__ void __launch_bounds__(32 * WG) gen_close_kernel(int32_t ppl, int32_t b0, int32_t M,
+                                                            const double2* xi, const double* part,
+                                                            float4* blocks, double* xy64,
+                                                            int32_t n_loops) {
+  __shared__ double sums[WG][32][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int bl = blockIdx.x;
+  const int b = b0 + bl;
+  const int32_t local = b * 32 + lane;
+  const int R = ppl / WG;   // points of this warp (even, a multiple of M)
+  const int k0 = w * R;
+  const int C = ppl / M;
+  double sx = 0.0, sy = 0.0, wx = 0.0, wy = 0.0;
+  const double* pp = part + (static_cast<size_t>(bl) * C + k0 / M) * 128 + lane;
+  for (int j = 0; j < R / M; ++j, pp += 128) {
+    sx += pp[0]; sy += pp[32]; wx += pp[64]; wy += pp[96];
+  }
+  sums[w][lane][0] = sx; sums[w][lane][1] = sy;
+  sums[w][lane][2] = wx; sums[w][lane][3] = wy;
   __syncthreads();
   double tx = 0.0, ty = 0.0, twx = 0.0, twy = 0.0, px = 0.0, py = 0.0;
   for (int v = 0; v < WG; ++v) {
     if (v == w) { px = tx; py = ty; }
-    tx += part[v][lane][0]; ty += part[v][lane][1];
-    twx += part[v][lane][2]; twy += part[v][lane][3];
+    tx += sums[v][lane][0]; ty += sums[v][lane][1];
+    twx += sums[v][lane][2]; twy += sums[v][lane][3];
   }
   const double N = ppl;
   const double mux = tx / N, muy = ty / N;
@@ -89,16 +121,17 @@ __global__ void __launch_bounds__(32 * WG) gen_loops_kernel(uint64_t seed, int64
   const double cmy = ((N - 1.0) * ty - twy) / N - muy * (N - 1.0) * 0.5;
   double pxk = px - k0 * mux, pyk = py - k0 * muy;
 
-  float4* row = blocks + (static_cast<size_t>(blockIdx.x) * (ppl / 2) + k0 / 2) * 32 + lane;
+  const double2* in = xi + (static_cast<size_t>(bl) * ppl + k0) * 32 + lane;
+  float4* row = blocks + (static_cast<size_t>(b) * (ppl / 2) + k0 / 2) * 32 + lane;
   double* ox = xy64 ? xy64 + static_cast<size_t>(local) * 2 * ppl : nullptr;
   const bool real = local < n_loops;
-  for (int k = k0; k < k0 + M; k += 2) {
-    double x0, y0, x1, y1;
-    increments(seed, loop, k >> 1, scale, x0, y0, x1, y1);
+  for (int k = k0; k < k0 + R; k += 2) {
+    const double2 a = in[0], c = in[32];
+    in += 64;
     const double ax = pxk - cmx, ay = pyk - cmy;
-    pxk += x0 - mux; pyk += y0 - muy;
+    pxk += a.x - mux; pyk += a.y - muy;
     const double bx = pxk - cmx, by = pyk - cmy;
-    pxk += x1 - mux; pyk += y1 - muy;
+    pxk += c.x - mux; pyk += c.y - muy;
     *row = make_float4(__double2float_rn(ax), __double2float_rn(ay), __double2float_rn(bx),
                        __double2float_rn(by));
     row += 32;
@@ -275,15 +308,47 @@ cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate) {
-  const int wg = e.ppl >= 16 ? 8 : e.ppl / 2;
-  switch (wg) {
-    case 8: gen_loops_kernel<8><<<e.n_blocks, 256, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
-    case 2: gen_loops_kernel<2><<<e.n_blocks, 64, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
-    case 4: gen_loops_kernel<4><<<e.n_blocks, 128, 0, s>>>(seed, e.loop0, e.ppl, e.blocks, e.xy64, e.n_loops); break;
-    default: return cudaErrorInvalidValue;
+int gen_warps(int32_t ppl) { return ppl >= 16 ? 8 : ppl / 2; }
+int gen_chunk(int32_t ppl) { return ppl / gen_warps(ppl) < kGenChunk ? ppl / gen_warps(ppl) : kGenChunk; }
+
+int gen_slice_blocks(int32_t n_blocks, int32_t ppl) {
+  const size_t per_block = static_cast<size_t>(ppl) * 32 * sizeof(double2) +
+                           static_cast<size_t>(ppl / gen_chunk(ppl)) * 128 * sizeof(double);
+  const size_t fit = kGenWorkBytes / per_block;
+  const size_t slice = fit < 1 ? 1 : fit;
+  return static_cast<int>(slice < static_cast<size_t>(n_blocks) ? slice : n_blocks);
+}
+
+size_t gen_loops_work_bytes(int32_t n_blocks, int32_t ppl) {
+  const size_t slice = static_cast<size_t>(gen_slice_blocks(n_blocks, ppl));
+  return slice * ppl * 32 * sizeof(double2) + slice * (ppl / gen_chunk(ppl)) * 128 * sizeof(double);
+}
+
+int gen_loops_launches(int32_t n_blocks, int32_t ppl) {
+  const int slice = gen_slice_blocks(n_blocks, ppl);
+  return 2 * ((n_blocks + slice - 1) / slice) + 2;
+}
+
+cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
+                             int* d_degenerate) {
+  const int wg = gen_warps(e.ppl), M = gen_chunk(e.ppl);
+  const int slice = gen_slice_blocks(e.n_blocks, e.ppl);
+  double2* xi = static_cast<double2*>(work);
+  double* part = reinterpret_cast<double*>(xi + static_cast<size_t>(slice) * e.ppl * 32);
+  cudaError_t err = cudaSuccess;
+  for (int b0 = 0; b0 < e.n_blocks && err == cudaSuccess; b0 += slice) {
+    const int nb = e.n_blocks - b0 < slice ? e.n_blocks - b0 : slice;
+    const int n_items = nb * (e.ppl / M);
+    gen_increments_kernel<<<(n_items + kGenWarps - 1) / kGenWarps, 32 * kGenWarps, 0, s>>>(
+        seed, e.loop0, e.ppl, b0, n_items, M, xi, part);
+    switch (wg) {
+      case 8: gen_close_kernel<8><<<nb, 256, 0, s>>>(e.ppl, b0, M, xi, part, e.blocks, e.xy64, e.n_loops); break;
+      case 4: gen_close_kernel<4><<<nb, 128, 0, s>>>(e.ppl, b0, M, xi, part, e.blocks, e.xy64, e.n_loops); break;
+      case 2: gen_close_kernel<2><<<nb, 64, 0, s>>>(e.ppl, b0, M, xi, part, e.blocks, e.xy64, e.n_loops); break;
+      default: return cudaErrorInvalidValue;
+    }
+    err = cudaGetLastError();
   }
-  cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
   degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,

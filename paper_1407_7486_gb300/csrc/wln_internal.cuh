@@ -216,7 +216,19 @@ ProfileDev profile_constants(const wln_profile& pr, int ppl);
 // Generation (wln_gen.cu).
 cudaError_t launch_philox_stream(cudaStream_t s, uint64_t seed, int64_t loop0, int32_t n_loops,
                                  int32_t n_calls, uint32_t* out);
-cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, int* d_degenerate);
+// Unit loops: increments drawn once into `work` (gen_loops_work_bytes of
+// it), then closed and centred; blocks are taken in slices so that `work`
+// stays within kGenWorkBytes.  gen_loops_launches counts the kernels.
+constexpr int kGenChunk = 32;                       // points per warp drawing increments
+constexpr int kGenWarps = 4;                        // warps per CTA drawing increments
+constexpr size_t kGenWorkBytes = size_t(1) << 30;   // increments and chunk sums of a slice
+int gen_warps(int32_t ppl);
+int gen_chunk(int32_t ppl);
+int gen_slice_blocks(int32_t n_blocks, int32_t ppl);
+size_t gen_loops_work_bytes(int32_t n_blocks, int32_t ppl);
+int gen_loops_launches(int32_t n_blocks, int32_t ppl);
+cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
+                             int* d_degenerate);
 cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
                               int* d_degenerate);
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
