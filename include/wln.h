@@ -173,6 +173,15 @@ wln_status wln_gen_dloops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_
  */
 wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops,
                                   int32_t ppl, wln_ensemble** out);
+/*
+ * Free an ensemble.  With a context (on the ensemble's device) the call waits
+ * for the context's stream, and the context keeps the device memory of up to
+ * two freed ensembles for the next ensemble of the same shape it makes (no
+ * cudaMalloc / cudaFree, which wait for the whole device, in a loop that
+ * draws and frees an ensemble every step); wln_destroy releases it.  Work on
+ * the ensemble queued on other streams must be complete before the call.
+ * With ctx NULL the memory is released at once.
+ */
 wln_status wln_free_ensemble(wln_ctx* ctx, wln_ensemble* ens);
 /* Sizes of an ensemble; any output may be NULL. */
 wln_status wln_ensemble_info(const wln_ensemble* ens, int32_t* n_loops, int32_t* ppl,

@@ -133,12 +133,24 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
   en->e.ppl = ppl;
   en->e.n_blocks = (n_loops + 31) / 32;
   const size_t n4 = static_cast<size_t>(en->e.n_blocks) * (ppl / 2) * 32;
+  const size_t n64 = fp64 ? static_cast<size_t>(n_loops) * 2 * ppl : 0;
+  for (size_t i = 0; i < ctx->ens_cache.size(); ++i) {
+    const wln_ctx::EnsembleMem m = ctx->ens_cache[i];
+    if (m.n4 == n4 && m.n_blocks == static_cast<size_t>(en->e.n_blocks) && m.n64 == n64) {
+      en->e.blocks = m.blocks;
+      en->e.stats = m.stats;
+      en->e.maxlen = reinterpret_cast<float*>(en->e.stats + en->e.n_blocks);
+      en->e.xy64 = m.xy64;
+      ctx->ens_cache.erase(ctx->ens_cache.begin() + static_cast<std::ptrdiff_t>(i));
+      *out = en;
+      return WLN_OK;
+    }
+  }
   cudaError_t err = cudaMalloc(&en->e.blocks, n4 * sizeof(float4));
   if (err == cudaSuccess)
     err = cudaMalloc(&en->e.stats, static_cast<size_t>(en->e.n_blocks) * (sizeof(float2) + sizeof(float)));
   if (err == cudaSuccess) en->e.maxlen = reinterpret_cast<float*>(en->e.stats + en->e.n_blocks);
-  if (err == cudaSuccess && fp64)
-    err = cudaMalloc(&en->e.xy64, static_cast<size_t>(n_loops) * 2 * ppl * sizeof(double));
+  if (err == cudaSuccess && fp64) err = cudaMalloc(&en->e.xy64, n64 * sizeof(double));
   if (err != cudaSuccess) {
     if (en->e.blocks) cudaFree(en->e.blocks);
     if (en->e.stats) cudaFree(en->e.stats);
@@ -401,6 +413,11 @@ wln_status wln_destroy(wln_ctx* ctx) {
   if (!ctx) return WLN_EINVAL;
   DeviceGuard guard(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (const wln_ctx::EnsembleMem& m : ctx->ens_cache) {
+    cudaFree(m.blocks);
+    cudaFree(m.stats);
+    if (m.xy64) cudaFree(m.xy64);
+  }
   if (ctx->scratch.ptr) cudaFree(ctx->scratch.ptr);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_flag) cudaFree(ctx->d_flag);
@@ -554,6 +571,17 @@ wln_status wln_free_ensemble(wln_ctx* ctx, wln_ensemble* ens) {
   if (!ens) return fail(ctx, WLN_EINVAL, "null ensemble");
   DeviceGuard guard(ens->device);
   if (ctx) cudaStreamSynchronize(ctx->stream);
+  if (ctx && ctx->device == ens->device && ens->e.blocks && ens->e.stats &&
+      ctx->ens_cache.size() < kEnsembleCache) {
+    // kept for the next ensemble of this shape (wln_destroy frees it)
+    ctx->ens_cache.push_back(wln_ctx::EnsembleMem{
+        ens->e.blocks, ens->e.stats, ens->e.xy64,
+        static_cast<size_t>(ens->e.n_blocks) * (ens->e.ppl / 2) * 32,
+        static_cast<size_t>(ens->e.n_blocks),
+        ens->e.xy64 ? static_cast<size_t>(ens->e.n_loops) * 2 * ens->e.ppl : 0});
+    delete ens;
+    return WLN_OK;
+  }
   if (ens->e.blocks) cudaFree(ens->e.blocks);
   if (ens->e.stats) cudaFree(ens->e.stats);
   if (ens->e.xy64) cudaFree(ens->e.xy64);

@@ -172,7 +172,18 @@ struct wln_ctx {
                         // recorded loop, a check of the double-float walk)
   unsigned long long* d_guard_totals = nullptr;   // escalated loops, overflows, saturated, launches
   int* d_items = nullptr;   // a Wilson launch's item counter (dynamic schedule), zeroed per launch
+  // Device memory of the last freed ensembles, reused by the next ensemble of
+  // the same shape: a loop that draws and frees an ensemble every step then
+  // makes no cudaMalloc / cudaFree, which would wait for the whole device.
+  struct EnsembleMem {
+    float4* blocks;
+    float2* stats;
+    double* xy64;
+    size_t n4, n_blocks, n64;
+  };
+  std::vector<EnsembleMem> ens_cache;
 };
+constexpr size_t kEnsembleCache = 2;   // freed ensembles a context keeps
 
 struct wln_ensemble {
   wln::Ensemble e;

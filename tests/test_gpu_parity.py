@@ -126,6 +126,34 @@ def test_generated_loops_match_oracle(ctx, n_loops, ppl):
     ens.free()
 
 
+def test_freed_ensemble_memory_is_reused_cleanly():
+    """A context keeps freed ensembles' device memory for the next ensemble of
+    the same shape: ensembles drawn into reused memory (with and without the
+    double copy, the d-loop generator too) equal the oracle's, and ensembles
+    of other shapes still come out right beside them."""
+    c = wln.Context(0)
+    try:
+        for _ in range(2):
+            for seed in (3, 4, 5):
+                ens = c.gen_loops(seed, 96, 256, keep_fp64=True)
+                f32, f64 = c.loops_copy(ens, f32=True, f64=True)
+                ref = oracle.gen_loops(seed, 96, 256)
+                assert np.abs(f64 - ref).max() < 1e-13
+                assert np.all(np.abs(f32 - ref.astype(np.float32)) <=
+                              np.spacing(np.abs(ref.astype(np.float32))))
+                ens.free()
+            a = c.gen_loops(6, 64, 128)          # float only: another shape
+            b = c.gen_dloops(7, 96, 256)         # the float shape of the freed ones
+            fa, _ = c.loops_copy(a)
+            fb, _ = c.loops_copy(b)
+            assert np.all(np.abs(fa - oracle.gen_loops(6, 64, 128).astype(np.float32)) <= 1e-6)
+            assert np.all(np.abs(fb - oracle.gen_dloops(7, 96, 256).astype(np.float32)) <= 1e-6)
+            a.free()
+            b.free()
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("n_loops,ppl", [(40, 4), (96, 64), (33, 512), (32, 16384)])
 def test_generated_dloops_match_oracle(ctx, n_loops, ppl):
     ens = ctx.gen_dloops(8, n_loops, ppl, keep_fp64=True, loop0=5)
