@@ -228,15 +228,15 @@ def _peaks():
     return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
 
 
-def _kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1407_7486_gb300", "csrc", "wln_wilson.cu"), "rb") as f:
+def _kernel_source_hash(src: str = "wln_wilson.cu") -> str:
+    with open(os.path.join(ROOT, "paper_1407_7486_gb300", "csrc", src), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _ncu_traffic(summary: str):
-    """DRAM bytes per Wilson launch from the committed ncu summary
-    profiles/<summary>.md, or None when the kernel source changed since the
-    capture."""
+def _ncu_value(summary: str, key: str = "dram_bytes_per_launch", src: str = "wln_wilson.cu"):
+    """A figure (`key: value` line) from the committed ncu summary
+    profiles/<summary>.md, or None when the kernel source `src` changed since
+    the capture."""
     path = os.path.join(ROOT, "profiles", f"{summary}.md")
     if not os.path.exists(path):
         return None
@@ -245,9 +245,14 @@ def _ncu_traffic(summary: str):
     for line in text.splitlines():
         if line.startswith("kernel_source_sha256_16:"):
             h = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
+        if line.startswith(key + ":"):
             k = float(line.split(":", 1)[1].strip())
-    return k if (h == _kernel_source_hash() and k) else None
+    return k if (h == _kernel_source_hash(src) and k) else None
+
+
+def _ncu_traffic(summary: str):
+    """DRAM bytes per Wilson launch from the committed ncu summary."""
+    return _ncu_value(summary)
 
 
 class ClockSampler:
@@ -594,6 +599,8 @@ def main():
                     help="comma list: 'sat' (2000 req/s) and/or fractions of measured capacity")
     ap.add_argument("--correlation", action="store_true",
                     help="time per-loop values, randomised groups and Eq. corrcoef")
+    ap.add_argument("--dloops", action="store_true",
+                    help="time the d-loop generator (Eqs. yn2, ynk) on the workload's ensemble")
     ap.add_argument("--levels", action="store_true",
                     help="time the discretisation-level pass (N, N/2, N/4) and extrapolation")
     ap.add_argument("--nested", action="store_true",
@@ -618,6 +625,8 @@ def main():
         return run_batched(args, wl)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.dloops:
+        return run_dloops(args, wl)
     if args.levels:
         return run_levels(args, wl)
     if args.correlation:
@@ -934,6 +943,99 @@ def run_batched(args, wl: I.Workload):
     line["autotune_candidates"] = tuned.get("candidates")
     line["finite_gamma"] = bool(np.isfinite(g).all())
     b.free(); ens.free(); ctx.close()
+    print(json.dumps(line))
+
+
+def run_dloops(args, wl: I.Workload):
+    """The paper's d-loop generator (Eqs. yn2, ynk) on the workload's
+    ensemble: one step = wln_gen_dloops (Gaussians drawn by short warps, the
+    bisection levels built, centre of mass removed, float store, degeneracy
+    check and block statistics) and the ensemble freed.  The roofline is the
+    FP64 pipe: the draw's work is Philox in integer arithmetic and one
+    double-precision Box-Muller (log, sqrt, sincospi) per point, the build's
+    a few FP64 additions per point; their FP64 operations per point are
+    counted by ncu (the library calls have no count of their own) and read
+    from the committed summary while wln_gen.cu is unchanged."""
+    import torch
+    from paper_1407_7486_gb300 import build, wln
+    import oracle
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    ctx = wln.Context(0, stream)
+    pts = wl.n_loops * wl.ppl
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.gen_dloops(wl.seed, wl.n_loops, wl.ppl).free()
+        stream.synchronize()
+        n0 = ctx.launch_count
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        inc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            for a, b in ev:
+                a.record(stream)
+                ctx.gen_dloops(wl.seed, wl.n_loops, wl.ppl).free()
+                b.record(stream)
+            launches = ctx.launch_count - n0
+            for a, b in inc:      # the increment generator on the same ensemble, for context
+                a.record(stream)
+                ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl).free()
+                b.record(stream)
+            stream.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        inc_ms = statistics.mean(a.elapsed_time(b) for a, b in inc)
+        # end to end: the float loops copied to page-locked host memory each step
+        host = torch.empty((wl.n_loops, 2, wl.ppl), dtype=torch.float32, pin_memory=True).numpy()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e = ctx.gen_dloops(wl.seed, wl.n_loops, wl.ppl)
+            ctx.loops_copy(e, f32=True, out32=host)
+            e.free()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+    # the oracle on the host cores: the same construction for a bounded sample of loops
+    threads = oracle.max_threads()
+    n_cpu = 64
+    t0 = time.perf_counter()
+    ref = oracle.gen_dloops(wl.seed, n_cpu, wl.ppl, threads=threads)
+    while time.perf_counter() - t0 < 10.0 and n_cpu < wl.n_loops:
+        n_cpu = min(wl.n_loops, n_cpu * 2)
+        t0 = time.perf_counter()
+        ref = oracle.gen_dloops(wl.seed, n_cpu, wl.ppl, threads=threads)
+    cpu_s = time.perf_counter() - t0
+    e = ctx.gen_dloops(wl.seed, wl.n_loops, wl.ppl, keep_fp64=True)
+    _, y64 = ctx.loops_copy(e, f32=False, f64=True)
+    e.free()
+    err = float(np.abs(y64[:n_cpu] - ref).max())
+    peaks, _ = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sm_count() * FP64_LANES_PER_SM * sm_mhz * 1e6 / 1e9          # G FP64 op/s
+    ops_pt = _ncu_value(f"gen_dloops_{args.workload}", "fp64_ops_per_point", "wln_gen.cu")
+    achieved = ops_pt * pts / (ms / 1e3) / 1e9 if ops_pt else None
+    line = _common_line("loop-points generated/s (d-loops, Eqs. yn2 and ynk)", pts / (ms / 1e3),
+                        "loop-points/s", args.steps, args.warmup, ms, "f64",
+                        {"workload": f"{wl.name}: the ensemble's {wl.n_loops} loops x {wl.ppl} points "
+                                     f"as d-loops", "n_loops": wl.n_loops, "ppl": wl.ppl,
+                         "l2": l2_note(pts * 8, False, "written every step")})
+    line["roofline"] = {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "G FP64 op/s",
+                        "frac": achieved / peak if achieved else None,
+                        "traffic": _ncu_value(f"gen_dloops_{args.workload}", "dram_bytes_per_launch",
+                                              "wln_gen.cu"),
+                        "kernel": "gen_dgauss_kernel + gen_dbuild_kernel (the whole generation call)",
+                        "kernel_ms": ms, "fp64_ops_per_point": ops_pt,
+                        "peak_basis": f"{sm_count()} SMs x {FP64_LANES_PER_SM} FP64 lanes x "
+                                      f"{sm_mhz:.0f} MHz"}
+    line["increments_ms"] = inc_ms
+    line["e2e"] = {"value": pts / e2e_s, "unit": "loop-points/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": int(host.nbytes)}
+    line["cpu_baseline"] = {"value": n_cpu * wl.ppl / cpu_s, "unit": "loop-points/s",
+                            "cores": threads, "kind": "oracle",
+                            "sample": f"the first {n_cpu} loops of the ensemble ({cpu_s:.1f} s)"}
+    line["gpu_error_vs_oracle_on_sample"] = {"double_copy_max_abs": err}
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clk.summary()
+    ctx.close()
     print(json.dumps(line))
 
 

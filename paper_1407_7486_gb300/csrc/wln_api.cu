@@ -521,13 +521,13 @@ wln_status wln_gen_dloops(wln_ctx* ctx, uint64_t seed, int64_t loop0, int32_t n_
   en->e.loop0 = loop0;
   Carve cv;
   const size_t o_deg = cv.take<int>(1);
-  const size_t o_work = cv.take<double>(static_cast<size_t>(en->e.n_blocks) * 32 * 2 * ppl);
+  const size_t o_work = cv.take<char>(gen_dloops_work_bytes(en->e.n_blocks, ppl));
   if ((st = ensure_scratch(ctx, cv.off)) != WLN_OK) { wln_free_ensemble(ctx, en); return st; }
   int* d_deg = at<int>(ctx->scratch.ptr, o_deg);
   cudaError_t err = cudaMemsetAsync(d_deg, 0, sizeof(int), ctx->stream);
   if (err == cudaSuccess)
-    err = launch_gen_dloops(ctx->stream, seed, en->e, at<double>(ctx->scratch.ptr, o_work), d_deg);
-  ctx->launches += 3;
+    err = launch_gen_dloops(ctx->stream, seed, en->e, at<char>(ctx->scratch.ptr, o_work), d_deg);
+  ctx->launches += gen_dloops_launches(en->e.n_blocks, ppl);
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "launch d-loop generation");

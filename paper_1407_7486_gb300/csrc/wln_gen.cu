@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(32 * WG) gen_close_kernel(int32_t ppl, int32_t
   // mean_k p_k = (1/N) sum_k (S_k - k mu) = (1/N) sum_j xi_j (N-1-j) - mu (N-1)/2
   const double cmx = ((N - 1.0) * tx - twx) / N - mux * (N - 1.0) * 0.5;
   const double cmy = ((N - 1.0) * ty - twy) / N - muy * (N - 1.0) * 0.5;
-  double pxk = px - k0 * mux, pyk = py - k0 * muy;
+  // y_k = p_k - mean(p), carried from the warp's first point
+  double yx = (px - k0 * mux) - cmx, yy = (py - k0 * muy) - cmy;
 
   const double2* in = xi + (static_cast<size_t>(bl) * ppl + k0) * 32 + lane;
   float4* row = blocks + (static_cast<size_t>(b) * (ppl / 2) + k0 / 2) * 32 + lane;
@@ -128,10 +129,10 @@ __global__ void __launch_bounds__(32 * WG) gen_close_kernel(int32_t ppl, int32_t
   for (int k = k0; k < k0 + R; k += 2) {
     const double2 a = in[0], c = in[32];
     in += 64;
-    const double ax = pxk - cmx, ay = pyk - cmy;
-    pxk += a.x - mux; pyk += a.y - muy;
-    const double bx = pxk - cmx, by = pyk - cmy;
-    pxk += c.x - mux; pyk += c.y - muy;
+    const double ax = yx, ay = yy;
+    yx += a.x - mux; yy += a.y - muy;
+    const double bx = yx, by = yy;
+    yx += c.x - mux; yy += c.y - muy;
     *row = make_float4(__double2float_rn(ax), __double2float_rn(ay), __double2float_rn(bx),
                        __double2float_rn(by));
     row += 32;
@@ -147,50 +148,124 @@ __global__ void __launch_bounds__(32 * WG) gen_close_kernel(int32_t ppl, int32_t
 // Gaussian about the mean of its two neighbours of the previous level with
 // variance 1/N_k per component; then the centre of mass is removed.
 // Gaussian number m (in creation order) comes from Philox call m/2 with
-// counter (m/2, loop, 1, 0): (u0,u1) for even m, (u2,u3) for odd m.
-// One warp per 32 loops, lane = loop, positions in double in `work`
-// ([block][point][x|y][lane], coalesced); each lane builds its loop level by
-// level (every parent it reads was written by the same lane earlier).
-__global__ void __launch_bounds__(32) gen_dloops_kernel(uint64_t seed, int64_t loop0, int32_t ppl,
-                                                       double* work, float4* blocks, double* xy64,
-                                                       int32_t n_loops) {
-  const int lane = threadIdx.x;
-  const int32_t local = static_cast<int32_t>(blockIdx.x * 32u + lane);
-  const uint32_t loop = static_cast<uint32_t>(loop0 + local);
-  double* W = work + static_cast<size_t>(blockIdx.x) * ppl * 2 * 32 + lane;
-  auto X = [&](int i) -> double& { return W[(2 * i) * 32]; };
-  auto Y = [&](int i) -> double& { return W[(2 * i + 1) * 32]; };
-  X(0) = 0.0;
-  Y(0) = 0.0;
+// counter (m/2, loop, 1, 0): (u0,u1) for even m, (u2,u3) for odd m.  Number m
+// belongs to level N_k = 2^(floor(log2(m + 1)) + 1), as its
+// (m + 2 - N_k/2)-th new point: q = 2 (m + 1 - N_k/2) + 1.
+//
+// Two kernels over a slice of blocks (32 loops each, lane = loop), positions
+// in double2 at g[block][point][lane]:
+//  gen_dgauss_kernel: one warp per (block, M consecutive numbers m) draws
+//   the Gaussians and stores sqrt(1/N_k) z at the point each one places (the
+//   double-precision Box-Muller work, spread evenly over the SMs);
+//  gen_dbuild_kernel: one CTA per block adds, level by level, the mean of
+//   each new point's two neighbours (the level's points split over the
+//   warps, a barrier between levels: every parent was written one level
+//   earlier), removes the centre of mass and stores.
+__global__ void __launch_bounds__(32 * kGenWarps) gen_dgauss_kernel(uint64_t seed, int64_t loop0,
+                                                                   int32_t ppl, int32_t b0,
+                                                                   int32_t n_items, int32_t M,
+                                                                   double2* g) {
+  const int lane = threadIdx.x & 31;
+  const int item = static_cast<int>(blockIdx.x) * kGenWarps + static_cast<int>(threadIdx.x >> 5);
+  if (item >= n_items) return;
+  const int C = ppl / M;
+  const int bl = item / C;
+  const int m0 = (item - bl * C) * M;
+  const uint32_t loop =
+      static_cast<uint32_t>(loop0 + (static_cast<int64_t>(b0) + bl) * 32 + lane);
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
-  int32_t m = 0;
+  double2* G = g + static_cast<size_t>(bl) * ppl * 32 + lane;
+  const int m1 = min(m0 + M, ppl - 1);   // numbers 0 .. N - 2 place points 1 .. N - 1
   uint4 u = make_uint4(0, 0, 0, 0);
-  for (int32_t Nk = 2; Nk <= ppl; Nk *= 2) {
-    const int32_t stride = ppl / Nk;
-    const double sigma = sqrt(1.0 / Nk);
-    for (int32_t q = 1; q < Nk; q += 2, ++m) {
-      if ((m & 1) == 0) u = philox4x32_10(make_uint4(static_cast<uint32_t>(m >> 1), loop, 1u, 0u), k0, k1);
-      const uint32_t ua = (m & 1) ? u.z : u.x, ub = (m & 1) ? u.w : u.y;
-      double sn, cs;
-      const double r = sqrt(-2.0 * log(uniform_open(ua)));
-      sincospi(2.0 * uniform_open(ub), &sn, &cs);
-      const int32_t i = q * stride, left = (q - 1) * stride, right = ((q + 1) * stride) % ppl;
-      X(i) = 0.5 * (X(left) + X(right)) + sigma * (r * cs);
-      Y(i) = 0.5 * (Y(left) + Y(right)) + sigma * (r * sn);
+  int level_n = 0;      // the N_k whose sigma is held (a chunk spans at most two levels)
+  double sigma = 0.0;
+  for (int m = m0; m < m1; ++m) {
+    if ((m & 1) == 0) u = philox4x32_10(make_uint4(static_cast<uint32_t>(m >> 1), loop, 1u, 0u), k0, k1);
+    const uint32_t ua = (m & 1) ? u.z : u.x, ub = (m & 1) ? u.w : u.y;
+    const int Nk = 2 << (31 - __clz(m + 1));   // 2^(floor(log2(m + 1)) + 1)
+    const int q = 2 * (m + 1 - Nk / 2) + 1;
+    if (Nk != level_n) {   // the same on every lane
+      level_n = Nk;
+      sigma = sqrt(1.0 / Nk);
     }
+    double sn, cs;
+    const double r = sqrt(-2.0 * log(uniform_open(ua)));
+    sincospi(2.0 * uniform_open(ub), &sn, &cs);
+    G[static_cast<size_t>(q) * (ppl / Nk) * 32] = make_double2(sigma * (r * cs), sigma * (r * sn));
   }
+}
+
+template <int WG>
+__global__ void __launch_bounds__(32 * WG) gen_dbuild_kernel(int32_t ppl, int32_t b0, double2* g,
+                                                            float4* blocks, double* xy64,
+                                                            int32_t n_loops) {
+  __shared__ double cms[WG][32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int bl = blockIdx.x;
+  const int b = b0 + bl;
+  const int32_t local = b * 32 + lane;
+  double2* W = g + static_cast<size_t>(bl) * ppl * 32 + lane;
+  if (w == 0) W[0] = make_double2(0.0, 0.0);
+  __syncthreads();
+  constexpr int kBatch = WG >= 8 ? 4 : 8;   // new points of a warp handled together
+  for (int32_t Nk = 2; Nk <= ppl; Nk *= 2) {
+    // the level's new points split over the warps; the barrier below makes
+    // them visible to every warp before the next level reads them as parents
+    const int32_t stride = ppl / Nk, n_new = Nk / 2;
+    const int32_t per = (n_new + WG - 1) / WG;
+    const int32_t ja = w * per, jb = min(n_new, ja + per);
+    for (int32_t j0 = ja; j0 < jb; j0 += kBatch) {
+      // parents (the previous level) first, then the new points: within a
+      // level no new point is another's parent
+      double2 a[kBatch], c[kBatch], d[kBatch];
+#pragma unroll
+      for (int t = 0; t < kBatch; ++t) {
+        if (j0 + t < jb) {
+          const int32_t q = 2 * (j0 + t) + 1;
+          a[t] = W[static_cast<size_t>((q - 1) * stride) * 32];
+          c[t] = W[static_cast<size_t>(((q + 1) * stride) % ppl) * 32];
+          d[t] = W[static_cast<size_t>(q * stride) * 32];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kBatch; ++t) {
+        if (j0 + t < jb) {
+          const int32_t q = 2 * (j0 + t) + 1;
+          W[static_cast<size_t>(q * stride) * 32] =
+              make_double2(0.5 * (a[t].x + c[t].x) + d[t].x, 0.5 * (a[t].y + c[t].y) + d[t].y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // centre of mass: each warp's points, then the warps' sums in warp order
+  const int32_t R = ppl / WG;
+  const int32_t k0 = w * R;
+  double sx = 0.0, sy = 0.0;
+  for (int32_t i = k0; i < k0 + R; ++i) {
+    const double2 v = W[static_cast<size_t>(i) * 32];
+    sx += v.x;
+    sy += v.y;
+  }
+  cms[w][lane][0] = sx;
+  cms[w][lane][1] = sy;
+  __syncthreads();
   double cmx = 0.0, cmy = 0.0;
-  for (int32_t i = 0; i < ppl; ++i) cmx += X(i);
-  for (int32_t i = 0; i < ppl; ++i) cmy += Y(i);
+  for (int v = 0; v < WG; ++v) {
+    cmx += cms[v][lane][0];
+    cmy += cms[v][lane][1];
+  }
   cmx /= ppl;
   cmy /= ppl;
-  float4* row = blocks + static_cast<size_t>(blockIdx.x) * (ppl / 2) * 32 + lane;
+  float4* row = blocks + (static_cast<size_t>(b) * (ppl / 2) + k0 / 2) * 32 + lane;
   double* ox = xy64 ? xy64 + static_cast<size_t>(local) * 2 * ppl : nullptr;
   const bool real = local < n_loops;
-  for (int32_t k = 0; k < ppl; k += 2) {
-    const double ax = X(k) - cmx, ay = Y(k) - cmy, bx = X(k + 1) - cmx, by = Y(k + 1) - cmy;
-    row[(k / 2) * 32] = make_float4(__double2float_rn(ax), __double2float_rn(ay),
-                                    __double2float_rn(bx), __double2float_rn(by));
+  for (int32_t k = k0; k < k0 + R; k += 2) {
+    const double2 p0 = W[static_cast<size_t>(k) * 32], p1 = W[static_cast<size_t>(k + 1) * 32];
+    const double ax = p0.x - cmx, ay = p0.y - cmy, bx = p1.x - cmx, by = p1.y - cmy;
+    *row = make_float4(__double2float_rn(ax), __double2float_rn(ay), __double2float_rn(bx),
+                       __double2float_rn(by));
+    row += 32;
     if (ox && real) {
       ox[k] = ax; ox[k + 1] = bx;
       ox[ppl + k] = ay; ox[ppl + k + 1] = by;
@@ -198,7 +273,6 @@ __global__ void __launch_bounds__(32) gen_dloops_kernel(uint64_t seed, int64_t l
   }
 }
 
-// float xy[l][2][N] -> blocks; padding lanes are zero.
 __global__ void pack_kernel(const float* xy, float4* blocks, int32_t n_loops, int32_t ppl,
                             int32_t n_blocks) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -358,10 +432,43 @@ cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, v
   return launch_block_stats(s, e);
 }
 
-cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
+int gen_dslice_blocks(int32_t n_blocks, int32_t ppl) {
+  const size_t per_block = static_cast<size_t>(ppl) * 32 * sizeof(double2);
+  const size_t fit = kGenWorkBytes / per_block;
+  const size_t slice = fit < 1 ? 1 : fit;
+  return static_cast<int>(slice < static_cast<size_t>(n_blocks) ? slice : n_blocks);
+}
+
+size_t gen_dloops_work_bytes(int32_t n_blocks, int32_t ppl) {
+  return static_cast<size_t>(gen_dslice_blocks(n_blocks, ppl)) * ppl * 32 * sizeof(double2);
+}
+
+int gen_dloops_launches(int32_t n_blocks, int32_t ppl) {
+  const int slice = gen_dslice_blocks(n_blocks, ppl);
+  return 2 * ((n_blocks + slice - 1) / slice) + 2;
+}
+
+cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
                               int* d_degenerate) {
-  gen_dloops_kernel<<<e.n_blocks, 32, 0, s>>>(seed, e.loop0, e.ppl, work, e.blocks, e.xy64, e.n_loops);
-  cudaError_t err = cudaGetLastError();
+  const int M = e.ppl < kGenChunk ? e.ppl : kGenChunk;
+  const int slice = gen_dslice_blocks(e.n_blocks, e.ppl);
+  double2* g = static_cast<double2*>(work);
+  cudaError_t err = cudaSuccess;
+  for (int b0 = 0; b0 < e.n_blocks && err == cudaSuccess; b0 += slice) {
+    const int nb = e.n_blocks - b0 < slice ? e.n_blocks - b0 : slice;
+    const int n_items = nb * (e.ppl / M);
+    gen_dgauss_kernel<<<(n_items + kGenWarps - 1) / kGenWarps, 32 * kGenWarps, 0, s>>>(
+        seed, e.loop0, e.ppl, b0, n_items, M, g);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) break;
+    switch (gen_warps(e.ppl)) {
+      case 8: gen_dbuild_kernel<8><<<nb, 256, 0, s>>>(e.ppl, b0, g, e.blocks, e.xy64, e.n_loops); break;
+      case 4: gen_dbuild_kernel<4><<<nb, 128, 0, s>>>(e.ppl, b0, g, e.blocks, e.xy64, e.n_loops); break;
+      case 2: gen_dbuild_kernel<2><<<nb, 64, 0, s>>>(e.ppl, b0, g, e.blocks, e.xy64, e.n_loops); break;
+      default: return cudaErrorInvalidValue;
+    }
+    err = cudaGetLastError();
+  }
   if (err != cudaSuccess) return err;
   const int64_t n = static_cast<int64_t>(e.n_loops) * (e.ppl / 2);
   degenerate_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(e.blocks, e.n_loops,

@@ -240,7 +240,13 @@ size_t gen_loops_work_bytes(int32_t n_blocks, int32_t ppl);
 int gen_loops_launches(int32_t n_blocks, int32_t ppl);
 cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
                              int* d_degenerate);
-cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, double* work,
+// d-loops: Gaussians drawn into `work` (gen_dloops_work_bytes of it), then
+// the bisection levels built in place, in slices of blocks within
+// kGenWorkBytes.
+int gen_dslice_blocks(int32_t n_blocks, int32_t ppl);
+size_t gen_dloops_work_bytes(int32_t n_blocks, int32_t ppl);
+int gen_dloops_launches(int32_t n_blocks, int32_t ppl);
+cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
                               int* d_degenerate);
 cudaError_t launch_pack_loops(cudaStream_t s, const float* xy, const Ensemble& e, int* d_degenerate);
 cudaError_t launch_unpack_loops(cudaStream_t s, const Ensemble& e, float* xy);

@@ -326,10 +326,17 @@ class Context:
                                                   ctypes.byref(h)))
         return Ensemble(self, h.value)
 
-    def loops_copy(self, ens: Ensemble, f32=True, f64=False, where: str = "host"):
+    def loops_copy(self, ens: Ensemble, f32=True, f64=False, where: str = "host",
+                   out32=None, out64=None):
+        """The loops as float (and/or double) [n_loops][2][ppl]; out32 / out64
+        are caller-owned destinations (C-contiguous, that shape and type)."""
         shape = (ens.n_loops, 2, ens.ppl)
-        a = self._empty(shape, np.float32, where) if f32 else None
-        b = self._empty(shape, np.float64, where) if f64 else None
+        for o, t in ((out32, np.float32), (out64, np.float64)):
+            if o is not None and (tuple(o.shape) != shape or o.dtype != t
+                                  or not o.flags["C_CONTIGUOUS"]):
+                raise ValueError(f"output must be C-contiguous {t.__name__} of shape {shape}")
+        a = out32 if out32 is not None else (self._empty(shape, np.float32, where) if f32 else None)
+        b = out64 if out64 is not None else (self._empty(shape, np.float64, where) if f64 else None)
         self._check(load().wln_loops_copy(self.handle, ens.handle, _ptr(a), _ptr(b)))
         return a, b
 

@@ -126,6 +126,29 @@ def test_generated_loops_match_oracle(ctx, n_loops, ppl):
     ens.free()
 
 
+@pytest.mark.parametrize("gen", ["increments", "dloops"])
+def test_generation_across_scratch_slices(ctx, gen):
+    """Ensembles whose raw increments (Gaussians) exceed one 1 GiB slice of
+    scratch are generated slice by slice: at ppl = 16384 a slice holds 120
+    blocks of 32 loops for the increments (3840 loops) and 128 for d-loops
+    (4096).  Loops on both sides of every slice boundary, and the last
+    (partial) block, match the oracle regenerated from their global index."""
+    n_loops, ppl, loop0 = 8200, 16384, 7
+    draw = ctx.gen_loops if gen == "increments" else ctx.gen_dloops
+    ref_of = oracle.gen_loops if gen == "increments" else oracle.gen_dloops
+    slice_loops = 3840 if gen == "increments" else 4096
+    ens = draw(11, n_loops, ppl, keep_fp64=True, loop0=loop0)
+    _, f64 = ctx.loops_copy(ens, f32=False, f64=True)
+    ens.free()
+    picks = []
+    for b in (slice_loops, 2 * slice_loops):
+        picks += [b - 2, b - 1, b, b + 1]
+    picks += [0, n_loops - 1]
+    for l in picks:
+        ref = ref_of(11, 1, ppl, loop0=loop0 + l)[0]
+        assert np.abs(f64[l] - ref).max() < 1e-13, (gen, l)
+
+
 def test_freed_ensemble_memory_is_reused_cleanly():
     """A context keeps freed ensembles' device memory for the next ensemble of
     the same shape: ensembles drawn into reused memory (with and without the
