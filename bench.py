@@ -108,6 +108,9 @@ N_ALG_FP64_TINY_SAVED = 10
 # 1/(Q0 Q1) (r^3 1, the bracket 1, two FMAs into the sum) in place of the
 # bracket and its sum (6, 1/D by no reciprocal at all), with C/3 and 2C/5
 # shared by the radii (2/P): 9 + 2 - 2/P fewer than the low form (MUFU: 2).
+# Rows per sub-block of the ensemble statistics (kSubRows in csrc/wln_internal.cuh):
+# the plain walks choose the form of theta per chunk of at most that many rows.
+SUB_ROWS = 64
 N_ALG_LOW_SAVED = 6
 N_ALG_MID_SAVED = 7
 
@@ -126,24 +129,46 @@ def n_alg_tiny_saved(P: int) -> float:
 N_ALG_DF = 503
 
 
-def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float):
+def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float,
+                       sub_rows: int = 0):
     """Fractions of the flux-tube segment evaluations of one pass that the
     kernel walks with the pi/4 form of the arctangent or better, with the
     five-term series or better, and with the three-term series: the same
     float32 tests per (tile of P radii at one T, block of 32 loops) that the
-    kernel makes from the block's longest segment and largest |y|
-    (accounting only).  Returns (low, mid, short), each a part of the one
-    before."""
+    kernel makes from the block's longest segment and largest |y|, and with
+    sub_rows > 0 (whole loops in chunks of that many rows) per sub-block of
+    sub_rows rows as well: a block that does not take the three-term form
+    takes, chunk by chunk, the best of its own and the sub-block's forms up
+    to the five-term one (accounting only).  Returns (low, mid, short), each
+    a part of the one before."""
     f = np.float32
-    n_loops = y32.shape[0]
+    n_loops, _, ppl = y32.shape
     n_blocks = (n_loops + 31) // 32
-    d = np.sqrt(np.sum((np.roll(y32, -1, axis=2) - y32) ** 2, axis=1, dtype=f)).max(axis=1)
-    r = np.sqrt(np.sum(y32 * y32, axis=1, dtype=f)).max(axis=1)
     pad = n_blocks * 32 - n_loops
     up = f(1.0 + 2.0 ** -20)
-    dm = np.concatenate([d, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
-    rm = np.concatenate([r, np.zeros(pad, f)]).reshape(n_blocks, 32).max(axis=1) * up
+    seg = np.sqrt(np.sum((np.roll(y32, -1, axis=2) - y32) ** 2, axis=1, dtype=f))   # [loop][k]
+    rad = np.sqrt(np.sum(y32 * y32, axis=1, dtype=f))                                # [loop][k]
+
+    def per_block(a, n_sub):
+        a = np.concatenate([a, np.zeros((pad, a.shape[1]), f)])
+        return a.reshape(n_blocks, 32, n_sub, -1).max(axis=(1, 3)) * up             # [block][sub]
+
+    dm = per_block(seg, 1)
+    rm = per_block(rad, 1)
+    n_sub = 0
+    if sub_rows:
+        n_sub = max(1, ppl // (2 * sub_rows))
+        ds = per_block(seg, n_sub)                                  # segments starting in the sub-block
+        rs = per_block(np.maximum(rad, np.roll(rad, -1, axis=1)), n_sub)   # and their end points
     in_block = np.minimum(32, n_loops - 32 * np.arange(n_blocks)).astype(np.float64)
+
+    def forms(a2, sT, rmin, lam2, d, r):
+        gap = np.maximum(f(0.0), rmin[:, None, None] - sT * r[None])
+        lhs = a2 * d[None]
+        rhs = np.sqrt(f(lam2) + gap * gap)
+        return np.where(lhs <= f(0.09) * rhs, 3,
+                        np.where(lhs <= f(0.3) * rhs, 2, np.where(lhs <= f(0.9) * rhs, 1, 0)))
+
     low = mid = tiny = tot = 0.0
     for prof, rho, T in zip(profiles, rhos, Ts):
         if prof.kind != I.PROFILE_FLUX_TUBE:
@@ -152,17 +177,21 @@ def low_angle_fraction(y32: np.ndarray, profiles, rhos, Ts, P: int, span: float)
         starts = np.arange(0, len(rho), P)
         rmin = np.array([rho[a:a + P].min() for a in starts], np.float64).astype(f)
         nval = np.array([min(P, len(rho) - a) for a in starts], np.float64)
+        lam2 = prof.lam * prof.lam
         for t in np.asarray(T, np.float64):
             a2 = f(2.0 * span * np.sqrt(t))
             sT = f(np.sqrt(t))
-            gap = np.maximum(f(0.0), rmin[:, None] - sT * rm[None, :])
-            lhs = a2 * dm[None, :]
-            rhs = np.sqrt(f(prof.lam * prof.lam) + gap * gap)
-            w = nval[:, None] * in_block[None, :]
-            low += float(((lhs <= f(0.9) * rhs) * w).sum())
-            mid += float(((lhs <= f(0.3) * rhs) * w).sum())
-            tiny += float(((lhs <= f(0.09) * rhs) * w).sum())
-            tot += float(w.sum())
+            fb = forms(a2, sT, rmin, lam2, dm, rm)                  # [tile][block][1]
+            if n_sub:
+                fs = forms(a2, sT, rmin, lam2, ds, rs)              # [tile][block][sub]
+                fm = np.where(fb == 3, 3, np.maximum(fb, np.minimum(fs, 2)))
+            else:
+                fm = fb
+            w = (nval[:, None] * in_block[None, :])[:, :, None] / fm.shape[2]
+            low += float(((fm >= 1) * w).sum())
+            mid += float(((fm >= 2) * w).sum())
+            tiny += float(((fm == 3) * w).sum())
+            tot += float(w.sum()) * fm.shape[2]
     return (low / tot, mid / tot, tiny / tot) if tot else (0.0, 0.0, 0.0)
 
 
@@ -735,7 +764,7 @@ def main():
         ens = ctx.gen_loops(seed, wl.n_loops, wl.ppl, loop0=loop0)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
-        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 4, 1.0)
+        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, 4, 1.0, sub_rows=SUB_ROWS)
         n_alg = _n_alg(N_ALG_FP32, f_low)
     # the Wilson stage (float pass, double-float recomputation, fixup) does
     # the float walk's work on every segment and the double-float walk's on
@@ -930,7 +959,7 @@ def run_batched(args, wl: I.Workload):
                    "d2h_bytes_per_step": int(S2.nbytes + st2.nbytes + g2.nbytes)}
     y32, _ = ctx.loops_copy(ens)
     if args.prec == "fp32":
-        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, b.P, 1.0)
+        f_low = low_angle_fraction(y32, wl.profiles, wl.rho, wl.T, b.P, 1.0, sub_rows=SUB_ROWS)
         n_alg = _n_alg(N_ALG_FP32 + 11 / b.P - 11 / 4, f_low, P=b.P)
         ach = n_alg * wl.segment_evals / (ms / 1e3) / 1e12
         line["roofline"].update({"achieved": ach, "frac": ach / line["roofline"]["peak"],
@@ -1238,7 +1267,7 @@ def run_correlation(args, wl: I.Workload):
         ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
         y32, _ = ctx.loops_copy(ens)
         ens.free()
-        f_low = low_angle_fraction(y32, prof, rho, T, 4, 1.0)
+        f_low = low_angle_fraction(y32, prof, rho, T, 4, 1.0, sub_rows=SUB_ROWS)
         n_alg = _n_alg(N_ALG_FP32, f_low)
     achieved = n_alg * seg / (kern_ms / 1e3) / 1e12
     line = _common_line("loop-point evals/s (per-loop values + randomised groups + Eq. corrcoef)",

@@ -139,7 +139,7 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
     if (m.n4 == n4 && m.n_blocks == static_cast<size_t>(en->e.n_blocks) && m.n64 == n64) {
       en->e.blocks = m.blocks;
       en->e.stats = m.stats;
-      en->e.maxlen = reinterpret_cast<float*>(en->e.stats + en->e.n_blocks);
+      bind_ensemble_stats(en->e);
       en->e.xy64 = m.xy64;
       ctx->ens_cache.erase(ctx->ens_cache.begin() + static_cast<std::ptrdiff_t>(i));
       *out = en;
@@ -148,8 +148,8 @@ wln_status alloc_ensemble(wln_ctx* ctx, int32_t n_loops, int32_t ppl, bool fp64,
   }
   cudaError_t err = cudaMalloc(&en->e.blocks, n4 * sizeof(float4));
   if (err == cudaSuccess)
-    err = cudaMalloc(&en->e.stats, static_cast<size_t>(en->e.n_blocks) * (sizeof(float2) + sizeof(float)));
-  if (err == cudaSuccess) en->e.maxlen = reinterpret_cast<float*>(en->e.stats + en->e.n_blocks);
+    err = cudaMalloc(&en->e.stats, ensemble_stats_bytes(en->e.n_blocks, ppl));
+  if (err == cudaSuccess) bind_ensemble_stats(en->e);
   if (err == cudaSuccess && fp64) err = cudaMalloc(&en->e.xy64, n64 * sizeof(double));
   if (err != cudaSuccess) {
     if (en->e.blocks) cudaFree(en->e.blocks);
@@ -559,7 +559,7 @@ wln_status wln_ensemble_from_host(wln_ctx* ctx, const float* xy, int32_t n_loops
     src = d_xy;
   }
   if (err == cudaSuccess) err = launch_pack_loops(ctx->stream, src, en->e, d_deg);
-  ctx->launches += 3;
+  ctx->launches += 4;   // pack, degeneracy check, block and sub-block statistics
   if (err != cudaSuccess) {
     wln_free_ensemble(ctx, en);
     return cuda_fail(ctx, err, "pack loops");

@@ -366,8 +366,46 @@ __global__ void block_stats_kernel(const float4* blocks, int32_t n_loops, int32_
   }
 }
 
+// The block statistics per sub-block of kSubRows rows, one warp each: the
+// longest segment starting in the rows (the last one ending at the next
+// row's first point, cyclically) and the largest |y| of their points and of
+// that next point, rounded up as the block's.  Every segment a chunk of at
+// most kSubRows aligned rows walks, and its end points, are covered.
+__global__ void sub_stats_kernel(const float4* blocks, int32_t n_loops, int32_t ppl,
+                                 int32_t n_blocks, int32_t n_sub, float2* sub) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= static_cast<int64_t>(n_blocks) * n_sub) return;
+  const int64_t b = item / n_sub;
+  const int c = static_cast<int>(item - b * n_sub);
+  const int rows = ppl / 2;
+  const int r0 = c * kSubRows, r1 = min(rows, r0 + kSubRows);
+  const float4* base = blocks + b * rows * 32 + lane;
+  float d2 = 0.f, r2 = 0.f;
+  if (b * 32 + lane < n_loops) {
+    for (int r = r0; r < r1; ++r) {
+      const float4 a = base[static_cast<size_t>(r) * 32];
+      const float4 n = base[static_cast<size_t>((r + 1) % rows) * 32];
+      const float ux = a.z - a.x, uy = a.w - a.y, vx = n.x - a.z, vy = n.y - a.w;
+      d2 = fmaxf(d2, fmaxf(ux * ux + uy * uy, vx * vx + vy * vy));
+      r2 = fmaxf(r2, fmaxf(fmaxf(a.x * a.x + a.y * a.y, a.z * a.z + a.w * a.w),
+                           n.x * n.x + n.y * n.y));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+  }
+  if (lane == 0) sub[item] = make_float2(sqrtf(d2) * (1.0f + 0x1p-20f), sqrtf(r2) * (1.0f + 0x1p-20f));
+}
+
 cudaError_t launch_block_stats(cudaStream_t s, const Ensemble& e) {
   block_stats_kernel<<<e.n_blocks, 256, 0, s>>>(e.blocks, e.n_loops, e.ppl, e.stats, e.maxlen);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t n = static_cast<int64_t>(e.n_blocks) * e.n_sub;
+  sub_stats_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(e.blocks, e.n_loops, e.ppl,
+                                                                     e.n_blocks, e.n_sub, e.sub_stats);
   return cudaGetLastError();
 }
 
@@ -400,7 +438,7 @@ size_t gen_loops_work_bytes(int32_t n_blocks, int32_t ppl) {
 
 int gen_loops_launches(int32_t n_blocks, int32_t ppl) {
   const int slice = gen_slice_blocks(n_blocks, ppl);
-  return 2 * ((n_blocks + slice - 1) / slice) + 2;
+  return 2 * ((n_blocks + slice - 1) / slice) + 3;
 }
 
 cudaError_t launch_gen_loops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,
@@ -445,7 +483,7 @@ size_t gen_dloops_work_bytes(int32_t n_blocks, int32_t ppl) {
 
 int gen_dloops_launches(int32_t n_blocks, int32_t ppl) {
   const int slice = gen_dslice_blocks(n_blocks, ppl);
-  return 2 * ((n_blocks + slice - 1) / slice) + 2;
+  return 2 * ((n_blocks + slice - 1) / slice) + 3;
 }
 
 cudaError_t launch_gen_dloops(cudaStream_t s, uint64_t seed, const Ensemble& e, void* work,

@@ -58,10 +58,26 @@ struct Ensemble {
   float4* blocks = nullptr;   // [n_blocks][ppl/2][32]
   double* xy64 = nullptr;     // optional [n_loops][2][ppl]
   float2* stats = nullptr;    // [n_blocks]: longest segment, largest |y| of the block's loops
-  float* maxlen = nullptr;    // [n_blocks]: longest loop (sum of its segment lengths), in
-                              // the same allocation as stats
+  float2* sub_stats = nullptr;  // [n_blocks][n_sub]: the same over kSubRows rows (their
+                                // segments, the next row's first point included)
+  float* maxlen = nullptr;    // [n_blocks]: longest loop (sum of its segment lengths)
+  int32_t n_sub = 0;          // ceil(ppl / 2 / kSubRows); stats, sub_stats and maxlen
+                              // share one allocation (ensemble_stats_bytes)
   float ymax = 0.0f;          // host copy of the largest |y| of any loop (host-side bounds)
 };
+
+constexpr int kSubRows = 64;   // rows (point pairs) per sub-block of the statistics
+inline int32_t ensemble_n_sub(int32_t ppl) { return (ppl / 2 + kSubRows - 1) / kSubRows; }
+inline size_t ensemble_stats_bytes(int32_t n_blocks, int32_t ppl) {
+  return static_cast<size_t>(n_blocks) * (1 + ensemble_n_sub(ppl)) * sizeof(float2) +
+         static_cast<size_t>(n_blocks) * sizeof(float);
+}
+// The views into the statistics allocation at e.stats.
+inline void bind_ensemble_stats(Ensemble& e) {
+  e.n_sub = ensemble_n_sub(e.ppl);
+  e.sub_stats = e.stats + e.n_blocks;
+  e.maxlen = reinterpret_cast<float*>(e.sub_stats + static_cast<size_t>(e.n_blocks) * e.n_sub);
+}
 
 // Per-profile constants used by the Wilson kernels.
 struct ProfileDev {

@@ -280,6 +280,8 @@ struct KParams {
   int* flag;
   double* loops_out;     // per-loop mode: [n_points][n_loops][2]
   const float2* stats;   // per block: longest segment, largest |y|
+  const float2* sub_stats;  // the same per (block, kSubRows rows)
+  int32_t n_sub;         // sub-blocks per block
   const float* maxlen;   // per block: longest loop
   int* item_counter;     // items claimed beyond the first wave (zeroed before the launch);
                          // nullptr: the static round-robin schedule
@@ -302,8 +304,9 @@ struct KParams {
 // float: the margins are far above its rounding.)
 struct LowAngle {
   float two_span_sT, sT, rho_min, l2;
-  __device__ __forceinline__ int block(const KParams& k, int b) const {
-    const float2 st = k.stats[b];
+  __device__ __forceinline__ int block(const KParams& k, int b) const { return of(k.stats[b]); }
+  // the form the statistics st (longest segment, largest |y|) allow
+  __device__ __forceinline__ int of(const float2 st) const {
     const float gap = fmaxf(0.0f, rho_min - sT * st.y);
     const float lhs = two_span_sT * st.x, rhs = sqrtf(l2 + gap * gap);
     return lhs <= 0.09f * rhs ? 3 : (lhs <= 0.3f * rhs ? 2 : (lhs <= 0.9f * rhs ? 1 : 0));
@@ -1148,8 +1151,9 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   // double and double-float, formed where W is formed
   auto st_d = [&]() { return prof.spin_per * tile.T; };
   // the form of theta for block b (the same on every lane), from the block's
-  // statistics; sub-loop segments join points up to 4 apart
-  auto block_form = [&](int b) {
+  // statistics (sub == -1) or those of its sub-block sub; sub-loop segments
+  // join points up to 4 apart
+  auto block_form = [&](int b, int sub) {
     if (!(A::kLowAngle && k.low_angle && prof.kind == WLN_PROFILE_FLUX_TUBE && tile.n_valid > 0))
       return 0;
     double rho_min = k.rho[tile.rho0];
@@ -1157,9 +1161,21 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
     const LowAngle la{static_cast<float>(2.0 * (LV ? 4.0 : 1.0) * sqrt(tile.T)),
                       static_cast<float>(sqrt(tile.T)), static_cast<float>(rho_min),
                       static_cast<float>(prof.l2)};
-    int f = la.block(k, b);
+    int f = sub < 0 ? la.block(k, b)
+                    : la.of(k.sub_stats[static_cast<size_t>(b) * k.n_sub + sub]);
     if (!A::kFiveTerm && f == 2) f = 1;
     return k.low_angle >= 2 ? f : min(f, k.low_angle);   // level 2: the series forms too
+  };
+  // Whole loops, a chunk of rows [r0, r0 + n): the block's form, or where
+  // the block does not take the three-term series (whose spin unit holds
+  // for the whole block), the best of the block's and the chunk's sub-blocks'
+  // forms up to the five-term series.
+  auto chunk_form = [&](int b, int bform, int r0, int n) {
+    if (bform == 3) return 3;
+    int f = A::kFiveTerm ? 2 : 1;
+    for (int sb = r0 / kSubRows; sb <= (r0 + n - 1) / kSubRows && f > bform; ++sb)
+      f = min(f, block_form(b, sb));
+    return max(f, bform);
   };
   const int b0 = c * k.chain;
   const int b1 = min(b0 + k.chain, k.n_blocks);
@@ -1188,7 +1204,7 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
   for (int b = b0; b < b1; ++b) {
     const int loop = b * 32 + lane;
     const bool valid = loop < k.n_loops;
-    const int form = block_form(b);
+    const int form = block_form(b, -1);
     // the block's spin sums hold int dt/Q^2 itself, not twice it, where its
     // segments take the three-term series
     const bool half_spin = WalkT::kSeriesSpin && form == 3;
@@ -1218,10 +1234,11 @@ __device__ bool run_item(const KParams& k, Pipe& pp, double* acc, int c, const T
             else w[0].step(v.z, v.w);
             r = 1;
           }
-          // the form of theta for this block is the same on every lane
-          if (form == 3) rows_plain<3>(w, rowp, r, pp.chunk_rows);
-          else if (form == 2) rows_plain<2>(w, rowp, r, pp.chunk_rows);
-          else if (form == 1) rows_plain<1>(w, rowp, r, pp.chunk_rows);
+          // the form of theta for this chunk is the same on every lane
+          const int cf = chunk_form(b, form, ch * pp.chunk_rows, pp.chunk_rows);
+          if (cf == 3) rows_plain<3>(w, rowp, r, pp.chunk_rows);
+          else if (cf == 2) rows_plain<2>(w, rowp, r, pp.chunk_rows);
+          else if (cf == 1) rows_plain<1>(w, rowp, r, pp.chunk_rows);
           else rows_plain<0>(w, rowp, r, pp.chunk_rows);
         } else if constexpr (NEST) {
           // Rows in pairs hold points 4j .. 4j + 3: the full walk takes all
@@ -1625,6 +1642,8 @@ cudaError_t launch_any(cudaStream_t s, const WilsonPlan& plan_in, const Ensemble
   kp.n_tile_groups = plan.n_tile_groups; kp.n_chains = plan.n_chains; kp.n_items = plan.n_items;
   kp.flag = d_flag;
   kp.stats = e.stats;
+  kp.sub_stats = e.sub_stats;
+  kp.n_sub = e.n_sub;
   kp.maxlen = e.maxlen;
   kp.low_angle = plan.low_angle;
   if (guard) kp.guard = *guard;

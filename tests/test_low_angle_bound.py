@@ -97,6 +97,50 @@ def test_block_bound_covers_every_segment():
                 assert np.all(u <= u_block * (1 + 1e-12))
 
 
+def test_sub_block_bound_covers_every_segment():
+    """The per-chunk form takes a sub-block's statistics: the longest segment
+    starting in its 64 rows (128 points; the last one ends at the next
+    sub-block's first point) and the largest |y| of those points and that
+    next point.  Every segment a chunk walks stays within that bound."""
+    y = oracle.gen_loops(5, 64, 512)                       # 2 blocks, 4 sub-blocks each
+    d = np.roll(y, -1, axis=2) - y                         # segment k: point k -> k + 1
+    seg = np.sqrt(np.sum(d * d, axis=1))
+    rad = np.sqrt(np.sum(y * y, axis=1))
+    rad_end = np.maximum(rad, np.roll(rad, -1, axis=1))
+    lam = 0.7
+    for T in (1e-3, 0.5, 6.0):
+        for rho in (0.0, 2.0, 9.0):
+            for b in range(2):
+                lo = slice(32 * b, 32 * b + 32)
+                for c in range(4):
+                    ks = slice(128 * c, 128 * c + 128)
+                    dm, rm = seg[lo, ks].max(), rad_end[lo, ks].max()
+                    gap = max(0.0, rho - np.sqrt(T) * rm)
+                    u_sub = np.sqrt(T) * dm / np.sqrt(lam * lam + gap * gap)
+                    r = np.stack([rho + np.sqrt(T) * y[lo, 0, ks], np.sqrt(T) * y[lo, 1, ks]], axis=-1)
+                    dd = np.sqrt(T) * np.stack([d[lo, 0, ks], d[lo, 1, ks]], axis=-1)
+                    _, u = _theta_u(r, dd, lam)
+                    assert np.all(u <= u_sub * (1 + 1e-12))
+
+
+def test_sub_block_accounting():
+    """Per-chunk forms only improve on the block's, never reach the
+    three-term form the block does not take, and change nothing where a
+    block is a single sub-block."""
+    import bench
+    prof = I.Profile(I.PROFILE_FLUX_TUBE, F=10.0, lam=1.0)
+    rho = I.lin_grid(0.0, 4.0, 9)
+    T = I.log_grid(0.01, 10.0, 7)
+    y32 = oracle.gen_loops(6, 96, 1024).astype(np.float32)
+    blk = bench.low_angle_fraction(y32, [prof], [rho], [T], 4, 1.0)
+    sub = bench.low_angle_fraction(y32, [prof], [rho], [T], 4, 1.0, sub_rows=64)
+    assert sub[0] >= blk[0] and sub[1] >= blk[1] and sub[1] > blk[1]
+    assert sub[2] == blk[2]
+    y32 = oracle.gen_loops(6, 96, 128).astype(np.float32)
+    assert (bench.low_angle_fraction(y32, [prof], [rho], [T], 4, 1.0, sub_rows=64) ==
+            bench.low_angle_fraction(y32, [prof], [rho], [T], 4, 1.0))
+
+
 def test_accounting_extremes():
     import bench
     y32 = oracle.gen_loops(4, 64, 128).astype(np.float32)
