@@ -375,7 +375,8 @@ def host_buffers(wl: I.Workload, pinned: bool = True):
     b = {"S": buf(wl.n_points, G, 5), "prof": []}
     for r, t in zip(wl.rho, wl.T):
         n = len(r) * len(t)
-        b["prof"].append({"ferm": {"mean": buf(n), "sem": buf(n), "jk_var": buf(n), "cov": buf(n, n)},
+        b["prof"].append({"ferm": {"mean": buf(n), "sem": buf(n), "jk_var": buf(n),
+                                   "cov": buf(n * (n + 1) // 2)},
                           "scal": {"mean": buf(n), "sem": buf(n)}})
     b["gamma"] = (buf(len(wl.profiles), G), buf(len(wl.profiles), 2))
     return b
@@ -397,7 +398,8 @@ def run_step(ctx, wl: I.Workload, seed: int, prec: str, where: str = "device", c
         n = len(r) * len(t)
         Sq = S[off:off + n]
         pb = bufs["prof"][q] if bufs else {}
-        jf = ctx.jackknife(Sq, wl.n_groups, lpg, 1, jk_var=True, cov=cov, where=where,
+        jf = ctx.jackknife(Sq, wl.n_groups, lpg, 1, jk_var=True, cov="packed" if cov else False,
+                           where=where,
                            out=pb.get("ferm"))
         js = ctx.jackknife(Sq, wl.n_groups, lpg, 0, jk_var=False, cov=False, where=where,
                            out=pb.get("scal"))
@@ -710,7 +712,7 @@ def main():
             off = 0
             for q, (r, t) in enumerate(zip(wl.rho, wl.T)):
                 n = len(r) * len(t)
-                ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 1, jk_var=True, cov=True)
+                ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 1, jk_var=True, cov="packed")
                 ctx.jackknife(S[off:off + n], wl.n_groups, lpg, 0, jk_var=False, cov=False)
                 off += n
             _action(ctx, wl, S, lpg)
@@ -780,7 +782,7 @@ def main():
         "config": {"workload": wl.name, "n_loops": wl.n_loops, "ppl": wl.ppl,
                    "n_points": wl.n_points, "n_groups": wl.n_groups,
                    "precision": "fp32 compensated" if args.prec == "fp32" else "fp64",
-                   "covariance": "full, spinor, per profile",
+                   "covariance": "full, spinor, per profile (its upper triangle, packed)",
                    "l2": l2_note(ens_bytes, flush is not None, "regenerated every step", dev)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
                      "unit": "T FP32 op/s", "frac": achieved / peak_ops, "traffic": traffic,

@@ -369,6 +369,15 @@ wln_status wln_wilson_loops(wln_ctx* ctx, const wln_ensemble* ens,
 wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
                          int32_t n_groups, int32_t loops_per_group, int32_t comp,
                          double* mean, double* sem, double* jk_var, double* cov);
+/*
+ * As wln_jackknife, with the covariance (symmetric) as its upper triangle,
+ * row by row: cov_packed double[n_points (n_points + 1) / 2], cov(p, q) for
+ * q >= p at p n_points - p (p - 1) / 2 + (q - p).  The same values as the
+ * full matrix's, bit for bit, in half the bytes (host or device).
+ */
+wln_status wln_jackknife_packed(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                                int32_t n_groups, int32_t loops_per_group, int32_t comp,
+                                double* mean, double* sem, double* jk_var, double* cov_packed);
 
 /*
  * Group sums from per-loop values (wln_wilson_loops), with the paper's

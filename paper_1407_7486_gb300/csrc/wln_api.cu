@@ -925,9 +925,13 @@ wln_status wln_extrapolate(wln_ctx* ctx, const double* level_sums, int32_t n_poi
   return WLN_OK;
 }
 
-wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
-                         int32_t n_groups, int32_t loops_per_group, int32_t comp, double* mean,
-                         double* sem, double* jk_var, double* cov) {
+}  // extern "C"
+
+namespace wln {
+namespace {
+wln_status jackknife_impl(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                          int32_t n_groups, int32_t loops_per_group, int32_t comp, double* mean,
+                          double* sem, double* jk_var, double* cov, bool packed) {
   if (!ctx || !group_sums || !mean || !sem) return fail(ctx, WLN_EINVAL, "null argument");
   if (n_points < 1 || n_groups < 2 || loops_per_group < 1 || comp < 0 || comp >= WLN_K)
     return fail(ctx, WLN_EINVAL, "bad jackknife sizes");
@@ -941,7 +945,10 @@ wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_point
   const size_t o_dev = cov ? cv.take<double>(static_cast<size_t>(n_groups) * n_points) : 0;
   Out om = plan_out(cv, mean, n_points), os = plan_out(cv, sem, n_points);
   Out oj = plan_out(cv, jk_var, n_points);
-  Out oc = plan_out(cv, cov, cov ? static_cast<size_t>(n_points) * n_points : 0);
+  const size_t n_cov = !cov ? 0
+                      : packed ? static_cast<size_t>(n_points) * (n_points + 1) / 2
+                               : static_cast<size_t>(n_points) * n_points;
+  Out oc = plan_out(cv, cov, n_cov);
   wln_status st = ensure_scratch(ctx, cv.off + 256);
   if (st != WLN_OK) return st;
   bind_out(om, ctx->scratch.ptr); bind_out(os, ctx->scratch.ptr);
@@ -959,13 +966,31 @@ wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_point
                            static_cast<double*>(om.dev), static_cast<double*>(os.dev),
                            static_cast<double*>(oj.dev),
                            cov ? at<double>(ctx->scratch.ptr, o_dev) : nullptr,
-                           static_cast<double*>(oc.dev), &launches);
+                           static_cast<double*>(oc.dev), &launches, packed);
   ctx->launches += launches;
   for (const Out* o : {&om, &os, &oj, &oc})
     if (err == cudaSuccess) err = copy_back(*o, ctx->stream);
   if (err != cudaSuccess) return cuda_fail(ctx, err, "jackknife");
   if (om.host || os.host || oj.host || oc.host || !s_dev) return check_flag(ctx);
   return WLN_OK;
+}
+}  // namespace
+}  // namespace wln
+
+extern "C" {
+
+wln_status wln_jackknife(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                         int32_t n_groups, int32_t loops_per_group, int32_t comp, double* mean,
+                         double* sem, double* jk_var, double* cov) {
+  return wln::jackknife_impl(ctx, group_sums, n_points, n_groups, loops_per_group, comp, mean,
+                             sem, jk_var, cov, false);
+}
+
+wln_status wln_jackknife_packed(wln_ctx* ctx, const double* group_sums, int32_t n_points,
+                                int32_t n_groups, int32_t loops_per_group, int32_t comp,
+                                double* mean, double* sem, double* jk_var, double* cov_packed) {
+  return wln::jackknife_impl(ctx, group_sums, n_points, n_groups, loops_per_group, comp, mean,
+                             sem, jk_var, cov_packed, true);
 }
 
 wln_status wln_loop_sem(wln_ctx* ctx, const double* group_sums, int32_t n_points,

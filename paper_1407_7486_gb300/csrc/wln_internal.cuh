@@ -332,9 +332,12 @@ cudaError_t launch_reduce_partials(cudaStream_t s, const WilsonPlan& plan, const
                                    int32_t loops_per_group, double* group_sums);
 
 // Statistics (wln_stats.cu).
+// cov_packed: the covariance as its upper triangle, row by row
+// (n (n + 1) / 2 doubles), else the full n x n matrix.
 cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
                              int32_t lpg, int32_t comp, double* mean, double* sem,
-                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches);
+                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches,
+                             bool cov_packed = false);
 cudaError_t launch_extrapolate(cudaStream_t s, const double* level_sums, int32_t n_points,
                                int32_t G, int32_t lpg, double* out);
 cudaError_t launch_loop_sem(cudaStream_t s, const double* S, int32_t n_points, int32_t G,

@@ -75,10 +75,14 @@ __global__ void extrapolate_kernel(const double* S, int32_t n_points, int32_t G,
 
 // cov[p][q] = sum_g dev[g][p] dev[g][q] / (G (G - 1)).  64x64 tiles, only
 // tiles on or above the diagonal are computed; the mirror image is written
-// through a shared-memory transpose so both stores are coalesced.
+// through a shared-memory transpose so both stores are coalesced.  Packed:
+// only q >= p, row p at p n - p (p - 1) / 2 (the upper triangle row by row).
 constexpr int kTile = 64, kKc = 16;
+__device__ __forceinline__ int64_t packed_index(int64_t p, int64_t q, int64_t n) {
+  return p * n - p * (p - 1) / 2 + (q - p);
+}
 __global__ void __launch_bounds__(256) covariance_kernel(const double* dev, int32_t n_points,
-                                                         int32_t G, double* cov) {
+                                                         int32_t G, double* cov, int packed) {
   const int ti = blockIdx.y, tj = blockIdx.x;
   if (ti > tj) return;
   __shared__ double a[kKc][kTile], b[kKc][kTile];
@@ -115,11 +119,15 @@ __global__ void __launch_bounds__(256) covariance_kernel(const double* dev, int3
     for (int c = 0; c < 4; ++c) {
       const int q = tj * kTile + tx * 4 + c;
       acc[r][c] *= scale;
-      if (p < n_points && q < n_points) cov[static_cast<int64_t>(p) * n_points + q] = acc[r][c];
-      tr[ty * 4 + r][tx * 4 + c] = acc[r][c];
+      if (packed) {
+        if (q >= p && q < n_points) cov[packed_index(p, q, n_points)] = acc[r][c];
+      } else {
+        if (p < n_points && q < n_points) cov[static_cast<int64_t>(p) * n_points + q] = acc[r][c];
+        tr[ty * 4 + r][tx * 4 + c] = acc[r][c];
+      }
     }
   }
-  if (ti == tj) return;
+  if (packed || ti == tj) return;
   __syncthreads();
   for (int i = threadIdx.x; i < kTile * kTile; i += 256) {
     const int row = i / kTile, col = i % kTile;  // output row in tile tj, column in tile ti
@@ -468,7 +476,8 @@ __global__ void group_mean_sem_kernel(const double* x, int32_t n_rows, int32_t G
 
 cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, int32_t G,
                              int32_t lpg, int32_t comp, double* mean, double* sem,
-                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches) {
+                             double* jk_var, double* dev_scratch, double* cov, int64_t* launches,
+                             bool cov_packed) {
   const unsigned blocks = static_cast<unsigned>((n_points + 255) / 256);
   jackknife_kernel<<<blocks, 256, 0, s>>>(S, n_points, G, lpg, comp, mean, sem, jk_var,
                                           cov ? dev_scratch : nullptr);
@@ -476,7 +485,7 @@ cudaError_t launch_jackknife(cudaStream_t s, const double* S, int32_t n_points, 
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess || !cov) return err;
   const unsigned nt = static_cast<unsigned>((n_points + kTile - 1) / kTile);
-  covariance_kernel<<<dim3(nt, nt), 256, 0, s>>>(dev_scratch, n_points, G, cov);
+  covariance_kernel<<<dim3(nt, nt), 256, 0, s>>>(dev_scratch, n_points, G, cov, cov_packed ? 1 : 0);
   ++*launches;
   return cudaGetLastError();
 }

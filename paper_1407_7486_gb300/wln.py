@@ -66,6 +66,7 @@ SIGNATURES = {
                              ctypes.c_int),
     "wln_corrcoef": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_jackknife": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "wln_jackknife_packed": ([_P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "wln_loop_sem": ([_P, _P, _I32, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "wln_effective_action": ([_P, _P, _I32, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
                              ctypes.c_int),
@@ -451,10 +452,13 @@ class Context:
 
     # --------------------------------------------------------- statistics
     def jackknife(self, group_sums, n_groups: int, loops_per_group: int, comp: int,
-                  jk_var: bool = True, cov: bool = False, where: str = "device", out=None):
+                  jk_var: bool = True, cov=False, where: str = "device", out=None):
         """Group mean, SEM, jackknife variance and covariance; `out` may hold
-        caller-owned buffers under the same keys (reused across calls)."""
+        caller-owned buffers under the same keys (reused across calls).
+        cov="packed": the covariance as its upper triangle, row by row
+        (wln_jackknife_packed)."""
         n_points = group_sums.shape[0]
+        packed = cov == "packed"
         out = out or {}
         mean = out.get("mean")
         mean = self._empty((n_points,), np.float64, where) if mean is None else mean
@@ -465,10 +469,11 @@ class Context:
             jv = self._empty((n_points,), np.float64, where)
         cv = out.get("cov") if cov else None
         if cov and cv is None:
-            cv = self._empty((n_points, n_points), np.float64, where)
-        self._check(load().wln_jackknife(self.handle, _ptr(group_sums), n_points, n_groups,
-                                         loops_per_group, comp, _ptr(mean), _ptr(sem), _ptr(jv),
-                                         _ptr(cv)))
+            shape = (n_points * (n_points + 1) // 2,) if packed else (n_points, n_points)
+            cv = self._empty(shape, np.float64, where)
+        fn = load().wln_jackknife_packed if packed else load().wln_jackknife
+        self._check(fn(self.handle, _ptr(group_sums), n_points, n_groups, loops_per_group, comp,
+                       _ptr(mean), _ptr(sem), _ptr(jv), _ptr(cv)))
         return {"mean": mean, "sem": sem, "jk_var": jv, "cov": cv}
 
     def loop_sem(self, group_sums, n_groups: int, n_loops: int, comp_sum: int, comp_sq: int,

@@ -276,6 +276,29 @@ def test_statistics_match_oracle(ctx):
     assert np.allclose(rd["cov"].cpu().numpy(), r["cov"], rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("n_points", [1, 63, 64, 65, 300])
+def test_packed_covariance_is_the_upper_triangle(ctx, n_points):
+    """wln_jackknife_packed: the upper triangle of the full covariance, row by
+    row, bit for bit (tile edges at 64 points, a ragged last tile), from host
+    and device inputs into host and device outputs; mean, SEM and jackknife
+    variance as the full call's."""
+    rng = np.random.default_rng(n_points)
+    G, lpg = 16, 10
+    S = rng.normal(size=(n_points, G, 5)) * 3.0
+    full = ctx.jackknife(S, G, lpg, 1, jk_var=True, cov=True, where="host")
+    pk = ctx.jackknife(S, G, lpg, 1, jk_var=True, cov="packed", where="host")
+    iu = np.triu_indices(n_points)
+    assert pk["cov"].shape == (n_points * (n_points + 1) // 2,)
+    assert np.array_equal(pk["cov"], full["cov"][iu])
+    for k in ("mean", "sem", "jk_var"):
+        assert np.array_equal(pk[k], full[k])
+    assert np.allclose(pk["cov"], ost.covariance(S, lpg, 1)[iu], rtol=1e-12, atol=1e-16)
+    Sd = torch.from_numpy(S).cuda()
+    pd = ctx.jackknife(Sd, G, lpg, 1, cov="packed")
+    torch.cuda.synchronize()
+    assert np.array_equal(pd["cov"].cpu().numpy(), pk["cov"])
+
+
 @pytest.mark.parametrize("spinor", [True, False])
 def test_effective_action_matches_oracle(ctx, spinor):
     profs = [I.Profile(0, F=10.0, lam=1.0), I.Profile(0, F=2.0, lam=0.5), I.Profile(1, B=0.5)]
