@@ -973,7 +973,10 @@ def run_batched(args, wl: I.Workload):
     line["autotune"] = {k: v for k, v in tuned.items() if k != "candidates"}
     line["autotune_candidates"] = tuned.get("candidates")
     line["finite_gamma"] = bool(np.isfinite(g).all())
-    b.free(); ens.free(); ctx.close()
+    b.free(); ens.free()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, ctx)
+    ctx.close()
     print(json.dumps(line))
 
 
@@ -1194,6 +1197,50 @@ def run_levels(args, wl: I.Workload):
     print(json.dumps(line))
 
 
+def _correlation_cpu(ctx, wl: I.Workload, prof, rho, T, W):
+    """The oracle on the host cores for the correlation step on a bounded
+    sample: every loop's W - 1 (its per-loop values) at every 8th radius and
+    time for the first 1024 loops, their contiguous group sums and Eq.
+    corrcoef with the sample's mid-T point at rho = 0, timed together; and
+    the GPU's per-loop values on that sample against the oracle's."""
+    import oracle
+    from oracle import stats as ost
+    threads = oracle.max_threads()
+    ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
+    y32, _ = ctx.loops_copy(ens)
+    ens.free()
+    n_cpu = min(1024, wl.n_loops)
+    ir, it = np.arange(0, len(rho), 8), np.arange(0, len(T), 8)
+    y = y32[:n_cpu].astype(np.float64)
+    t0 = time.perf_counter()
+    Wc = oracle.loop_values(y, prof, rho[ir], T[it], threads=threads)
+    ost.group_sums_perm(Wc, max(2, n_cpu // (wl.n_loops // wl.n_groups)))
+    ost.corrcoef_ref(Wc[:, :, 1], (len(it) // 2) * len(ir))
+    cpu_s = time.perf_counter() - t0
+    pts = (it[:, None] * len(rho) + ir[None, :]).ravel()
+    import torch
+    Wg = W[torch.as_tensor(pts, device=W.device), :n_cpu].cpu().numpy()
+    # each loop's cosh(spin) scales its spinor error (the fermion factor, Sec.
+    # "Uncertainties and the Fermion Problem")
+    cosh = np.empty(Wc.shape[:2])
+    for j, (a, b) in enumerate((t_, r_) for t_ in it for r_ in ir):
+        _, sp = oracle.phase_spin(y, prof, float(rho[b]), float(T[a]), threads=threads)
+        with np.errstate(over="ignore"):
+            cosh[j] = np.cosh(sp)
+    with np.errstate(over="ignore", invalid="ignore"):
+        fin = np.isfinite(Wc[:, :, 1]) & np.isfinite(Wg[:, :, 1]) & np.isfinite(cosh)
+        e_f = float(np.where(fin, np.abs(Wg[:, :, 1] - Wc[:, :, 1]) / np.maximum(1.0, cosh), 0.0).max())
+    e_s = float(np.abs(Wg[:, :, 0] - Wc[:, :, 0]).max())
+    cpu = {"value": n_cpu * len(pts) / cpu_s, "unit": "loop-point evals/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"F={prof.F}, {len(ir)} rho x {len(it)} T (every 8th), the first {n_cpu} loops "
+                     f"x {wl.ppl} ppl: per-loop values, group sums, corrcoef; {cpu_s:.1f} s"}
+    err = {"per_loop_scalar_max_abs": e_s,
+           "per_loop_spinor_max_rel_to_max(1,cosh s)": e_f,
+           "loops_x_points": int(n_cpu * len(pts))}
+    return cpu, err
+
+
 def run_correlation(args, wl: I.Workload):
     """Correlations between evaluations and randomised grouping (Sec.
     "Correlations between Wilson Loops", Sec. "Grouping Worldlines"): per
@@ -1248,7 +1295,7 @@ def run_correlation(args, wl: I.Workload):
         # end to end with host buffers: values stay on the device, the three
         # correlation curves come back
         t0 = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 2))
+        e2e_steps = args.steps
         for _ in range(e2e_steps):
             ens = ctx.gen_loops(wl.seed, wl.n_loops, wl.ppl)
             ctx.wilson_loops(ens, prof, rho, T, prec=args.prec, out=W)
@@ -1292,6 +1339,9 @@ def run_correlation(args, wl: I.Workload):
                    int(sum(a.nbytes for a in rho + T)), "d2h_bytes_per_step": int(3 * n_points * 8)}
     line["gpu_launches"] = int(launches)
     line["clocks"] = clk.summary()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"], line["gpu_error_vs_oracle_on_sample"] = _correlation_cpu(
+            ctx, wl, prof[0], rho[0], T[0], W)
     others = np.arange(n_points) != ref
     line["corr_with_reference"] = {
         "reference_point": {"T": float(T[0][ref // len(rho[0])]), "rho": 0.0},
